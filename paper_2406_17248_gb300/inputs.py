@@ -1,0 +1,246 @@
+"""Seeded synthetic workloads for the state-vector VQA hot path.
+
+This module only *describes* inputs: gate lists, Pauli-sum Hamiltonians, graphs
+and parameter vectors drawn from seeded numpy generators.  It contains none of
+the simulation arithmetic (no gate matrices, no amplitudes, no expectations), so
+both the FP64 oracle and the CUDA path can consume the same inputs without
+sharing any of the method's code.
+
+Workload recipes (shapes follow the paper's benchmarks, §7.1 random circuits and
+§7.2 QAOA MaxCut, and the ansatz/Hamiltonian families of §4.2 and §5.2):
+
+* ``random_circuit``   gate kind uniform over {H, RX, RY, RZ, CNOT, CZ}; one-qubit
+                       targets uniform in [0, n); two-qubit (control, target)
+                       uniform over ordered distinct pairs; angles U[-pi, pi].
+* ``hea_circuit``      hardware-efficient ansatz: per layer RY then RZ on every
+                       qubit (one parameter each; order layer, qubit, (RY, RZ)),
+                       then an open CNOT ladder i -> i+1.
+* ``chain_zz_x``       H = sum_i Z_i Z_{i+1} + hx * sum_i X_i on an open chain.
+* ``tfim``             H = sum_i J_i Z_i Z_{i+1} + h sum_i X_i, J_i ~ N(1, 0.2),
+                       h ~ U[0.5, 1.5].
+* ``random_regular_graph``  configuration (pairing) model with rejection of
+                       self-loops and multi-edges.
+* ``erdos_renyi``      G(n, p).
+* ``qaoa_circuit``     |+>^n, then per layer RZZ(gamma_l) on every edge followed by
+                       RX(beta_l) on every qubit (cost first, mixer second, §5.2).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+# Gate kinds understood by both sides (names follow §2.3; CNOT = X with one
+# control, CZ = Z with one control, §2.3.5).
+FIXED_GATES = ("I", "X", "Y", "Z", "H", "S", "SDG", "T", "TDG", "SWAP")
+PARAM_GATES = ("RX", "RY", "RZ", "PS", "RXX", "RYY", "RZZ")
+MATRIX_GATES = ("MATRIX",)
+ALL_GATES = FIXED_GATES + PARAM_GATES + MATRIX_GATES
+TWO_TARGET = ("SWAP", "RXX", "RYY", "RZZ")
+
+
+@dataclasses.dataclass(frozen=True)
+class Gate:
+    """One gate record: kind, target qubits, control qubits and its angle binding.
+
+    angle = const + coef * params[param]   (param = -1: fixed angle = const)
+    ``matrix`` (row-major, complex) is only used by kind "MATRIX"; its basis index
+    is sum_j bit(targets[j]) << j.
+    """
+
+    kind: str
+    targets: Tuple[int, ...]
+    ctrls: Tuple[int, ...] = ()
+    param: int = -1
+    coef: float = 1.0
+    const: float = 0.0
+    matrix: Optional[Tuple[complex, ...]] = None
+
+    def angle(self, params: Sequence[float]) -> float:
+        if self.param < 0:
+            return float(self.const)
+        return float(self.const + self.coef * params[self.param])
+
+
+@dataclasses.dataclass
+class Circuit:
+    n_qubits: int
+    gates: List[Gate]
+    n_params: int = 0
+
+
+@dataclasses.dataclass
+class PauliSum:
+    """sum_k coef_k * P_k with each P_k given as (xmask, zmask); Y = both bits set."""
+
+    n_qubits: int
+    xmask: np.ndarray  # uint64[n_terms]
+    zmask: np.ndarray  # uint64[n_terms]
+    coef: np.ndarray  # float64[n_terms]
+
+    @property
+    def n_terms(self) -> int:
+        return int(self.coef.shape[0])
+
+
+def pauli_sum_from_strings(n_qubits: int, terms: Sequence[Tuple[float, str]]) -> PauliSum:
+    """Parse terms like (2.0, "X0 Z1") into masks (§2.5.1 string notation)."""
+    xs, zs, cs = [], [], []
+    for coef, word in terms:
+        x = z = 0
+        for tok in word.split():
+            p, q = tok[0].upper(), int(tok[1:])
+            if not 0 <= q < n_qubits:
+                raise ValueError(f"qubit {q} out of range in {word!r}")
+            bit = 1 << q
+            if (x | z) & bit:
+                raise ValueError(f"qubit {q} repeated in {word!r}")
+            if p == "X":
+                x |= bit
+            elif p == "Y":
+                x |= bit
+                z |= bit
+            elif p == "Z":
+                z |= bit
+            else:
+                raise ValueError(f"bad Pauli {p!r}")
+        xs.append(x)
+        zs.append(z)
+        cs.append(float(coef))
+    return PauliSum(n_qubits, np.array(xs, dtype=np.uint64), np.array(zs, dtype=np.uint64),
+                    np.array(cs, dtype=np.float64))
+
+
+# --------------------------------------------------------------------------- circuits
+
+def random_circuit(n: int, n_gates: int, seed: int) -> Circuit:
+    rng = np.random.default_rng(seed)
+    kinds = ("H", "RX", "RY", "RZ", "CNOT", "CZ")
+    gates: List[Gate] = []
+    for _ in range(n_gates):
+        k = kinds[int(rng.integers(0, len(kinds)))]
+        if k in ("CNOT", "CZ"):
+            c = int(rng.integers(0, n))
+            t = int(rng.integers(0, n - 1))
+            if t >= c:
+                t += 1
+            gates.append(Gate("X" if k == "CNOT" else "Z", (t,), (c,)))
+        else:
+            t = int(rng.integers(0, n))
+            if k == "H":
+                gates.append(Gate("H", (t,)))
+            else:
+                gates.append(Gate(k, (t,), const=float(rng.uniform(-np.pi, np.pi))))
+    return Circuit(n, gates, 0)
+
+
+def hea_circuit(n: int, layers: int) -> Circuit:
+    gates: List[Gate] = []
+    p = 0
+    for _ in range(layers):
+        for q in range(n):
+            gates.append(Gate("RY", (q,), param=p))
+            gates.append(Gate("RZ", (q,), param=p + 1))
+            p += 2
+        for q in range(n - 1):
+            gates.append(Gate("X", (q + 1,), (q,)))
+    return Circuit(n, gates, p)
+
+
+def uniform_params(count: int, seed: int, lo: float = -np.pi, hi: float = np.pi) -> np.ndarray:
+    return np.random.default_rng(seed).uniform(lo, hi, size=count)
+
+
+def chain_zz_x(n: int, hx: float = 0.5) -> PauliSum:
+    terms = [(1.0, f"Z{i} Z{i + 1}") for i in range(n - 1)]
+    terms += [(hx, f"X{i}") for i in range(n)]
+    return pauli_sum_from_strings(n, terms)
+
+
+def tfim(n: int, rng: np.random.Generator) -> PauliSum:
+    J = rng.normal(1.0, 0.2, size=n - 1)
+    h = float(rng.uniform(0.5, 1.5))
+    terms = [(float(J[i]), f"Z{i} Z{i + 1}") for i in range(n - 1)]
+    terms += [(h, f"X{i}") for i in range(n)]
+    return pauli_sum_from_strings(n, terms)
+
+
+# --------------------------------------------------------------------------- graphs
+
+def random_regular_graph(n: int, d: int, seed: int, max_tries: int = 10000) -> List[Tuple[int, int]]:
+    if (n * d) % 2 or d >= n:
+        raise ValueError("n*d must be even and d < n")
+    rng = np.random.default_rng(seed)
+    for _ in range(max_tries):
+        stubs = np.repeat(np.arange(n), d)
+        rng.shuffle(stubs)
+        pairs = stubs.reshape(-1, 2)
+        ok = True
+        seen = set()
+        for a, b in pairs:
+            a, b = int(a), int(b)
+            if a == b:
+                ok = False
+                break
+            e = (min(a, b), max(a, b))
+            if e in seen:
+                ok = False
+                break
+            seen.add(e)
+        if ok:
+            return sorted(seen)
+    raise RuntimeError("pairing model failed")
+
+
+def erdos_renyi(n: int, p: float, seed: int) -> List[Tuple[int, int]]:
+    rng = np.random.default_rng(seed)
+    edges = []
+    for i in range(n):
+        for j in range(i + 1, n):
+            if rng.random() < p:
+                edges.append((i, j))
+    return edges
+
+
+def complete_graph(n: int) -> List[Tuple[int, int]]:
+    return [(i, j) for i in range(n) for j in range(i + 1, n)]
+
+
+def maxcut_zz(n: int, edges: Sequence[Tuple[int, int]]) -> PauliSum:
+    return pauli_sum_from_strings(n, [(1.0, f"Z{a} Z{b}") for a, b in edges])
+
+
+def qaoa_circuit(n: int, edges: Sequence[Tuple[int, int]], p: int, gamma_coef: float = 1.0) -> Circuit:
+    """Gate-level QAOA: H on every qubit, then per layer RZZ(gamma_coef*gamma_l) on
+    every edge and RX(beta_l) on every qubit.  Parameters: [gamma_1..gamma_p,
+    beta_1..beta_p].  gamma_coef = 2 gives the exp(-i gamma sum ZZ) form."""
+    gates: List[Gate] = [Gate("H", (q,)) for q in range(n)]
+    for l in range(p):
+        for a, b in edges:
+            gates.append(Gate("RZZ", (a, b), param=l, coef=gamma_coef))
+        for q in range(n):
+            gates.append(Gate("RX", (q,), param=p + l))
+    return Circuit(n, gates, 2 * p)
+
+
+# --------------------------------------------------------------------------- batches
+
+@dataclasses.dataclass
+class Instance:
+    circuit: Circuit
+    ham: PauliSum
+    params: np.ndarray
+
+
+def batched_vqe(count: int, seed: int, n_range=(10, 20), depth_range=(2, 10)) -> List[Instance]:
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        depth = int(rng.integers(depth_range[0], depth_range[1] + 1))
+        circ = hea_circuit(n, depth)
+        ham = tfim(n, rng)
+        params = rng.uniform(-np.pi, np.pi, size=circ.n_params)
+        out.append(Instance(circ, ham, params))
+    return out

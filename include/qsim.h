@@ -1,0 +1,204 @@
+/*
+ * qsim.h -- C ABI of the GB300 state-vector engine for variational quantum
+ * algorithms (MindSpore Quantum whitepaper, arXiv 2406.17248).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - A state of n qubits is 2^n complex amplitudes, little endian: qubit q is
+ *   bit q of the amplitude index (§2.6 "Basic Usage of Simulator").  Storage is
+ *   interleaved (re, im): float2 for QS_C64 (complex64), double2 for QS_C128
+ *   (complex128) (§2.1 "Data Type").
+ * - Every call returns a qs_status; nothing aborts.  On an error the call has
+ *   not modified any output, and qs_last_error() returns a message (thread-local,
+ *   valid until the next failing call on that thread).  Arguments are checked on
+ *   the host before any launch.
+ * - Device work is enqueued on the CUDA stream given at qs_state_create (the
+ *   state's stream).  Calls that return host values (energies, gradients,
+ *   samples, copies to host) synchronise that stream before returning; all
+ *   other calls are asynchronous with respect to the host.
+ * - Energies, gradients and inner products are returned in FP64 for both
+ *   dtypes; complex64 reductions accumulate in FP32 per thread over a bounded
+ *   run, then in FP64 in a fixed order, so results are bitwise repeatable for a
+ *   given launch configuration.
+ * - Pointers named dev_* are device pointers; every other pointer is host.
+ * - Handles are opaque and owned by the library; *_destroy frees them.
+ *   Device buffers passed in by the caller stay owned by the caller.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define QS_API __attribute__((visibility("default")))
+#else
+#define QS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QS_OK = 0,
+  QS_ERR_INVALID_ARG = 1,   /* bad handle, qubit index, size or mismatched n/dtype */
+  QS_ERR_OUT_OF_MEMORY = 2, /* a library allocation failed */
+  QS_ERR_CUDA = 3,          /* a CUDA runtime call failed (message has the CUDA error) */
+  QS_ERR_TIMEOUT = 4,       /* a bounded device-side wait ran out */
+  QS_ERR_UNSUPPORTED = 5    /* valid request outside what this build implements */
+} qs_status;
+
+typedef enum { QS_C64 = 0, QS_C128 = 1 } qs_dtype;
+
+/* Gate kinds.  Fixed gates §2.3.2; parameterised gates §2.3.3 with the
+ * half-angle convention R_P(theta) = exp(-i theta P / 2), and RZZ/RXX/RYY(theta)
+ * = exp(-i theta/2 P(x)P); PS(theta) = diag(1, e^{i theta}); custom matrix gates
+ * §2.3.4.  Any gate may carry control qubits (§2.3.5): it acts where every
+ * control bit is 1.  Two-target matrices use the basis index
+ * bit(targets[0]) + 2 * bit(targets[1]). */
+typedef enum {
+  QS_GATE_I = 0,
+  QS_GATE_X = 1,
+  QS_GATE_Y = 2,
+  QS_GATE_Z = 3,
+  QS_GATE_H = 4,
+  QS_GATE_S = 5,
+  QS_GATE_SDG = 6,
+  QS_GATE_T = 7,
+  QS_GATE_TDG = 8,
+  QS_GATE_SWAP = 9,
+  QS_GATE_RX = 16,
+  QS_GATE_RY = 17,
+  QS_GATE_RZ = 18,
+  QS_GATE_PS = 19,
+  QS_GATE_RXX = 20,
+  QS_GATE_RYY = 21,
+  QS_GATE_RZZ = 22,
+  QS_GATE_MATRIX = 32
+} qs_gate_kind;
+
+typedef struct qs_state qs_state;
+typedef struct qs_circuit qs_circuit;
+typedef struct qs_ham qs_ham;
+typedef struct qs_qaoa qs_qaoa;
+
+/* Execution options for a circuit plan.  Zero means "library default". */
+typedef struct {
+  int fuse;      /* 1 (default): fused shared-memory tile passes; -1: one kernel per gate */
+  int tile_bits; /* log2 amplitudes per fused tile, 6..13 (default 12 for c64, 11 for c128) */
+  int low_bits;  /* low (contiguous) qubits present in every tile, 1..tile_bits (default 4) */
+} qs_options;
+
+/* Library version string and the last error message of this thread. */
+QS_API const char* qs_version(void);
+QS_API const char* qs_last_error(void);
+
+/* ------------------------------------------------------------------ states */
+
+/* Create a state of n_qubits (1..34) and dtype on `cuda_stream` (a cudaStream_t,
+ * NULL = legacy default stream).  dev_buf: caller-owned device buffer of at
+ * least buf_bytes >= 2^n * sizeof(amplitude), 256-byte aligned; NULL = the
+ * library allocates (and later frees) the buffer.  Contents are undefined until
+ * a set_* or copy_in call. */
+QS_API qs_status qs_state_create(int n_qubits, qs_dtype dtype, void* dev_buf, size_t buf_bytes,
+                          void* cuda_stream, qs_state** out);
+QS_API qs_status qs_state_destroy(qs_state* s);
+/* Device pointer of the amplitudes (for zero-copy views by the caller). */
+QS_API qs_status qs_state_device_ptr(const qs_state* s, void** dev_ptr);
+/* |index>  (§2.6: the simulator starts in |0...0>). */
+QS_API qs_status qs_state_set_basis(qs_state* s, uint64_t index);
+/* |+>^n = 2^{-n/2} sum_x |x>  (the QAOA start state, §5.2). */
+QS_API qs_status qs_state_set_plus(qs_state* s);
+/* set_qs / get_qs (§2.6.2, §6.2): copy 2^n amplitudes of the state's dtype in
+ * or out.  src_on_device / dst_on_device: 1 = device pointer, 0 = host pointer. */
+QS_API qs_status qs_state_copy_in(qs_state* s, const void* src, int src_on_device);
+QS_API qs_status qs_state_copy_out(const qs_state* s, void* dst, int dst_on_device);
+/* dst <- src (same n and dtype). */
+QS_API qs_status qs_state_copy(qs_state* dst, const qs_state* src);
+/* sum_x |psi_x|^2 in FP64. */
+QS_API qs_status qs_state_norm2(const qs_state* s, double* out);
+
+/* ---------------------------------------------------------------- circuits */
+
+QS_API qs_status qs_circuit_create(int n_qubits, qs_circuit** out);
+QS_API qs_status qs_circuit_destroy(qs_circuit* c);
+/* Append one gate.  targets[n_t] (n_t = 1, or 2 for SWAP/RXX/RYY/RZZ/2-qubit
+ * MATRIX), ctrls[n_c] (n_c >= 0), all distinct and < n_qubits.
+ * Angle binding (§2.2 parameter resolver, linear in one parameter):
+ *   angle = constant + coef * params[param_idx]; param_idx = -1 for a fixed angle.
+ * matrix: for QS_GATE_MATRIX only, (2^n_t)^2 complex entries row-major as
+ * interleaved (re, im) doubles; the library copies it.  Invalidates any plan. */
+QS_API qs_status qs_circuit_add(qs_circuit* c, int kind, const int* targets, int n_t, const int* ctrls,
+                         int n_c, int param_idx, double coef, double constant, const double* matrix);
+/* Build the execution plan (fusion into tile passes) for `dtype`.  opts may be
+ * NULL.  Called implicitly by the first apply if absent. */
+QS_API qs_status qs_circuit_finalize(qs_circuit* c, qs_dtype dtype, const qs_options* opts);
+/* Plan statistics: gates, parameters (max param_idx + 1), forward HBM passes. */
+QS_API qs_status qs_circuit_info(const qs_circuit* c, int* n_gates, int* n_params, int* n_passes);
+
+/* psi <- U(params) psi: the circuit applied in order (§2.6.1 apply_circuit).
+ * params[n_params] on the host, n_params >= the circuit's parameter count. */
+QS_API qs_status qs_apply_circuit(qs_state* s, qs_circuit* c, const double* params, int n_params);
+
+/* ------------------------------------------------------------ Hamiltonians */
+
+/* H = sum_k coef[k] P_k with real coefficients (§2.5.1), P_k given by masks:
+ * bit q of xmask[k] / zmask[k] = X / Z on qubit q, both set = Y. */
+QS_API qs_status qs_ham_create(int n_qubits, int n_terms, const uint64_t* xmask, const uint64_t* zmask,
+                        const double* coef, qs_ham** out);
+QS_API qs_status qs_ham_destroy(qs_ham* h);
+
+/* dst <- H src, unnormalised (§2.6.1 apply_hamiltonian).  dst != src. */
+QS_API qs_status qs_apply_hamiltonian(qs_state* dst, const qs_state* src, const qs_ham* h);
+/* *energy = <psi|H|psi> (§2.6.2 get_expectation; real for real coefficients). */
+QS_API qs_status qs_expectation(const qs_state* s, const qs_ham* h, double* energy);
+/* out2[0] + i out2[1] = <bra|ket> (§2.6.2, the H = I case). */
+QS_API qs_status qs_inner_product(const qs_state* bra, const qs_state* ket, double* out2);
+
+/* Energy and its gradient with respect to every parameter by the adjoint
+ * method (§4.1 get_expectation_with_grad; adjoint method named in §7.2):
+ *   psi_N = U psi_0, E = <psi_N|H|psi_N>, lam = H psi_N, then for k = N..1:
+ *   psi <- U_k^dag psi, grad[p(k)] += coef_k * 2 Re <lam| dU_k |psi>, lam <- U_k^dag lam.
+ * psi: holds psi_0 on entry; on return it holds psi_0 again up to rounding.
+ * lam: a second state of the same n and dtype, used as the adjoint buffer.
+ * energy: host double; grad: host double[n_params] (overwritten). */
+QS_API qs_status qs_expectation_with_grad(qs_state* psi, qs_state* lam, qs_circuit* c, const qs_ham* h,
+                                   const double* params, int n_params, double* energy, double* grad);
+
+/* Draw `shots` outcomes of measuring every qubit (§2.6.3 sampling): outcome s is
+ * the smallest x with cdf(x) > u_s * cdf(2^n - 1), cdf the FP64 prefix sums of
+ * |psi_x|^2 and u_s = splitmix64(seed + s * 0x9E3779B97F4A7C15) >> 11, times 2^-53.
+ * out_bits: host uint64[shots], little-endian bitstrings. */
+QS_API qs_status qs_sample(const qs_state* s, uint64_t shots, uint64_t seed, uint64_t* out_bits);
+
+/* -------------------------------------------------------------------- QAOA */
+
+/* MaxCut QAOA engine (§5.2 ansatz; QuPack QAOA simulator interface §6.2):
+ * cost C(x) = sum_{(a,b) in edges} z_a z_b, z = 1 - 2 bit; start |+>^n; layer
+
+ * (n_qubits >= 4) l = 1..p applies exp(-i gamma_scale * gamma_l * C) then RX(beta_l) on every
+ * qubit.  gamma_scale = 1: the QuPack form; 0.5: RZZ(gamma_l) on every edge.
+ * edges: host int[2 * n_edges] (pairs of distinct qubits, no repeats).
+ * opts may be NULL. */
+QS_API qs_status qs_qaoa_create(int n_qubits, const int* edges, int n_edges, int p, double gamma_scale,
+                         qs_dtype dtype, const qs_options* opts, qs_qaoa** out);
+QS_API qs_status qs_qaoa_destroy(qs_qaoa* q);
+/* Forward passes and planned HBM traffic of one energy+gradient evaluation. */
+QS_API qs_status qs_qaoa_info(const qs_qaoa* q, int* fwd_passes, int* rev_passes, double* bytes_per_eval);
+/* psi <- U(gamma, beta)|+>^n (QuPack evolution()). */
+QS_API qs_status qs_qaoa_evolve(qs_qaoa* q, qs_state* psi, const double* gamma, const double* beta);
+/* *energy = <psi(gamma,beta)|C|psi(gamma,beta)>; psi is overwritten with the final state. */
+QS_API qs_status qs_qaoa_expectation(qs_qaoa* q, qs_state* psi, const double* gamma, const double* beta,
+                              double* energy);
+/* Energy and dE/dgamma[p], dE/dbeta[p] by the adjoint method (QuPack
+ * get_expectation_with_grad).  psi, lam: work states (contents on entry
+ * ignored; on return undefined).  Host outputs. */
+QS_API qs_status qs_qaoa_expectation_with_grad(qs_qaoa* q, qs_state* psi, qs_state* lam, const double* gamma,
+                                        const double* beta, double* energy, double* dgamma, double* dbeta);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSIM_H */

@@ -1,0 +1,106 @@
+// Opaque handle types behind the C ABI and the host helpers shared by api.cu
+// and qaoa.cu.
+#pragma once
+
+#include <vector>
+
+#include "plan.h"
+#include "qsim_internal.h"
+
+using namespace qs;
+
+
+struct qs_state {
+  int n = 0;   // qubits as created
+  int ne = 0;  // qubits of the stored array (n padded up to kRegBits)
+  qs_dtype dt = QS_C64;
+  void* ptr = nullptr;
+  bool owned = false;
+  size_t bytes = 0;
+  cudaStream_t st = nullptr;
+  double* scratch = nullptr;
+  size_t scratch_n = 0;
+  std::vector<double> host_out;
+};
+
+struct CircuitPlan {
+  bool valid = false;
+  qs_dtype dt = QS_C64;
+  int fuse = 1, m = 0, c = 0, ne = 0;
+  TilePlan fwd, rev;
+  SlotMap rev_slots;
+  std::vector<int> off_u, off_ud, off_a, gclass;
+  int n_coef = 0;
+  void* d_coef = nullptr;
+  int* d_row = nullptr;
+  int* d_sidx = nullptr;
+  double* d_w = nullptr;
+  int n_params = 0;
+  int grid1 = 1, grid2 = 1;
+  void release() {
+    fwd.free_device();
+    rev.free_device();
+    if (d_coef) cudaFree(d_coef);
+    if (d_row) cudaFree(d_row);
+    if (d_sidx) cudaFree(d_sidx);
+    if (d_w) cudaFree(d_w);
+    d_coef = nullptr;
+    d_row = d_sidx = nullptr;
+    d_w = nullptr;
+    fwd = TilePlan();
+    rev = TilePlan();
+    rev_slots = SlotMap();
+    valid = false;
+  }
+};
+
+struct qs_circuit {
+  int n = 0;
+  std::vector<HostGate> gates;
+  int n_params = 0;
+  qs_options opts{};
+  CircuitPlan plan;
+  std::vector<double> host_coef;  // staging of the per-call coefficient table
+};
+
+struct qs_ham {
+  int n = 0;
+  std::vector<uint64_t> x, z;
+  std::vector<double> c;
+  DevHamGroup* d_groups = nullptr;
+  DevHamTerm* d_terms = nullptr;
+  int n_groups = 0;
+};
+
+struct qs_qaoa {
+  int n = 0, ne = 0, p = 0, n_edges = 0;
+  double gs = 1.0;
+  qs_dtype dt = QS_C64;
+  int m = 0, c = 0;
+  std::vector<int> edges;
+  uint8_t* d_cut = nullptr;
+  int* d_edges = nullptr;
+  TilePlan gplan, eplan;
+  SlotMap gslots, eslots;
+  int n_fwd = 0;  // forward passes before the turnaround pass
+  void* d_coef = nullptr;
+  int n_coef = 0;
+  int *g_row = nullptr, *g_sidx = nullptr, *e_row = nullptr, *e_sidx = nullptr;
+  double *g_w = nullptr, *e_w = nullptr;
+  int grid1 = 1, grid2 = 1;
+  double bytes_per_eval = 0;
+  int rev_passes = 0;
+  std::vector<double> host_coef;
+};
+
+
+namespace qs {
+qs_status ensure_scratch(qs_state* s, size_t ndoubles);
+qs_status upload_table(const std::vector<double>& tab, qs_dtype dt, void* d_dst, cudaStream_t st,
+                       std::vector<double>& staging);
+qs_status build_csr(const SlotMap& sm, int n_out, int** d_row, int** d_sidx, double** d_w, cudaStream_t st);
+qs_status run_passes(const TilePlan& plan, int begin, int end, qs_dtype dt, void* psi, void* lam, const void* coef,
+                     const uint8_t* cut, double* partials, int n, int n_edges, int grid1, int grid2, cudaStream_t st);
+qs_status check_state(const qs_state* s);
+size_t amp_bytes(qs_dtype dt);
+}  // namespace qs

@@ -1,0 +1,574 @@
+// Per-gate kernels, state initialisation, Pauli-sum application and
+// expectation, deterministic reductions, MaxCut cut values and sampling.
+#include "qsim_internal.h"
+
+namespace qs {
+
+namespace {
+
+template <class T>
+struct V2;
+template <>
+struct V2<float> {
+  using V = float2;
+};
+template <>
+struct V2<double> {
+  using V = double2;
+};
+
+template <class V>
+__device__ __forceinline__ V mulc(V a, V b) {
+  V r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+
+constexpr int kThreads = 256;
+
+int blocks_for(uint64_t work, int per_block = kThreads) {
+  uint64_t b = (work + per_block - 1) / per_block;
+  if (b > (1u << 30)) b = 1u << 30;
+  return (int)(b ? b : 1);
+}
+
+// Insert a zero bit at position q (bits >= q shift up).
+__device__ __forceinline__ uint64_t insert0(uint64_t i, int q) {
+  const uint64_t lo = i & ((1ull << q) - 1);
+  return ((i >> q) << (q + 1)) | lo;
+}
+
+struct Mat4 {
+  double re[16], im[16];
+};
+
+// --------------------------------------------------------------- per-gate dense
+template <class T, int K>
+__global__ void gate_dense_kernel(typename V2<T>::V* psi, int n, int t0, int t1, uint64_t cmask, Mat4 M) {
+  using V = typename V2<T>::V;
+  const uint64_t groups = 1ull << (n - K);
+  const int lo = (K == 2 && t1 < t0) ? t1 : t0;
+  const int hi = (K == 2 && t1 < t0) ? t0 : t1;
+  constexpr int D = 1 << K;
+  V m[D * D];
+#pragma unroll
+  for (int i = 0; i < D * D; ++i) {
+    m[i].x = (T)M.re[i];
+    m[i].y = (T)M.im[i];
+  }
+  for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < groups;
+       g += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t base = insert0(g, lo);
+    if (K == 2) base = insert0(base, hi);
+    if ((base & cmask) != cmask) continue;
+    uint64_t idx[D];
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      uint64_t x = base;
+      if (b & 1) x |= 1ull << t0;
+      if (K == 2 && (b & 2)) x |= 1ull << t1;
+      idx[b] = x;
+    }
+    V in[D];
+#pragma unroll
+    for (int b = 0; b < D; ++b) in[b] = psi[idx[b]];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      V acc;
+      acc.x = 0;
+      acc.y = 0;
+#pragma unroll
+      for (int cidx = 0; cidx < D; ++cidx) {
+        V p = mulc(m[r * D + cidx], in[cidx]);
+        acc.x += p.x;
+        acc.y += p.y;
+      }
+      psi[idx[r]] = acc;
+    }
+  }
+}
+
+template <class T>
+__global__ void gate_diag_kernel(typename V2<T>::V* psi, int n, int nt, int t0, int t1, uint64_t cmask, Mat4 D) {
+  using V = typename V2<T>::V;
+  const uint64_t N = 1ull << n;
+  V d[4];
+  for (int i = 0; i < 4; ++i) {
+    d[i].x = (T)D.re[i];
+    d[i].y = (T)D.im[i];
+  }
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
+    if ((x & cmask) != cmask) continue;
+    int b = (int)((x >> t0) & 1);
+    if (nt == 2) b |= (int)((x >> t1) & 1) << 1;
+    psi[x] = mulc(d[b], psi[x]);
+  }
+}
+
+// --------------------------------------------------------------- init
+template <class T>
+__global__ void set_plus_kernel(typename V2<T>::V* psi, uint64_t N, T amp) {
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
+    typename V2<T>::V v;
+    v.x = amp;
+    v.y = 0;
+    psi[x] = v;
+  }
+}
+
+template <class T>
+__global__ void set_one_kernel(typename V2<T>::V* psi, uint64_t index) {
+  typename V2<T>::V v;
+  v.x = 1;
+  v.y = 0;
+  psi[index] = v;
+}
+
+// --------------------------------------------------------------- block reduction helpers
+__device__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+  }
+  __syncthreads();
+  return r;  // valid in thread 0
+}
+
+constexpr int kFlush = 16;  // FP32 partial sums are flushed to FP64 every kFlush elements
+
+// lam_y = sum_g psi_{y^m_g} * sum_{k in g} c'_k (-1)^{popcount((y^m_g) & z_k)};  E += Re(conj(psi_y) lam_y)
+template <class T>
+__global__ void ham_apply_kernel(const typename V2<T>::V* __restrict__ psi, typename V2<T>::V* __restrict__ lam, int n,
+                                 const DevHamGroup* __restrict__ groups, int n_groups,
+                                 const DevHamTerm* __restrict__ terms, double* partials) {
+  using V = typename V2<T>::V;
+  __shared__ double sh[32];
+  const uint64_t N = 1ull << n;
+  double acc_d = 0;
+  T acc = 0;
+  int cnt = 0;
+  for (uint64_t y = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; y < N; y += (uint64_t)gridDim.x * blockDim.x) {
+    T lr = 0, li = 0;
+    for (int g = 0; g < n_groups; ++g) {
+      const DevHamGroup G = groups[g];
+      const uint64_t x = y ^ G.xmask;
+      const V a = psi[x];
+      T fr = 0, fi = 0;
+      for (int k = G.begin; k < G.end; ++k) {
+        const DevHamTerm t = terms[k];
+        const T s = (__popcll(x & t.zmask) & 1) ? (T)-1 : (T)1;
+        fr += s * (T)t.re;
+        fi += s * (T)t.im;
+      }
+      lr += fr * a.x - fi * a.y;
+      li += fr * a.y + fi * a.x;
+    }
+    const V p = psi[y];
+    if (lam) {
+      V o;
+      o.x = lr;
+      o.y = li;
+      lam[y] = o;
+    }
+    acc += p.x * lr + p.y * li;
+    if (++cnt == kFlush) {
+      acc_d += (double)acc;
+      acc = 0;
+      cnt = 0;
+    }
+  }
+  acc_d += (double)acc;
+  const double s = block_sum(acc_d, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// <a|b> partials: [0][grid] real, [1][grid] imag
+template <class T>
+__global__ void inner_kernel(const typename V2<T>::V* __restrict__ a, const typename V2<T>::V* __restrict__ b, int n,
+                             double* partials) {
+  __shared__ double sh[32];
+  const uint64_t N = 1ull << n;
+  double re_d = 0, im_d = 0;
+  T re = 0, im = 0;
+  int cnt = 0;
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
+    const auto u = a[x], v = b[x];
+    re += u.x * v.x + u.y * v.y;
+    im += u.x * v.y - u.y * v.x;
+    if (++cnt == kFlush) {
+      re_d += re;
+      im_d += im;
+      re = im = 0;
+      cnt = 0;
+    }
+  }
+  re_d += re;
+  im_d += im;
+  const double r = block_sum(re_d, sh);
+  const double i = block_sum(im_d, sh);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = r;
+    partials[gridDim.x + blockIdx.x] = i;
+  }
+}
+
+template <class T>
+__global__ void norm2_kernel(const typename V2<T>::V* __restrict__ a, int n, double* partials) {
+  __shared__ double sh[32];
+  const uint64_t N = 1ull << n;
+  double s_d = 0;
+  T s = 0;
+  int cnt = 0;
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
+    const auto u = a[x];
+    s += u.x * u.x + u.y * u.y;
+    if (++cnt == kFlush) {
+      s_d += s;
+      s = 0;
+      cnt = 0;
+    }
+  }
+  s_d += s;
+  const double r = block_sum(s_d, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = r;
+}
+
+// One warp per slot, fixed order: lanes take strided partials, then a fixed tree.
+__global__ void reduce_slots_kernel(const double* partials, int n_slots, int nb, const double* scale, double* out) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n_slots) return;
+  double v = 0;
+  for (int b = lane; b < nb; b += 32) v += partials[(size_t)warp * nb + b];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) out[warp] = scale ? v * scale[warp] : v;
+}
+
+__global__ void param_gather_kernel(const double* gate_grad, const int* row_ptr, const int* gate_idx,
+                                    const double* gate_coef, int n_params, double* grad) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_params) return;
+  double s = 0;
+  for (int k = row_ptr[p]; k < row_ptr[p + 1]; ++k) s += gate_coef[k] * gate_grad[gate_idx[k]];
+  grad[p] = s;
+}
+
+// cut(x) = number of edges whose endpoints differ in x
+__global__ void cut_values_kernel(uint8_t* cut, int n, const int* __restrict__ edges, int n_edges) {
+  extern __shared__ int s_e[];
+  for (int i = threadIdx.x; i < 2 * n_edges; i += blockDim.x) s_e[i] = edges[i];
+  __syncthreads();
+  const uint64_t N = 1ull << n;
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
+    int c = 0;
+    for (int e = 0; e < n_edges; ++e) c += (int)(((x >> s_e[2 * e]) ^ (x >> s_e[2 * e + 1])) & 1ull);
+    cut[x] = (uint8_t)c;
+  }
+}
+
+// --------------------------------------------------------------- sampling
+constexpr int kChunkBits = 12;  // probabilities are summed in chunks of 4096 amplitudes
+
+template <class T>
+__device__ __forceinline__ double prob(const typename V2<T>::V& a) {
+  // products of the stored components are formed in FP64
+  return (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+}
+
+// chunk sums, one warp per chunk, lanes own contiguous segments (fixed order)
+template <class T>
+__global__ void chunk_sum_kernel(const typename V2<T>::V* __restrict__ psi, int n, double* chunk) {
+  const int cb = n < kChunkBits ? n : kChunkBits;
+  const uint64_t n_chunks = 1ull << (n - cb);
+  const uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n_chunks) return;
+  const uint64_t csize = 1ull << cb;
+  const uint64_t seg = (csize + 31) / 32;
+  const uint64_t b = w * csize + lane * seg;
+  double s = 0;
+  for (uint64_t i = 0; i < seg && lane * seg + i < csize; ++i) s += prob<T>(psi[b + i]);
+  // exclusive scan over lanes (Hillis-Steele, fixed order) -> total in lane 31
+  for (int o = 1; o < 32; o <<= 1) {
+    const double t = __shfl_up_sync(0xffffffffu, s, o);
+    if (lane >= o) s += t;
+  }
+  if (lane == 31) chunk[w] = s;
+}
+
+// exclusive prefix over chunk sums in place, single block; chunk[n_chunks] = total
+__global__ void chunk_scan_kernel(double* chunk, uint64_t n_chunks) {
+  __shared__ double sh[1024];
+  const int t = threadIdx.x, T_ = blockDim.x;
+  const uint64_t per = (n_chunks + T_ - 1) / T_;
+  const uint64_t b = t * per;
+  double s = 0;
+  for (uint64_t i = 0; i < per && b + i < n_chunks; ++i) s += chunk[b + i];
+  sh[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    double run = 0;
+    for (int i = 0; i < T_; ++i) {
+      const double v = sh[i];
+      sh[i] = run;
+      run += v;
+    }
+    chunk[n_chunks] = run;
+  }
+  __syncthreads();
+  double run = sh[t];
+  for (uint64_t i = 0; i < per && b + i < n_chunks; ++i) {
+    const double v = chunk[b + i];
+    chunk[b + i] = run;
+    run += v;
+  }
+}
+
+__device__ __forceinline__ uint64_t splitmix64_out(uint64_t state) {
+  uint64_t z = state + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// one warp per shot
+template <class T>
+__global__ void sample_kernel(const typename V2<T>::V* __restrict__ psi, int n, const double* __restrict__ chunk,
+                              uint64_t shots, uint64_t seed, uint64_t* out) {
+  const uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= shots) return;
+  const int cb = n < kChunkBits ? n : kChunkBits;
+  const uint64_t n_chunks = 1ull << (n - cb);
+  const double total = chunk[n_chunks];
+  const uint64_t z = splitmix64_out(seed + w * 0x9E3779B97F4A7C15ull);
+  const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  const double target = u * total;
+  // last chunk k with prefix[k] <= target
+  uint64_t lo = 0, hi = n_chunks - 1;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi + 1) >> 1;
+    if (chunk[mid] <= target)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const uint64_t csize = 1ull << cb;
+  const uint64_t seg = (csize + 31) / 32;
+  const uint64_t base = lo * csize;
+  double s = 0;
+  for (uint64_t i = 0; i < seg && lane * seg + i < csize; ++i) s += prob<T>(psi[base + lane * seg + i]);
+  double incl = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    const double t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const double start = chunk[lo] + (incl - s);
+  const double end = chunk[lo] + incl;
+  // first lane whose running sum passes the target
+  const unsigned passed = __ballot_sync(0xffffffffu, end > target);
+  uint64_t result = base + csize - 1;
+  if (passed == 0) {
+    // rounding left the target at or beyond this chunk's end: the last amplitude
+    // with non-zero probability in the chunk
+    if (lane == 0) {
+      for (uint64_t i = csize; i-- > 0;) {
+        if (prob<T>(psi[base + i]) > 0) {
+          result = base + i;
+          break;
+        }
+      }
+    }
+    result = __shfl_sync(0xffffffffu, result, 0);
+  } else {
+    const int L = __ffs(passed) - 1;
+    if (lane == L) {
+      double run = start;
+      const uint64_t b0 = base + lane * seg;
+      const uint64_t stop = base + (lane * seg + seg < csize ? lane * seg + seg : csize);
+      uint64_t x = b0;
+      for (; x < stop; ++x) {
+        run += prob<T>(psi[x]);
+        if (run > target) break;
+      }
+      result = x < stop ? x : stop - 1;
+    }
+    result = __shfl_sync(0xffffffffu, result, L);
+  }
+  if (lane == 0) out[w] = result;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------ launchers
+
+qs_status launch_gate_dense(qs_dtype dt, void* psi, int n, int nt, const int* t, uint64_t cmask, const double* mat,
+                            cudaStream_t st) {
+  Mat4 M;
+  const int D = 1 << nt;
+  for (int i = 0; i < D * D; ++i) {
+    M.re[i] = mat[2 * i];
+    M.im[i] = mat[2 * i + 1];
+  }
+  const uint64_t groups = 1ull << (n - nt);
+  const int grid = blocks_for(groups);
+  const int g = grid > 65535 * 16 ? 65535 * 16 : grid;
+  if (dt == QS_C64) {
+    if (nt == 1)
+      gate_dense_kernel<float, 1><<<g, kThreads, 0, st>>>((float2*)psi, n, t[0], t[0], cmask, M);
+    else
+      gate_dense_kernel<float, 2><<<g, kThreads, 0, st>>>((float2*)psi, n, t[0], t[1], cmask, M);
+  } else {
+    if (nt == 1)
+      gate_dense_kernel<double, 1><<<g, kThreads, 0, st>>>((double2*)psi, n, t[0], t[0], cmask, M);
+    else
+      gate_dense_kernel<double, 2><<<g, kThreads, 0, st>>>((double2*)psi, n, t[0], t[1], cmask, M);
+  }
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_gate_diag(qs_dtype dt, void* psi, int n, int nt, const int* t, uint64_t cmask, const double* diag,
+                           cudaStream_t st) {
+  Mat4 D;
+  for (int i = 0; i < (1 << nt); ++i) {
+    D.re[i] = diag[2 * i];
+    D.im[i] = diag[2 * i + 1];
+  }
+  const int grid = blocks_for(1ull << n);
+  const int g = grid > 65535 * 16 ? 65535 * 16 : grid;
+  if (dt == QS_C64)
+    gate_diag_kernel<float><<<g, kThreads, 0, st>>>((float2*)psi, n, nt, t[0], nt == 2 ? t[1] : 0, cmask, D);
+  else
+    gate_diag_kernel<double><<<g, kThreads, 0, st>>>((double2*)psi, n, nt, t[0], nt == 2 ? t[1] : 0, cmask, D);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_set_basis(qs_dtype dt, void* psi, int n, uint64_t index, cudaStream_t st) {
+  const size_t bytes = (size_t)(dt == QS_C64 ? 8 : 16) << n;
+  QS_CUDA(cudaMemsetAsync(psi, 0, bytes, st));
+  if (dt == QS_C64)
+    set_one_kernel<float><<<1, 1, 0, st>>>((float2*)psi, index);
+  else
+    set_one_kernel<double><<<1, 1, 0, st>>>((double2*)psi, index);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_set_plus(qs_dtype dt, void* psi, int n, cudaStream_t st) {
+  const int grid = blocks_for(1ull << n);
+  const int g = grid > 65535 * 16 ? 65535 * 16 : grid;
+  const double amp = std::ldexp(1.0, -n / 2) * ((n & 1) ? 0.70710678118654752440 : 1.0);
+  if (dt == QS_C64)
+    set_plus_kernel<float><<<g, kThreads, 0, st>>>((float2*)psi, 1ull << n, (float)amp);
+  else
+    set_plus_kernel<double><<<g, kThreads, 0, st>>>((double2*)psi, 1ull << n, amp);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+int ham_grid_size(int n) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 1;
+  const uint64_t need = ((1ull << n) + kThreads - 1) / kThreads;
+  const uint64_t g = (uint64_t)sms * 8;
+  return (int)(need < g ? need : g);
+}
+
+qs_status launch_ham_apply(qs_dtype dt, const void* psi, void* lam, int n, const DevHamGroup* groups, int n_groups,
+                           const DevHamTerm* terms, double* partials, int grid, cudaStream_t st) {
+  if (dt == QS_C64)
+    ham_apply_kernel<float><<<grid, kThreads, 0, st>>>((const float2*)psi, (float2*)lam, n, groups, n_groups, terms,
+                                                       partials);
+  else
+    ham_apply_kernel<double><<<grid, kThreads, 0, st>>>((const double2*)psi, (double2*)lam, n, groups, n_groups,
+                                                        terms, partials);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_inner(qs_dtype dt, const void* a, const void* b, int n, double* partials, int grid,
+                       cudaStream_t st) {
+  if (dt == QS_C64)
+    inner_kernel<float><<<grid, kThreads, 0, st>>>((const float2*)a, (const float2*)b, n, partials);
+  else
+    inner_kernel<double><<<grid, kThreads, 0, st>>>((const double2*)a, (const double2*)b, n, partials);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_norm2(qs_dtype dt, const void* a, int n, double* partials, int grid, cudaStream_t st) {
+  if (dt == QS_C64)
+    norm2_kernel<float><<<grid, kThreads, 0, st>>>((const float2*)a, n, partials);
+  else
+    norm2_kernel<double><<<grid, kThreads, 0, st>>>((const double2*)a, n, partials);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_reduce_slots(const double* partials, int n_slots, int nb, const double* scale, double* out,
+                              cudaStream_t st) {
+  if (n_slots <= 0) return QS_OK;
+  const int threads = 256;
+  const int blocks = (n_slots * 32 + threads - 1) / threads;
+  reduce_slots_kernel<<<blocks, threads, 0, st>>>(partials, n_slots, nb, scale, out);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_param_gather(const double* gate_grad, const int* row_ptr, const int* gate_idx,
+                              const double* gate_coef, int n_params, double* grad, cudaStream_t st) {
+  if (n_params <= 0) return QS_OK;
+  param_gather_kernel<<<(n_params + 127) / 128, 128, 0, st>>>(gate_grad, row_ptr, gate_idx, gate_coef, n_params,
+                                                              grad);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_cut_values(uint8_t* cut, int n, const int* d_edges, int n_edges, cudaStream_t st) {
+  const int grid = blocks_for(1ull << n);
+  const int g = grid > 65535 * 8 ? 65535 * 8 : grid;
+  cut_values_kernel<<<g, kThreads, 2 * n_edges * sizeof(int), st>>>(cut, n, d_edges, n_edges);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+size_t sample_scratch_doubles(int n) {
+  const int cb = n < kChunkBits ? n : kChunkBits;
+  return (1ull << (n - cb)) + 1;
+}
+
+qs_status launch_sample(qs_dtype dt, const void* psi, int n, uint64_t shots, uint64_t seed, double* scratch,
+                        uint64_t* d_out, cudaStream_t st) {
+  const int cb = n < kChunkBits ? n : kChunkBits;
+  const uint64_t n_chunks = 1ull << (n - cb);
+  const int threads = 256;
+  const uint64_t cblocks = (n_chunks * 32 + threads - 1) / threads;
+  if (dt == QS_C64)
+    chunk_sum_kernel<float><<<(unsigned)cblocks, threads, 0, st>>>((const float2*)psi, n, scratch);
+  else
+    chunk_sum_kernel<double><<<(unsigned)cblocks, threads, 0, st>>>((const double2*)psi, n, scratch);
+  QS_CUDA(cudaGetLastError());
+  chunk_scan_kernel<<<1, 1024, 0, st>>>(scratch, n_chunks);
+  QS_CUDA(cudaGetLastError());
+  if (shots) {
+    const uint64_t sblocks = (shots * 32 + threads - 1) / threads;
+    if (dt == QS_C64)
+      sample_kernel<float><<<(unsigned)sblocks, threads, 0, st>>>((const float2*)psi, n, scratch, shots, seed, d_out);
+    else
+      sample_kernel<double><<<(unsigned)sblocks, threads, 0, st>>>((const double2*)psi, n, scratch, shots, seed,
+                                                                   d_out);
+    QS_CUDA(cudaGetLastError());
+  }
+  return QS_OK;
+}
+
+}  // namespace qs

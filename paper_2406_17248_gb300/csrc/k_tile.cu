@@ -1,0 +1,624 @@
+// Fused shared-memory tile passes.
+//
+// One pass streams the state once through shared memory: the CTA loads a tile
+// of 2^m amplitudes whose index bits are a chosen set S of qubits (the low c
+// qubits, contiguous in HBM, plus m - c gathered higher qubits), applies a run
+// of gates whose non-diagonal targets lie in S, and stores the tile back.
+// Inside the tile, work proceeds in phases: each thread holds 2^kRegBits
+// amplitudes in registers, a sub-cube spanned by the phase's register bits R,
+// applies every op of the phase to them, and writes them back.  Controls and
+// diagonal gates may sit on any qubit: their bits are read from the local index
+// or from the tile offset.  The reverse (adjoint) passes carry psi and lam
+// together and accumulate <lam|A|psi> partials per gate (the adjoint gradient
+// of §4.1 / §7.2), reduced per warp in registers and per CTA in FP64.
+#include "qsim_internal.h"
+
+namespace qs {
+
+template <class T>
+struct VecT;
+template <>
+struct VecT<float> {
+  using V = float2;
+  using V4 = float4;
+};
+template <>
+struct VecT<double> {
+  using V = double2;
+  using V4 = double2;  // one amplitude per 16-byte chunk
+};
+
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <class V>
+__device__ __forceinline__ V cmul(V a, V b) {
+  V r;
+  r.x = fmaT(a.x, b.x, -a.y * b.y);
+  r.y = fmaT(a.x, b.y, a.y * b.x);
+  return r;
+}
+template <class V>
+__device__ __forceinline__ V cfma(V a, V b, V acc) {  // acc + a * b
+  acc.x = fmaT(a.x, b.x, acc.x);
+  acc.x = fmaT(-a.y, b.y, acc.x);
+  acc.y = fmaT(a.x, b.y, acc.y);
+  acc.y = fmaT(a.y, b.x, acc.y);
+  return acc;
+}
+// Re(conj(a) * b)
+template <class V>
+__device__ __forceinline__ decltype(V::x) re_conj_mul(V a, V b) {
+  return fmaT(a.x, b.x, a.y * b.y);
+}
+// Im(conj(a) * b)
+template <class V>
+__device__ __forceinline__ decltype(V::x) im_conj_mul(V a, V b) {
+  return fmaT(a.x, b.y, -a.y * b.x);
+}
+
+// Bank-conflict swizzle of a local index: XOR the bank bits with a fold of the
+// higher bits (a bijection that keeps pairs (2k, 2k+1) within one 16-byte chunk
+// for complex64).
+template <class T>
+__device__ __forceinline__ uint32_t swz(uint32_t l);
+template <>
+__device__ __forceinline__ uint32_t swz<float>(uint32_t l) {
+  uint32_t v = l >> 4;
+  return l ^ ((v ^ (v >> 4) ^ (v >> 8)) & 15u);
+}
+template <>
+__device__ __forceinline__ uint32_t swz<double>(uint32_t l) {
+  uint32_t v = l >> 3;
+  return l ^ ((v ^ (v >> 3) ^ (v >> 6) ^ (v >> 9)) & 7u);
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+constexpr int RN = 1 << kRegBits;
+
+struct TileKArgs {
+  void* psi;
+  void* lam;
+  const DevPass* pass;
+  const DevPhase* phases;
+  const DevOp* ops;
+  const void* coef;
+  const uint8_t* cut;
+  double* partials;
+  int n;
+  int n_edges;
+  int grid_stride;  // stride of the partials array (the plan's grid)
+};
+
+template <int J>
+__device__ __forceinline__ uint32_t off_of(const uint32_t (&rm)[kRegBits]) {
+  uint32_t o = 0;
+#pragma unroll
+  for (int i = 0; i < kRegBits; ++i)
+    if (J & (1 << i)) o |= rm[i];
+  return o;
+}
+
+template <class V, int RB>
+__device__ __forceinline__ void op_dense1(V (&a)[RN], const V* M, uint32_t jc, bool ok) {
+  const V m00 = M[0], m01 = M[1], m10 = M[2], m11 = M[3];
+#pragma unroll
+  for (int j = 0; j < RN; ++j) {
+    if (j & (1 << RB)) continue;
+    const int j1 = j | (1 << RB);
+    if (ok && ((uint32_t)j & jc) == jc) {
+      V x0 = a[j], x1 = a[j1];
+      a[j] = cfma(m01, x1, cmul(m00, x0));
+      a[j1] = cfma(m11, x1, cmul(m10, x0));
+    }
+  }
+}
+
+template <class V, int RB>
+__device__ __forceinline__ void op_rx(V (&a)[RN], V cs, uint32_t jc, bool ok) {
+  // [[c, -is], [-is, c]]: out0 = c x0 - i s x1, out1 = c x1 - i s x0
+  const auto c = cs.x, s = cs.y;
+#pragma unroll
+  for (int j = 0; j < RN; ++j) {
+    if (j & (1 << RB)) continue;
+    const int j1 = j | (1 << RB);
+    if (ok && ((uint32_t)j & jc) == jc) {
+      V x0 = a[j], x1 = a[j1], y0, y1;
+      y0.x = fmaT(c, x0.x, s * x1.y);
+      y0.y = fmaT(c, x0.y, -s * x1.x);
+      y1.x = fmaT(c, x1.x, s * x0.y);
+      y1.y = fmaT(c, x1.y, -s * x0.x);
+      a[j] = y0;
+      a[j1] = y1;
+    }
+  }
+}
+
+template <class V, int RB0, int RB1>
+__device__ __forceinline__ void op_dense2(V (&a)[RN], const V* M, uint32_t jc, bool ok) {
+#pragma unroll
+  for (int j = 0; j < RN; ++j) {
+    if (j & ((1 << RB0) | (1 << RB1))) continue;
+    if (!(ok && ((uint32_t)j & jc) == jc)) continue;
+    const int idx[4] = {j, j | (1 << RB0), j | (1 << RB1), j | (1 << RB0) | (1 << RB1)};
+    V x[4] = {a[idx[0]], a[idx[1]], a[idx[2]], a[idx[3]]};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      V y = cmul(M[4 * r], x[0]);
+      y = cfma(M[4 * r + 1], x[1], y);
+      y = cfma(M[4 * r + 2], x[2], y);
+      y = cfma(M[4 * r + 3], x[3], y);
+      a[idx[r]] = y;
+    }
+  }
+}
+
+template <class V, int RB>
+__device__ __forceinline__ auto grad_dense1(const V (&a)[RN], const V (&b)[RN], const V* A, uint32_t jc,
+                                            bool ok) -> decltype(V::x) {
+  decltype(V::x) acc = 0;
+  const V a00 = A[0], a01 = A[1], a10 = A[2], a11 = A[3];
+#pragma unroll
+  for (int j = 0; j < RN; ++j) {
+    if (j & (1 << RB)) continue;
+    const int j1 = j | (1 << RB);
+    if (ok && ((uint32_t)j & jc) == jc) {
+      V y0 = cfma(a01, a[j1], cmul(a00, a[j]));
+      V y1 = cfma(a11, a[j1], cmul(a10, a[j]));
+      acc += re_conj_mul(b[j], y0) + re_conj_mul(b[j1], y1);
+    }
+  }
+  return 2 * acc;
+}
+
+template <class V, int RB0, int RB1>
+__device__ __forceinline__ auto grad_dense2(const V (&a)[RN], const V (&b)[RN], const V* M, uint32_t jc,
+                                            bool ok) -> decltype(V::x) {
+  decltype(V::x) acc = 0;
+#pragma unroll
+  for (int j = 0; j < RN; ++j) {
+    if (j & ((1 << RB0) | (1 << RB1))) continue;
+    if (!(ok && ((uint32_t)j & jc) == jc)) continue;
+    const int idx[4] = {j, j | (1 << RB0), j | (1 << RB1), j | (1 << RB0) | (1 << RB1)};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      V y = cmul(M[4 * r], a[idx[0]]);
+      y = cfma(M[4 * r + 1], a[idx[1]], y);
+      y = cfma(M[4 * r + 2], a[idx[2]], y);
+      y = cfma(M[4 * r + 3], a[idx[3]], y);
+      acc += re_conj_mul(b[idx[r]], y);
+    }
+  }
+  return 2 * acc;
+}
+
+template <class V, int RB>
+__device__ __forceinline__ auto grad_x(const V (&a)[RN], const V (&b)[RN], uint32_t jc, bool ok)
+    -> decltype(V::x) {
+  decltype(V::x) acc = 0;
+#pragma unroll
+  for (int j = 0; j < RN; ++j) {
+    if (j & (1 << RB)) continue;
+    const int j1 = j | (1 << RB);
+    if (ok && ((uint32_t)j & jc) == jc) acc += im_conj_mul(b[j], a[j1]) + im_conj_mul(b[j1], a[j]);
+  }
+  return acc;
+}
+
+#define QS_RB_SWITCH(rb, CALL) \
+  switch (rb) {                \
+    case 0: CALL(0); break;    \
+    case 1: CALL(1); break;    \
+    case 2: CALL(2); break;    \
+    default: CALL(3); break;   \
+  }
+
+#define QS_RB2_SWITCH(r0, r1, CALL)      \
+  switch ((r0) * 4 + (r1)) {             \
+    case 1: CALL(0, 1); break;           \
+    case 2: CALL(0, 2); break;           \
+    case 3: CALL(0, 3); break;           \
+    case 4: CALL(1, 0); break;           \
+    case 6: CALL(1, 2); break;           \
+    case 7: CALL(1, 3); break;           \
+    case 8: CALL(2, 0); break;           \
+    case 9: CALL(2, 1); break;           \
+    case 11: CALL(2, 3); break;          \
+    case 12: CALL(3, 0); break;          \
+    case 13: CALL(3, 1); break;          \
+    default: CALL(3, 2); break;          \
+  }
+
+template <class T, int NS>
+__global__ void __launch_bounds__(kTileThreads) tile_pass_kernel(TileKArgs args) {
+  using V = typename VecT<T>::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+
+  const DevPass& P = *args.pass;
+  const int m = P.m, c = P.c;
+  const uint32_t flags = P.flags;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const uint32_t tile_n = 1u << m;
+
+  V* s_psi = reinterpret_cast<V*>(smem_raw);
+  V* s_lam = s_psi + (NS == 2 ? tile_n : 0);
+  uint8_t* s_cut = reinterpret_cast<uint8_t*>(s_psi + NS * tile_n);
+  double* s_acc = reinterpret_cast<double*>(s_cut + ((flags & PF_NEED_CUT) ? tile_n : 0));
+  uint64_t* s_hi = reinterpret_cast<uint64_t*>(s_acc + P.n_slots * kTileWarps);  // hiA[64], hiB[64]
+
+  for (int i = tid; i < 64; i += blockDim.x) {
+    s_hi[i] = P.hiA[i];
+    s_hi[64 + i] = P.hiB[i];
+  }
+  for (int i = tid; i < P.n_slots * kTileWarps; i += blockDim.x) s_acc[i] = 0.0;
+  __syncthreads();
+
+  const V* coef = reinterpret_cast<const V*>(args.coef);
+  V* g_psi = reinterpret_cast<V*>(args.psi);
+  V* g_lam = reinterpret_cast<V*>(args.lam);
+  const uint32_t lowmask = (1u << c) - 1u;
+  const uint64_t n_tiles = 1ull << (args.n - m);
+  const T plus_amp = (T)exp2(-0.5 * (double)args.n);
+  const int n_edges = args.n_edges;
+
+  for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    uint64_t toff = 0;
+    for (int i = 0; i < P.ncomp; ++i) toff |= ((tile >> i) & 1ull) << P.comp[i];
+
+    // ---------------------------------------------------------------- load
+    if (sizeof(T) == 4) {
+      const uint32_t nch = tile_n >> 1;
+      for (uint32_t ch = tid; ch < nch; ch += blockDim.x) {
+        const uint32_t l = ch << 1;
+        const uint64_t g = toff | (l & lowmask) | s_hi[(l >> c) & 63] | s_hi[64 + (l >> (c + 6))];
+        uint32_t p = swz<T>(l);
+        const bool sw = p & 1;
+        p &= ~1u;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          float4 v;
+          if (s == 0 && (flags & (PF_GEN_PLUS | PF_GEN_ZERO))) {
+            float a0 = (flags & PF_GEN_PLUS) ? (float)plus_amp : (g == 0 ? 1.f : 0.f);
+            float a1 = (flags & PF_GEN_PLUS) ? (float)plus_amp : 0.f;
+            v = make_float4(a0, 0.f, a1, 0.f);
+          } else if ((s == 0 && (flags & PF_LOAD_PSI)) || (s == 1 && (flags & PF_LOAD_LAM))) {
+            const float4* src = reinterpret_cast<const float4*>((s == 0 ? g_psi : g_lam) + g);
+            v = __ldcs(src);
+          } else {
+            continue;
+          }
+          if (sw) v = make_float4(v.z, v.w, v.x, v.y);
+          *reinterpret_cast<float4*>((s == 0 ? s_psi : s_lam) + p) = v;
+        }
+        if (flags & PF_NEED_CUT) {
+          s_cut[l] = args.cut[g];
+          s_cut[l + 1] = args.cut[g + 1];
+        }
+      }
+    } else {
+      for (uint32_t l = tid; l < tile_n; l += blockDim.x) {
+        const uint64_t g = toff | (l & lowmask) | s_hi[(l >> c) & 63] | s_hi[64 + (l >> (c + 6))];
+        const uint32_t p = swz<T>(l);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          V v;
+          if (s == 0 && (flags & (PF_GEN_PLUS | PF_GEN_ZERO))) {
+            v.x = (flags & PF_GEN_PLUS) ? plus_amp : (g == 0 ? (T)1 : (T)0);
+            v.y = 0;
+          } else if ((s == 0 && (flags & PF_LOAD_PSI)) || (s == 1 && (flags & PF_LOAD_LAM))) {
+            v = __ldcs((s == 0 ? g_psi : g_lam) + g);
+          } else {
+            continue;
+          }
+          (s == 0 ? s_psi : s_lam)[p] = v;
+        }
+        if (flags & PF_NEED_CUT) s_cut[l] = args.cut[g];
+      }
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------------------- phases
+    for (int ph = 0; ph < P.n_phases; ++ph) {
+      const DevPhase& PH = args.phases[P.phase_begin + ph];
+      uint32_t rm[kRegBits];
+#pragma unroll
+      for (int i = 0; i < kRegBits; ++i) rm[i] = 1u << PH.R[i];
+      const uint32_t nsub = tile_n >> kRegBits;
+      const uint32_t iters = (nsub + blockDim.x - 1) / blockDim.x;
+      for (uint32_t it = 0; it < iters; ++it) {
+        const uint32_t u = tid + it * blockDim.x;
+        const bool active = u < nsub;
+        uint32_t l0 = 0;
+        for (int i = 0; i < PH.nq; ++i) l0 |= ((u >> i) & 1u) << PH.Q[i];
+        V a[RN], b[RN];
+        uint32_t lj[RN];
+#pragma unroll
+        for (int j = 0; j < RN; ++j) {
+          lj[j] = 0;
+          if (j & 1) lj[j] |= rm[0];
+          if (j & 2) lj[j] |= rm[1];
+          if (j & 4) lj[j] |= rm[2];
+          if (j & 8) lj[j] |= rm[3];
+          lj[j] |= l0;
+        }
+        if (active) {
+#pragma unroll
+          for (int j = 0; j < RN; ++j) {
+            const uint32_t p = swz<T>(lj[j]);
+            a[j] = s_psi[p];
+            if (NS == 2) b[j] = s_lam[p];
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < RN; ++j) {
+            a[j].x = a[j].y = 0;
+            b[j].x = b[j].y = 0;
+          }
+        }
+        for (int o = PH.op_begin; o < PH.op_end; ++o) {
+          const DevOp op = args.ops[o];
+          const bool ok = active && ((l0 & op.lc) == op.lc) && ((toff & op.gc) == op.gc);
+          const uint32_t jc = op.jc;
+          const V* M = coef + op.coef;
+          T contrib = 0;
+          bool has_contrib = false;
+          switch (op.type) {
+            case OP_DENSE1: {
+#define CALL(R)                              \
+  op_dense1<V, R>(a, M, jc, ok);             \
+  if (NS == 2 && (op.flags & OPF_LAM)) op_dense1<V, R>(b, M, jc, ok);
+              QS_RB_SWITCH(op.rb0, CALL)
+#undef CALL
+              break;
+            }
+            case OP_RX: {
+              const V cs = M[0];
+#define CALL(R)                            \
+  op_rx<V, R>(a, cs, jc, ok);              \
+  if (NS == 2 && (op.flags & OPF_LAM)) op_rx<V, R>(b, cs, jc, ok);
+              QS_RB_SWITCH(op.rb0, CALL)
+#undef CALL
+              break;
+            }
+            case OP_DENSE2: {
+#define CALL(R0, R1)                             \
+  op_dense2<V, R0, R1>(a, M, jc, ok);            \
+  if (NS == 2 && (op.flags & OPF_LAM)) op_dense2<V, R0, R1>(b, M, jc, ok);
+              QS_RB2_SWITCH(op.rb0, op.rb1, CALL)
+#undef CALL
+              break;
+            }
+            case OP_DIAG:
+            case OP_GRADDIAG: {
+              const bool g0 = op.dglb[0] >= 0 && ((toff >> op.dglb[0]) & 1ull);
+              const bool g1 = op.dglb[1] >= 0 && ((toff >> op.dglb[1]) & 1ull);
+#pragma unroll
+              for (int j = 0; j < RN; ++j) {
+                if (!(ok && ((uint32_t)j & jc) == jc)) continue;
+                const uint32_t b0 = op.dloc[0] >= 0 ? (lj[j] >> op.dloc[0]) & 1u : (uint32_t)g0;
+                const uint32_t b1 = op.dloc[1] >= 0 ? (lj[j] >> op.dloc[1]) & 1u : (uint32_t)g1;
+                const V d = M[b0 + 2 * b1];
+                if (op.type == OP_DIAG) {
+                  a[j] = cmul(d, a[j]);
+                  if (NS == 2 && (op.flags & OPF_LAM)) b[j] = cmul(d, b[j]);
+                } else {
+                  contrib += 2 * re_conj_mul(b[j], cmul(d, a[j]));
+                }
+              }
+              has_contrib = op.type == OP_GRADDIAG;
+              break;
+            }
+            case OP_GRAD1: {
+#define CALL(R) contrib = grad_dense1<V, R>(a, b, M, jc, ok);
+              QS_RB_SWITCH(op.rb0, CALL)
+#undef CALL
+              has_contrib = true;
+              break;
+            }
+            case OP_GRAD2: {
+#define CALL(R0, R1) contrib = grad_dense2<V, R0, R1>(a, b, M, jc, ok);
+              QS_RB2_SWITCH(op.rb0, op.rb1, CALL)
+#undef CALL
+              has_contrib = true;
+              break;
+            }
+            case OP_GRADX: {
+#define CALL(R) contrib = grad_x<V, R>(a, b, jc, ok);
+              QS_RB_SWITCH(op.rb0, CALL)
+#undef CALL
+              has_contrib = true;
+              break;
+            }
+            case OP_COST: {
+              if (active) {
+#pragma unroll
+                for (int j = 0; j < RN; ++j) {
+                  const V d = M[s_cut[lj[j]]];
+                  a[j] = cmul(d, a[j]);
+                  if (NS == 2 && (op.flags & OPF_LAM)) b[j] = cmul(d, b[j]);
+                }
+              }
+              break;
+            }
+            case OP_GRADCOST: {
+              if (active) {
+#pragma unroll
+                for (int j = 0; j < RN; ++j) {
+                  const T C = (T)(n_edges - 2 * (int)s_cut[lj[j]]);
+                  contrib += C * im_conj_mul(b[j], a[j]);
+                }
+              }
+              has_contrib = true;
+              break;
+            }
+            case OP_ENERGY: {
+              if (active) {
+#pragma unroll
+                for (int j = 0; j < RN; ++j) {
+                  const T C = (T)(n_edges - 2 * (int)s_cut[lj[j]]);
+                  contrib += C * fmaT(a[j].x, a[j].x, a[j].y * a[j].y);
+                  b[j].x = C * a[j].x;
+                  b[j].y = C * a[j].y;
+                }
+              }
+              has_contrib = true;
+              break;
+            }
+            default:
+              break;
+          }
+          if (has_contrib) {  // uniform across the CTA (depends on op only)
+            const T w = warp_sum(contrib);
+            if (lane == 0) s_acc[op.slot * kTileWarps + warp] += (double)w;
+          }
+        }
+        if (active) {
+#pragma unroll
+          for (int j = 0; j < RN; ++j) {
+            const uint32_t p = swz<T>(lj[j]);
+            s_psi[p] = a[j];
+            if (NS == 2) s_lam[p] = b[j];
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---------------------------------------------------------------- store
+    if (flags & (PF_STORE_PSI | PF_STORE_LAM)) {
+      if (sizeof(T) == 4) {
+        const uint32_t nch = tile_n >> 1;
+        for (uint32_t ch = tid; ch < nch; ch += blockDim.x) {
+          const uint32_t l = ch << 1;
+          const uint64_t g = toff | (l & lowmask) | s_hi[(l >> c) & 63] | s_hi[64 + (l >> (c + 6))];
+          uint32_t p = swz<T>(l);
+          const bool sw = p & 1;
+          p &= ~1u;
+#pragma unroll
+          for (int s = 0; s < NS; ++s) {
+            if (!((s == 0 && (flags & PF_STORE_PSI)) || (s == 1 && (flags & PF_STORE_LAM)))) continue;
+            float4 v = *reinterpret_cast<const float4*>((s == 0 ? s_psi : s_lam) + p);
+            if (sw) v = make_float4(v.z, v.w, v.x, v.y);
+            __stcs(reinterpret_cast<float4*>((s == 0 ? g_psi : g_lam) + g), v);
+          }
+        }
+      } else {
+        for (uint32_t l = tid; l < tile_n; l += blockDim.x) {
+          const uint64_t g = toff | (l & lowmask) | s_hi[(l >> c) & 63] | s_hi[64 + (l >> (c + 6))];
+          const uint32_t p = swz<T>(l);
+#pragma unroll
+          for (int s = 0; s < NS; ++s) {
+            if (!((s == 0 && (flags & PF_STORE_PSI)) || (s == 1 && (flags & PF_STORE_LAM)))) continue;
+            __stcs((s == 0 ? g_psi : g_lam) + g, (s == 0 ? s_psi : s_lam)[p]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ------------------------------------------------------------------ partials
+  for (int s = tid; s < P.n_slots; s += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < kTileWarps; ++w) v += s_acc[s * kTileWarps + w];
+    args.partials[(size_t)(P.slot_base + s) * args.grid_stride + blockIdx.x] = v;
+  }
+}
+
+size_t tile_smem_bytes(qs_dtype dt, int m, int ns) {
+  const size_t amp = dt == QS_C64 ? 8 : 16;
+  const size_t tile = (size_t)1 << m;
+  return ns * tile * amp + tile /* cut */ + (size_t)kMaxSlotsPerPass * kTileWarps * 8 + 128 * 8;
+}
+
+template <class T, int NS>
+static int occupancy_for(size_t smem) {
+  static int cached[2] = {0, 0};
+  static size_t cached_smem[2] = {0, 0};
+  const int key = 0;
+  if (cached[key] && cached_smem[key] == smem) return cached[key];
+  int blocks = 0;
+  if (cudaFuncSetAttribute(tile_pass_kernel<T, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, tile_pass_kernel<T, NS>, kTileThreads, smem) !=
+          cudaSuccess ||
+      blocks < 1) {
+    (void)cudaGetLastError();  // the probe's error must not surface at a later launch check
+    blocks = 1;
+  }
+  cached[key] = blocks;
+  cached_smem[key] = smem;
+  return blocks;
+}
+
+static int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+int tile_grid_size(qs_dtype dt, int m, int ns, int n_tiles) {
+  const size_t smem = tile_smem_bytes(dt, m, ns);
+  int occ;
+  if (dt == QS_C64)
+    occ = ns == 2 ? occupancy_for<float, 2>(smem) : occupancy_for<float, 1>(smem);
+  else
+    occ = ns == 2 ? occupancy_for<double, 2>(smem) : occupancy_for<double, 1>(smem);
+  // the partials stride is shared by the 1- and 2-state passes of one plan: use
+  // the 2-state occupancy for both (it is never larger)
+  long g = (long)sm_count() * occ;
+  if (g > n_tiles) g = n_tiles;
+  return (int)(g < 1 ? 1 : g);
+}
+
+qs_status launch_tile_pass(qs_dtype dt, const TilePlan& plan, int pi, const TileLaunch& L, cudaStream_t st) {
+  const PlannedPass& pp = plan.passes[pi];
+  const uint32_t fl = pp.hdr.flags;
+  const int ns = (fl & (PF_LOAD_LAM | PF_STORE_LAM)) ? 2 : 1;
+  TileKArgs a;
+  a.psi = L.psi;
+  a.lam = L.lam;
+  a.pass = plan.d_pass + pi;
+  a.phases = plan.d_phase;
+  a.ops = plan.d_ops;
+  a.coef = L.coef;
+  a.cut = L.cut;
+  a.partials = L.partials;
+  a.n = L.n;
+  a.n_edges = L.n_edges;
+  a.grid_stride = L.stride;
+  const size_t smem = tile_smem_bytes(dt, pp.hdr.m, ns);
+  if (dt == QS_C64) {
+    if (ns == 2) {
+      occupancy_for<float, 2>(smem);
+      tile_pass_kernel<float, 2><<<L.grid, kTileThreads, smem, st>>>(a);
+    } else {
+      occupancy_for<float, 1>(smem);
+      tile_pass_kernel<float, 1><<<L.grid, kTileThreads, smem, st>>>(a);
+    }
+  } else {
+    if (ns == 2) {
+      occupancy_for<double, 2>(smem);
+      tile_pass_kernel<double, 2><<<L.grid, kTileThreads, smem, st>>>(a);
+    } else {
+      occupancy_for<double, 1>(smem);
+      tile_pass_kernel<double, 1><<<L.grid, kTileThreads, smem, st>>>(a);
+    }
+  }
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+}  // namespace qs

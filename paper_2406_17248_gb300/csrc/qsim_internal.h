@@ -1,0 +1,211 @@
+// Internal types shared by the host runtime (api.cu, plan.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "qsim.h"
+
+namespace qs {
+
+// ----------------------------------------------------------------------------- limits
+constexpr int kMaxQubits = 34;
+constexpr int kRegBits = 4;          // amplitudes per thread in a tile phase = 2^kRegBits
+constexpr int kTileThreads = 256;    // threads of a fused tile CTA
+constexpr int kTileWarps = kTileThreads / 32;
+constexpr int kMaxTileBits = 13;     // 2^13 amplitudes per tile
+// Largest tile whose two-state (psi, lam) pass fits in shared memory.
+constexpr int max_tile_bits(qs_dtype dt) { return dt == QS_C64 ? 13 : 12; }
+constexpr int kMinTileBits = 6;
+constexpr int kMaxSlotsPerPass = 256;  // gradient/energy accumulators of one launch
+constexpr int kMaxPhasesPerPass = 64;
+constexpr int kSmallMaxBytes = 96 * 1024;  // per-state bytes of the one-CTA engine
+
+// ----------------------------------------------------------------------------- ops
+// One instruction of a fused tile pass.  Register bits rb0/rb1 index the
+// phase's register set (the 2^kRegBits amplitudes a thread holds at a time).
+enum OpType : uint8_t {
+  OP_DENSE1 = 1,    // 2x2 complex matrix on register bit rb0
+  OP_DENSE2 = 2,    // 4x4 on register bits (rb0 = targets[0], rb1 = targets[1])
+  OP_DIAG = 3,      // diagonal D[b0 + 2 b1] on up to two qubits (any bit of the index)
+  OP_RX = 4,        // [[c, -is], [-is, c]] on rb0; coef = (c, s)
+  OP_GRAD1 = 5,     // acc += 2 Re <lam| A |psi>, A 2x2 on rb0
+  OP_GRAD2 = 6,     // acc += 2 Re <lam| A |psi>, A 4x4 on (rb0, rb1)
+  OP_GRADDIAG = 7,  // acc += 2 Re <lam| D |psi>, D diagonal as OP_DIAG
+  OP_GRADX = 8,     // acc += Im <lam| X_rb0 |psi>
+  OP_COST = 9,      // psi_x *= lut[cut(x)]
+  OP_GRADCOST = 10, // acc += C(x) Im(conj(lam_x) psi_x), C = n_edges - 2 cut
+  OP_ENERGY = 11    // acc += C(x) |psi_x|^2 and lam_x = C(x) psi_x
+};
+
+enum OpFlags : uint8_t { OPF_LAM = 1 };  // apply to lam as well as psi
+
+struct DevOp {
+  uint8_t type;
+  uint8_t rb0, rb1;
+  uint8_t flags;
+  uint16_t jc;       // control bits that are register bits (mask over register index)
+  uint16_t slot;     // accumulator slot within the launch
+  uint32_t lc;       // control bits that are tile bits but not register bits (local mask)
+  uint32_t coef;     // index of the first complex coefficient
+  int8_t dloc[2];    // OP_DIAG/GRADDIAG: local bit of qubit 0/1, or -1
+  int8_t dglb[2];    // ... or global bit (outside the tile), or -1
+  uint32_t pad;
+  uint64_t gc;       // control bits outside the tile (checked on the tile offset)
+};
+
+struct DevPhase {
+  int8_t R[kRegBits];  // local bits held in registers (register bit i <-> local bit R[i])
+  int8_t Q[16];        // local bits enumerated by the sub-cube index, low to high
+  int16_t nq;
+  int16_t pad;
+  int op_begin, op_end;
+};
+
+enum PassFlags : uint32_t {
+  PF_LOAD_PSI = 1,
+  PF_LOAD_LAM = 2,
+  PF_STORE_PSI = 4,
+  PF_STORE_LAM = 8,
+  PF_GEN_PLUS = 16,  // psi tile = 2^{-n/2} instead of a load
+  PF_GEN_ZERO = 32,  // psi tile = |0...0> instead of a load
+  PF_NEED_CUT = 64   // load the cut-value tile
+};
+
+struct DevPass {
+  int m;          // tile bits
+  int c;          // low contiguous bits (local bit i = global bit i for i < c)
+  int n_phases;
+  int phase_begin;
+  int ncomp;      // global bits not in the tile
+  uint32_t flags;
+  int n_slots;
+  int slot_base;
+  int8_t comp[40];
+  uint64_t hiA[64];  // deposit of local bits c..c+5 into their global positions
+  uint64_t hiB[128]; // deposit of local bits c+6..c+12
+};
+
+// ----------------------------------------------------------------------------- host plans
+struct HostGate {
+  int kind;
+  int nt;
+  int t[2];
+  std::vector<int> ctrls;
+  int param;
+  double coef, constant;
+  std::vector<double> matrix;  // interleaved complex, for QS_GATE_MATRIX
+};
+
+// Class of a gate for the engines: which tile-pass op realises it.
+enum GateClass { GC_DENSE1, GC_DENSE2, GC_DIAG1, GC_DIAG2 };
+
+struct PlannedPass {
+  DevPass hdr;
+  std::vector<DevPhase> phases;
+  std::vector<DevOp> ops;
+};
+
+// A compiled sequence of tile passes plus the coefficient recipe to fill per call.
+struct TilePlan {
+  int n = 0;
+  qs_dtype dtype = QS_C64;
+  int m = 0, c = 0;
+  std::vector<PlannedPass> passes;
+  int n_coef = 0;  // complex coefficients per call
+  int n_slots = 0;
+  // device copies
+  DevPass* d_pass = nullptr;
+  DevPhase* d_phase = nullptr;
+  DevOp* d_ops = nullptr;
+  void free_device();
+  qs_status upload(cudaStream_t st);
+};
+
+// ----------------------------------------------------------------------------- kernel launchers
+struct TileLaunch {
+  void* psi;
+  void* lam;
+  const void* coef;
+  const uint8_t* cut;
+  double* partials;  // [n_slots_total][grid]
+  int n;
+  int n_edges;
+  int grid;    // CTAs of this launch
+  int stride;  // stride of the partials array (the plan's 2-state grid)
+};
+
+qs_status launch_tile_pass(qs_dtype dt, const TilePlan& plan, int pass_index, const TileLaunch& L,
+                           cudaStream_t st);
+int tile_grid_size(qs_dtype dt, int m, int ns, int n_tiles);
+size_t tile_smem_bytes(qs_dtype dt, int m, int ns);
+
+// Per-gate (unfused) kernels.
+qs_status launch_gate_dense(qs_dtype dt, void* psi, int n, int nt, const int* t, uint64_t cmask,
+                            const double* mat /* interleaved complex (2^nt)^2 */, cudaStream_t st);
+qs_status launch_gate_diag(qs_dtype dt, void* psi, int n, int nt, const int* t, uint64_t cmask,
+                           const double* diag /* interleaved complex 2^nt */, cudaStream_t st);
+
+// States.
+qs_status launch_set_basis(qs_dtype dt, void* psi, int n, uint64_t index, cudaStream_t st);
+qs_status launch_set_plus(qs_dtype dt, void* psi, int n, cudaStream_t st);
+
+// Hamiltonians: groups of terms sharing an X mask.
+struct DevHamTerm {
+  uint64_t zmask;
+  double re, im;  // coef * i^{#Y}
+};
+struct DevHamGroup {
+  uint64_t xmask;
+  int begin, end;
+};
+qs_status launch_ham_apply(qs_dtype dt, const void* psi, void* lam /* nullable */, int n,
+                           const DevHamGroup* groups, int n_groups, const DevHamTerm* terms,
+                           double* partials, int grid, cudaStream_t st);
+int ham_grid_size(int n);
+qs_status launch_inner(qs_dtype dt, const void* a, const void* b, int n, double* partials /* [2][grid] */,
+                       int grid, cudaStream_t st);
+qs_status launch_norm2(qs_dtype dt, const void* a, int n, double* partials, int grid, cudaStream_t st);
+// out[s] = sum_b partials[s * nb + b] * scale[s] (scale nullable), fixed order.
+qs_status launch_reduce_slots(const double* partials, int n_slots, int nb, const double* scale,
+                              double* out, cudaStream_t st);
+// grad[p] = sum over gates g of param p: coef_g * gate_grad[g]  (CSR by parameter)
+qs_status launch_param_gather(const double* gate_grad, const int* row_ptr, const int* gate_idx,
+                              const double* gate_coef, int n_params, double* grad, cudaStream_t st);
+
+// QAOA
+qs_status launch_cut_values(uint8_t* cut, int n, const int* d_edges, int n_edges, cudaStream_t st);
+
+// Sampling
+qs_status launch_sample(qs_dtype dt, const void* psi, int n, uint64_t shots, uint64_t seed,
+                        double* scratch /* cdf of block sums */, uint64_t* d_out, cudaStream_t st);
+size_t sample_scratch_doubles(int n);
+
+// ----------------------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+qs_status cuda_fail(cudaError_t e, const char* what);
+
+#define QS_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t _e = (call);                           \
+    if (_e != cudaSuccess) return qs::cuda_fail(_e, #call); \
+  } while (0)
+
+#define QS_CHECK(cond, msg)                   \
+  do {                                        \
+    if (!(cond)) {                            \
+      qs::set_error(msg);                     \
+      return QS_ERR_INVALID_ARG;              \
+    }                                         \
+  } while (0)
+
+#define QS_TRY(expr)                  \
+  do {                                \
+    qs_status _s = (expr);            \
+    if (_s != QS_OK) return _s;       \
+  } while (0)
+
+}  // namespace qs

@@ -244,3 +244,54 @@ def batched_vqe(count: int, seed: int, n_range=(10, 20), depth_range=(2, 10)) ->
         params = rng.uniform(-np.pi, np.pi, size=circ.n_params)
         out.append(Instance(circ, ham, params))
     return out
+
+
+# --------------------------------------------------------------------------- test mixes
+
+ONE_Q_KINDS = ("I", "X", "Y", "Z", "H", "S", "SDG", "T", "TDG", "RX", "RY", "RZ", "PS")
+TWO_Q_KINDS = ("SWAP", "RXX", "RYY", "RZZ")
+
+
+def random_mixed_circuit(n: int, n_gates: int, seed: int, max_ctrls: int = 2, with_matrix: bool = True) -> Circuit:
+    """Every gate kind, random targets and 0..max_ctrls controls, linear angle
+    bindings (own parameter per rotation), optionally one random 2-qubit unitary.
+    The unitary is drawn as the Q factor of a complex Gaussian matrix."""
+    rng = np.random.default_rng(seed)
+    gates: List[Gate] = []
+    p = 0
+    for _ in range(n_gates):
+        two = rng.random() < 0.3 and n >= 2
+        kinds = TWO_Q_KINDS if two else ONE_Q_KINDS
+        kind = kinds[int(rng.integers(len(kinds)))]
+        qs = [int(q) for q in rng.permutation(n)]
+        nt = 2 if two else 1
+        targets = tuple(qs[:nt])
+        nc = int(rng.integers(0, min(max_ctrls, n - nt) + 1))
+        ctrls = tuple(qs[nt:nt + nc])
+        if kind in PARAM_GATES:
+            gates.append(Gate(kind, targets, ctrls, param=p, coef=float(rng.uniform(-2, 2)),
+                              const=float(rng.uniform(-1, 1))))
+            p += 1
+        else:
+            gates.append(Gate(kind, targets, ctrls))
+    if with_matrix and n >= 2 and rng.random() < 0.5:
+        a = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
+        q, _ = np.linalg.qr(a)
+        gates.append(Gate("MATRIX", (1, 0), (), matrix=tuple(complex(v) for v in q.reshape(-1))))
+    return Circuit(n, gates, p)
+
+
+def random_pauli_sum(n: int, n_terms: int, seed: int) -> PauliSum:
+    rng = np.random.default_rng(seed)
+    terms = []
+    for _ in range(n_terms):
+        word = " ".join(f"{'XYZ'[int(rng.integers(3))]}{q}" for q in range(n) if rng.random() < 0.5)
+        terms.append((float(rng.normal()), word))
+    return pauli_sum_from_strings(n, terms)
+
+
+def random_state(n: int, seed: int) -> np.ndarray:
+    """A normalised complex Gaussian vector (an input state, not a simulation result)."""
+    rng = np.random.default_rng(seed)
+    v = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    return v / np.linalg.norm(v)

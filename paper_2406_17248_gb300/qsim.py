@@ -1,0 +1,344 @@
+"""Thin ctypes binding of libqsim.so (the C ABI in include/qsim.h).
+
+Only argument marshalling lives here: every step of the simulation runs in the
+CUDA library.  PyTorch supplies device memory (state buffers are torch tensors
+the library views through qs_state_create's dev_buf) and the CUDA stream.  If
+the library has not been built, every entry point raises instead of falling
+back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import inputs as I
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libqsim.so")
+
+C64, C128 = 0, 1
+KIND = {"I": 0, "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "SDG": 6, "T": 7, "TDG": 8, "SWAP": 9,
+        "RX": 16, "RY": 17, "RZ": 18, "PS": 19, "RXX": 20, "RYY": 21, "RZZ": 22, "MATRIX": 32}
+STATUS = {0: "QS_OK", 1: "QS_ERR_INVALID_ARG", 2: "QS_ERR_OUT_OF_MEMORY", 3: "QS_ERR_CUDA",
+          4: "QS_ERR_TIMEOUT", 5: "QS_ERR_UNSUPPORTED"}
+
+# (name, argtypes) of every exported entry point, in header order.
+_VP, _I, _D, _U64, _SZ = C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_size_t
+_PD = C.POINTER(C.c_double)
+_PI = C.POINTER(C.c_int)
+_PU64 = C.POINTER(C.c_uint64)
+_PVP = C.POINTER(C.c_void_p)
+SIGNATURES = [
+    ("qs_version", []),
+    ("qs_last_error", []),
+    ("qs_state_create", [_I, _I, _VP, _SZ, _VP, _PVP]),
+    ("qs_state_destroy", [_VP]),
+    ("qs_state_device_ptr", [_VP, _PVP]),
+    ("qs_state_set_basis", [_VP, _U64]),
+    ("qs_state_set_plus", [_VP]),
+    ("qs_state_copy_in", [_VP, _VP, _I]),
+    ("qs_state_copy_out", [_VP, _VP, _I]),
+    ("qs_state_copy", [_VP, _VP]),
+    ("qs_state_norm2", [_VP, _PD]),
+    ("qs_circuit_create", [_I, _PVP]),
+    ("qs_circuit_destroy", [_VP]),
+    ("qs_circuit_add", [_VP, _I, _PI, _I, _PI, _I, _I, _D, _D, _PD]),
+    ("qs_circuit_finalize", [_VP, _I, _VP]),
+    ("qs_circuit_info", [_VP, _PI, _PI, _PI]),
+    ("qs_apply_circuit", [_VP, _VP, _PD, _I]),
+    ("qs_ham_create", [_I, _I, _PU64, _PU64, _PD, _PVP]),
+    ("qs_ham_destroy", [_VP]),
+    ("qs_apply_hamiltonian", [_VP, _VP, _VP]),
+    ("qs_expectation", [_VP, _VP, _PD]),
+    ("qs_inner_product", [_VP, _VP, _PD]),
+    ("qs_expectation_with_grad", [_VP, _VP, _VP, _VP, _PD, _I, _PD, _PD]),
+    ("qs_sample", [_VP, _U64, _U64, _PU64]),
+    ("qs_qaoa_create", [_I, _PI, _I, _I, _D, _I, _VP, _PVP]),
+    ("qs_qaoa_destroy", [_VP]),
+    ("qs_qaoa_info", [_VP, _PI, _PI, _PD]),
+    ("qs_qaoa_evolve", [_VP, _VP, _PD, _PD]),
+    ("qs_qaoa_expectation", [_VP, _VP, _PD, _PD, _PD]),
+    ("qs_qaoa_expectation_with_grad", [_VP, _VP, _VP, _PD, _PD, _PD, _PD, _PD]),
+]
+
+
+class QSimError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [("fuse", C.c_int), ("tile_bits", C.c_int), ("low_bits", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libqsim.so (built by paper_2406_17248_gb300.build); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libqsim.so is not built ({LIB_PATH}); run paper_2406_17248_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, args in SIGNATURES:
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_char_p if name in ("qs_version", "qs_last_error") else C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise QSimError(status, lib().qs_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_PD)
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+# --------------------------------------------------------------------------- states
+
+class State:
+    """A 2^n amplitude state in a torch-owned device buffer (complex64 / complex128)."""
+
+    def __init__(self, n: int, dtype: int = C64, stream=None, device=None):
+        import torch
+        self.n, self.dtype = n, dtype
+        ne = max(n, 4)
+        tdt = torch.complex64 if dtype == C64 else torch.complex128
+        self.buffer = torch.empty(1 << ne, dtype=tdt, device=device or "cuda")
+        self._stream = stream
+        h = C.c_void_p()
+        _check(lib().qs_state_create(n, dtype, C.c_void_p(self.buffer.data_ptr()),
+                                     self.buffer.numel() * self.buffer.element_size(),
+                                     C.c_void_p(_stream_ptr(stream)), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qs_state_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def amplitudes(self):
+        """Zero-copy torch view of the 2^n amplitudes (device)."""
+        return self.buffer[: 1 << self.n]
+
+    def set_basis(self, index: int = 0):
+        _check(lib().qs_state_set_basis(self.h, index))
+        return self
+
+    def set_plus(self):
+        _check(lib().qs_state_set_plus(self.h))
+        return self
+
+    def set_qs(self, amps: np.ndarray):
+        a = np.ascontiguousarray(amps, dtype=np.complex64 if self.dtype == C64 else np.complex128)
+        if a.size != 1 << self.n:
+            raise ValueError("wrong number of amplitudes")
+        _check(lib().qs_state_copy_in(self.h, a.ctypes.data_as(C.c_void_p), 0))
+        return self
+
+    def get_qs(self) -> np.ndarray:
+        out = np.empty(1 << self.n, dtype=np.complex64 if self.dtype == C64 else np.complex128)
+        _check(lib().qs_state_copy_out(self.h, out.ctypes.data_as(C.c_void_p), 0))
+        return out
+
+    def copy_from(self, other: "State"):
+        _check(lib().qs_state_copy(self.h, other.h))
+        return self
+
+    def norm2(self) -> float:
+        v = C.c_double()
+        _check(lib().qs_state_norm2(self.h, C.byref(v)))
+        return v.value
+
+
+# --------------------------------------------------------------------------- circuits
+
+class Circuit:
+    def __init__(self, n: int):
+        self.n = n
+        h = C.c_void_p()
+        _check(lib().qs_circuit_create(n, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qs_circuit_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, kind: str, targets: Sequence[int], ctrls: Sequence[int] = (), param: int = -1,
+            coef: float = 1.0, const: float = 0.0, matrix=None):
+        t = (C.c_int * len(targets))(*targets)
+        c = (C.c_int * max(len(ctrls), 1))(*ctrls) if ctrls else None
+        m = None
+        if matrix is not None:
+            mm = np.asarray(matrix, dtype=np.complex128).reshape(-1)
+            inter = np.empty(2 * mm.size)
+            inter[0::2], inter[1::2] = mm.real, mm.imag
+            self._keep = inter
+            m = _dptr(inter)
+        _check(lib().qs_circuit_add(self.h, KIND[kind], t, len(targets), c, len(ctrls), param, coef, const, m))
+        return self
+
+    def finalize(self, dtype: int = C64, fuse: int = 0, tile_bits: int = 0, low_bits: int = 0):
+        o = Options(fuse, tile_bits, low_bits)
+        _check(lib().qs_circuit_finalize(self.h, dtype, C.byref(o)))
+        return self
+
+    def info(self):
+        g, p, s = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().qs_circuit_info(self.h, C.byref(g), C.byref(p), C.byref(s)))
+        return {"gates": g.value, "params": p.value, "passes": s.value}
+
+    def apply(self, state: State, params=None):
+        pr = np.ascontiguousarray(params if params is not None else np.zeros(0), dtype=np.float64)
+        _check(lib().qs_apply_circuit(state.h, self.h, _dptr(pr) if pr.size else None, int(pr.size)))
+        return state
+
+
+def circuit_from(circ: I.Circuit) -> Circuit:
+    c = Circuit(circ.n_qubits)
+    for g in circ.gates:
+        c.add(g.kind, g.targets, g.ctrls, g.param, g.coef, g.const,
+              None if g.matrix is None else np.asarray(g.matrix))
+    return c
+
+
+class Hamiltonian:
+    def __init__(self, ham: I.PauliSum):
+        self.n = ham.n_qubits
+        x = np.ascontiguousarray(ham.xmask, dtype=np.uint64)
+        z = np.ascontiguousarray(ham.zmask, dtype=np.uint64)
+        cf = np.ascontiguousarray(ham.coef, dtype=np.float64)
+        h = C.c_void_p()
+        _check(lib().qs_ham_create(self.n, int(cf.size), x.ctypes.data_as(_PU64), z.ctypes.data_as(_PU64),
+                                   _dptr(cf), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qs_ham_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def expectation(state: State, ham: Hamiltonian) -> float:
+    v = C.c_double()
+    _check(lib().qs_expectation(state.h, ham.h, C.byref(v)))
+    return v.value
+
+
+def apply_hamiltonian(dst: State, src: State, ham: Hamiltonian) -> State:
+    _check(lib().qs_apply_hamiltonian(dst.h, src.h, ham.h))
+    return dst
+
+
+def inner_product(bra: State, ket: State) -> complex:
+    out = np.zeros(2)
+    _check(lib().qs_inner_product(bra.h, ket.h, _dptr(out)))
+    return complex(out[0], out[1])
+
+
+def expectation_with_grad(psi: State, lam: State, circ: Circuit, ham: Hamiltonian, params):
+    pr = np.ascontiguousarray(params, dtype=np.float64)
+    grad = np.zeros(max(pr.size, 1))
+    e = C.c_double()
+    _check(lib().qs_expectation_with_grad(psi.h, lam.h, circ.h, ham.h, _dptr(pr) if pr.size else None,
+                                          int(pr.size), C.byref(e), _dptr(grad)))
+    return e.value, grad[: pr.size]
+
+
+def sample(state: State, shots: int, seed: int) -> np.ndarray:
+    out = np.zeros(max(shots, 1), dtype=np.uint64)
+    _check(lib().qs_sample(state.h, shots, seed, out.ctypes.data_as(_PU64)))
+    return out[:shots]
+
+
+# --------------------------------------------------------------------------- QAOA
+
+class QAOA:
+    """MaxCut QAOA engine: |+>^n, p layers of exp(-i gs gamma C) then RX(beta)."""
+
+    def __init__(self, n: int, edges, p: int, gamma_scale: float = 1.0, dtype: int = C64,
+                 tile_bits: int = 0, low_bits: int = 0):
+        self.n, self.p, self.dtype = n, p, dtype
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+        self._edges = e
+        o = Options(0, tile_bits, low_bits)
+        h = C.c_void_p()
+        _check(lib().qs_qaoa_create(n, e.ctypes.data_as(_PI), int(e.size // 2), p, gamma_scale, dtype,
+                                    C.byref(o), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qs_qaoa_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        f, r, b = C.c_int(), C.c_int(), C.c_double()
+        _check(lib().qs_qaoa_info(self.h, C.byref(f), C.byref(r), C.byref(b)))
+        return {"fwd_passes": f.value, "rev_passes": r.value, "bytes_per_eval": b.value}
+
+    def _angles(self, gamma, beta):
+        g = np.ascontiguousarray(gamma, dtype=np.float64)
+        b = np.ascontiguousarray(beta, dtype=np.float64)
+        if g.size != self.p or b.size != self.p:
+            raise ValueError("gamma and beta need p entries each")
+        return g, b
+
+    def evolve(self, psi: State, gamma, beta) -> State:
+        g, b = self._angles(gamma, beta)
+        _check(lib().qs_qaoa_evolve(self.h, psi.h, _dptr(g), _dptr(b)))
+        return psi
+
+    def expectation(self, psi: State, gamma, beta) -> float:
+        g, b = self._angles(gamma, beta)
+        e = C.c_double()
+        _check(lib().qs_qaoa_expectation(self.h, psi.h, _dptr(g), _dptr(b), C.byref(e)))
+        return e.value
+
+    def expectation_with_grad(self, psi: State, lam: State, gamma, beta):
+        g, b = self._angles(gamma, beta)
+        e = C.c_double()
+        dg, db = np.zeros(self.p), np.zeros(self.p)
+        _check(lib().qs_qaoa_expectation_with_grad(self.h, psi.h, lam.h, _dptr(g), _dptr(b), C.byref(e),
+                                                   _dptr(dg), _dptr(db)))
+        return e.value, dg, db

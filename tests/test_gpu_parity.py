@@ -1,0 +1,259 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (stated per result): amplitudes max-abs 1e-11 (complex128) and
+5e-5 (complex64); energies and gradients abs error <= tol * max(1, sum |c_k|),
+the Hamiltonian's coefficient 1-norm (the largest |E| can be)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import qsim_oracle as O
+from paper_2406_17248_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+TOL = {0: 5e-5, 1: 1e-11}
+
+
+@pytest.fixture(scope="module")
+def Q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_17248_gb300 import build
+    build.build()
+    from paper_2406_17248_gb300 import qsim
+    return qsim
+
+
+def scale(ham):
+    return max(1.0, float(np.abs(ham.coef).sum()))
+
+
+def run_circuit(Q, circ, params, dt, psi0=None, **opts):
+    c = Q.circuit_from(circ).finalize(dt, **opts)
+    s = Q.State(circ.n_qubits, dt)
+    if psi0 is None:
+        s.set_basis(0)
+    else:
+        s.set_qs(psi0)
+    c.apply(s, params)
+    return s.get_qs().astype(np.complex128), c
+
+
+PLAN_OPTS = [dict(), dict(tile_bits=6, low_bits=1), dict(tile_bits=6, low_bits=3), dict(tile_bits=8, low_bits=2),
+             dict(tile_bits=13, low_bits=5), dict(fuse=-1)]
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 10, 13])
+def test_apply_mixed_circuits(Q, dt, n):
+    circ = I.random_mixed_circuit(n, 60, seed=1000 + n)
+    params = I.uniform_params(circ.n_params, 2000 + n)
+    psi0 = I.random_state(n, 3000 + n)
+    want = O.evolve(circ, params, psi0)
+    for opts in PLAN_OPTS:
+        got, _ = run_circuit(Q, circ, params, dt, psi0, **opts)
+        err = np.abs(got - want).max()
+        assert err < TOL[dt], (opts, err)
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_random_circuit_recipe_at_20_qubits(Q, dt):
+    """The 28-qubit benchmark recipe (500 gates over {H,RX,RY,RZ,CNOT,CZ}) at 20
+    qubits, where the oracle runs in seconds; spans many tiles and passes."""
+    n = 20
+    circ = I.random_circuit(n, 500, seed=2)
+    want = O.evolve(circ, [], O.zero_state(n))
+    got, c = run_circuit(Q, circ, [], dt)
+    err = np.abs(got - want).max()
+    assert err < TOL[dt], err
+    assert c.info()["passes"] < 500 / 4
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n", [1, 5, 9, 14])
+def test_expectation_apply_hamiltonian_inner(Q, dt, n):
+    ham = I.random_pauli_sum(n, 15, seed=n)
+    a = I.random_state(n, 10 + n)
+    b = I.random_state(n, 20 + n)
+    H = Q.Hamiltonian(ham)
+    sa = Q.State(n, dt).set_qs(a)
+    sb = Q.State(n, dt).set_qs(b)
+    e = Q.expectation(sa, H)
+    assert abs(e - O.expectation(a, ham)) < TOL[dt] * scale(ham)
+    Q.apply_hamiltonian(sb, sa, H)
+    got = sb.get_qs().astype(np.complex128)
+    assert np.abs(got - O.apply_hamiltonian(a, ham)).max() < TOL[dt] * scale(ham)
+    sb.set_qs(b)
+    ip = Q.inner_product(sa, sb)
+    assert abs(ip - O.inner_product(a, b)) < TOL[dt]
+    assert abs(sa.norm2() - 1.0) < TOL[dt]
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_paper_printed_values_through_the_abi(Q, dt):
+    g = json.load(open(os.path.join(GOLD, "paper_prints.json")))
+    c = Q.Circuit(2).add("RX", [0], const=g["zz_after_rx"]["theta"])
+    s = Q.State(2, dt).set_basis(0)
+    c.apply(s)
+    H = Q.Hamiltonian(I.pauli_sum_from_strings(2, [(1.0, "Z0 Z1")]))
+    assert abs(Q.expectation(s, H) - g["zz_after_rx"]["value"]) < TOL[dt]
+    phi = Q.State(2, dt).set_basis(0)
+    Q.Circuit(2).add("RY", [0], const=g["inner_product"]["ry"]).apply(phi)
+    ip = Q.inner_product(phi, s)
+    assert abs(ip - complex(g["inner_product"]["re"], g["inner_product"]["im"])) < TOL[dt]
+    # apply_hamiltonian(X0 Y1) on |00>, then H(0), X(1 <- 0)
+    src = Q.State(2, dt).set_basis(0)
+    dst = Q.State(2, dt)
+    Q.apply_hamiltonian(dst, src, Q.Hamiltonian(I.pauli_sum_from_strings(2, [(1.0, "X0 Y1")])))
+    Q.Circuit(2).add("H", [0]).add("X", [1], [0]).apply(dst)
+    want = np.array(g["apply_hamiltonian_then_circuit"]["amplitudes_re"]) + \
+        1j * np.array(g["apply_hamiltonian_then_circuit"]["amplitudes_im"])
+    assert np.abs(dst.get_qs() - want).max() < TOL[dt]
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_bell_ghz_closed_forms(Q, dt):
+    for n in (2, 3, 8, 17):
+        c = Q.Circuit(n).add("H", [0])
+        for q in range(1, n):
+            c.add("X", [q], [q - 1])
+        s = Q.State(n, dt).set_basis(0)
+        c.apply(s)
+        got = s.get_qs()
+        want = np.zeros(1 << n)
+        want[0] = want[-1] = 1 / math.sqrt(2)
+        assert np.abs(got - want).max() < TOL[dt]
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_adjoint_hea_12q(Q, dt):
+    """The 12-qubit HEA workload: 4 layers, 96 parameters U[-pi, pi] (seed 1),
+    H = sum Z_i Z_{i+1} + 0.5 sum X_i."""
+    n = 12
+    circ = I.hea_circuit(n, 4)
+    ham = I.chain_zz_x(n)
+    params = I.uniform_params(circ.n_params, 1)
+    E0, g0 = O.adjoint_gradient(circ, ham, params, O.zero_state(n))
+    c = Q.circuit_from(circ).finalize(dt)
+    psi, lam = Q.State(n, dt).set_basis(0), Q.State(n, dt)
+    E, g = Q.expectation_with_grad(psi, lam, c, Q.Hamiltonian(ham), params)
+    tol = TOL[dt] * scale(ham)
+    assert abs(E - E0) < tol
+    assert np.abs(g - g0).max() < tol
+    # psi is returned to the initial state up to rounding
+    assert np.abs(psi.get_qs() - O.zero_state(n)).max() < 100 * TOL[dt]
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n,opts", [(4, {}), (6, dict(tile_bits=6, low_bits=2)), (9, dict(tile_bits=7, low_bits=3)),
+                                    (11, {}), (14, dict(tile_bits=10, low_bits=4))])
+def test_adjoint_mixed_circuits(Q, dt, n, opts):
+    circ = I.random_mixed_circuit(n, 40, seed=500 + n)
+    # fold parameters onto 5 shared ones
+    gates = [I.Gate(g.kind, g.targets, g.ctrls, (g.param % 5) if g.param >= 0 else -1, g.coef, g.const, g.matrix)
+             for g in circ.gates]
+    circ = I.Circuit(n, gates, 5)
+    ham = I.random_pauli_sum(n, 8, seed=600 + n)
+    params = I.uniform_params(5, 700 + n)
+    psi0 = I.random_state(n, 800 + n)
+    E0, g0 = O.adjoint_gradient(circ, ham, params, psi0)
+    c = Q.circuit_from(circ).finalize(dt, **opts)
+    psi, lam = Q.State(n, dt).set_qs(psi0), Q.State(n, dt)
+    E, g = Q.expectation_with_grad(psi, lam, c, Q.Hamiltonian(ham), params)
+    tol = TOL[dt] * scale(ham)
+    assert abs(E - E0) < tol
+    assert np.abs(g - g0).max() < tol * 10
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_qaoa_qupack_k5_pin(Q, dt):
+    g = json.load(open(os.path.join(GOLD, "qupack_qaoa_k5.json")))
+    n, p = g["n_qubits"], g["depth"]
+    q = Q.QAOA(n, I.complete_graph(n), p, gamma_scale=1.0, dtype=dt)
+    psi, lam = Q.State(n, dt), Q.State(n, dt)
+    E, dg, db = q.expectation_with_grad(psi, lam, [g["gamma"]] * p, [g["beta"]] * p)
+    tol = TOL[dt] * 10  # sum |c| = 10 edges
+    assert abs(E - g["expectation"]) < tol
+    assert np.abs(dg - g["gamma_grad"]).max() < tol * p
+    assert np.abs(db - g["beta_grad"]).max() < tol * p
+    assert abs(q.expectation(psi, [g["gamma"]] * p, [g["beta"]] * p) - g["expectation"]) < tol
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n,p,opts", [(6, 1, {}), (8, 3, dict(tile_bits=6, low_bits=2)), (12, 8, {}),
+                                      (14, 4, dict(tile_bits=8, low_bits=3)), (16, 8, dict(tile_bits=12, low_bits=4)),
+                                      (18, 2, dict(tile_bits=13))])
+def test_qaoa_random_regular(Q, dt, n, p, opts):
+    edges = I.random_regular_graph(n, 3, seed=n)
+    angles = I.uniform_params(2 * p, n, 0.0, np.pi)
+    E0, dg0, db0 = O.qaoa_expectation_with_grad(n, edges, angles[:p], angles[p:], 0.5)
+    q = Q.QAOA(n, edges, p, gamma_scale=0.5, dtype=dt, **opts)
+    psi, lam = Q.State(n, dt), Q.State(n, dt)
+    E, dg, db = q.expectation_with_grad(psi, lam, angles[:p], angles[p:])
+    tol = TOL[dt] * len(edges)
+    assert abs(E - E0) < tol
+    assert np.abs(dg - dg0).max() < tol
+    assert np.abs(db - db0).max() < tol
+    # energy-only and evolve paths
+    assert abs(q.expectation(psi, angles[:p], angles[p:]) - E0) < tol
+    want = O.qaoa_layers_state(n, edges, angles[:p], angles[p:], 0.5)
+    assert np.abs(psi.get_qs() - want).max() < TOL[dt]
+
+
+def test_qaoa_24q_against_stored_oracle_values(Q):
+    path = os.path.join(GOLD, "qaoa24_p8.json")
+    g = json.load(open(path))
+    n, p = g["n"], g["p"]
+    edges = [tuple(e) for e in g["edges"]]
+    assert edges == I.random_regular_graph(n, 3, g["seed"])
+    for dt in (0, 1):
+        q = Q.QAOA(n, edges, p, gamma_scale=g["gamma_scale"], dtype=dt)
+        psi, lam = Q.State(n, dt), Q.State(n, dt)
+        E, dg, db = q.expectation_with_grad(psi, lam, g["gamma"], g["beta"])
+        tol = TOL[dt] * len(edges)
+        assert abs(E - g["energy"]) < tol
+        assert np.abs(dg - g["dgamma"]).max() < tol
+        assert np.abs(db - g["dbeta"]).max() < tol
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n", [3, 10, 16])
+def test_sampling_matches_oracle_on_the_same_state(Q, dt, n):
+    circ = I.random_circuit(n, 8 * n, seed=40 + n)
+    s = Q.State(n, dt).set_basis(0)
+    Q.circuit_from(circ).apply(s)
+    shots, seed = 20000, 12345 + n
+    got = Q.sample(s, shots, seed)
+    amps = s.get_qs().astype(np.complex128)
+    want = O.sample(amps, shots, seed)
+    bad = np.nonzero(got != want)[0]
+    # a mismatch is allowed only where the uniform sits within rounding of a CDF step
+    p = amps.real ** 2 + amps.imag ** 2
+    cdf = np.cumsum(p)
+    for sidx in bad:
+        u = O.shot_uniform(seed, int(sidx)) * cdf[-1]
+        assert np.min(np.abs(cdf - u)) < 1e-12, (sidx, got[sidx], want[sidx])
+    assert len(bad) <= 2
+
+
+def test_error_paths(Q):
+    s = Q.State(4, 0)
+    h = Q.Hamiltonian(I.pauli_sum_from_strings(5, [(1.0, "Z0")]))
+    with pytest.raises(Q.QSimError, match="qubit count"):
+        Q.expectation(s, h)
+    c = Q.circuit_from(I.hea_circuit(4, 1)).finalize(0)
+    with pytest.raises(Q.QSimError, match="different states"):
+        Q.expectation_with_grad(s, s, c, Q.Hamiltonian(I.chain_zz_x(4)), np.zeros(8))
+    with pytest.raises(Q.QSimError, match="too few parameters"):
+        c.apply(s, np.zeros(3))
+    with pytest.raises(Q.QSimError, match="basis index"):
+        s.set_basis(16)
+    q = Q.QAOA(5, [(0, 1)], 2)
+    with pytest.raises(Q.QSimError, match="n/dtype"):
+        q.expectation(s, [0, 0], [0, 0])

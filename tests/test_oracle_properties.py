@@ -67,29 +67,7 @@ def test_ry_expectations_closed_form(theta):
 
 
 def _random_mixed_circuit(n, n_gates, seed):
-    rng = np.random.default_rng(seed)
-    gates = []
-    p = 0
-    for _ in range(n_gates):
-        two = rng.random() < 0.3 and n >= 2
-        kinds = ALL_2Q if two else ALL_1Q
-        kind = kinds[int(rng.integers(len(kinds)))]
-        qs = [int(q) for q in rng.permutation(n)]
-        nt = 2 if two else 1
-        targets = tuple(qs[:nt])
-        nc = int(rng.integers(0, min(2, n - nt) + 1))
-        ctrls = tuple(qs[nt:nt + nc])
-        if kind in I.PARAM_GATES:
-            gates.append(I.Gate(kind, targets, ctrls, param=p, coef=float(rng.uniform(-2, 2)),
-                                const=float(rng.uniform(-1, 1))))
-            p += 1
-        else:
-            gates.append(I.Gate(kind, targets, ctrls))
-    if rng.random() < 0.5 and n >= 2:  # one custom matrix gate (a random unitary)
-        a = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
-        q, _ = np.linalg.qr(a)
-        gates.append(I.Gate("MATRIX", (1, 0), (), matrix=tuple(q.reshape(-1))))
-    return I.Circuit(n, gates, p)
+    return I.random_mixed_circuit(n, n_gates, seed)
 
 
 @pytest.mark.parametrize("seed", range(6))
@@ -116,12 +94,7 @@ def test_norm_preserved_and_inverse_restores():
 
 
 def _random_pauli_sum(n, n_terms, seed):
-    rng = np.random.default_rng(seed)
-    terms = []
-    for _ in range(n_terms):
-        word = " ".join(f"{'XYZ'[int(rng.integers(3))]}{q}" for q in range(n) if rng.random() < 0.5)
-        terms.append((float(rng.normal()), word))
-    return I.pauli_sum_from_strings(n, terms)
+    return I.random_pauli_sum(n, n_terms, seed)
 
 
 @pytest.mark.parametrize("n", [1, 3, 6])

@@ -1,0 +1,343 @@
+"""Benchmark: adjoint energy + gradient evaluations of 30-qubit complex64 QAOA.
+
+Workload (the 30-qubit QAOA MaxCut configuration): a seeded random 3-regular
+graph on 30 nodes (pairing model, seed 3, 45 edges), p = 8 layers of RZZ(gamma_l)
+on every edge then RX(beta_l) on every qubit, 16 angles U[0, pi] (seed 3),
+complex64 state from |+>^30 (8.6 GB, larger than L2, so no flush is needed).
+One step = one call of qs_qaoa_expectation_with_grad: energy <C> and its 16
+gradient entries by the adjoint method.
+
+Run:  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+Prints one JSON line (rank 0).  With N > 1 (torchrun), every rank evaluates its
+own independent angle vector (replicas: the evaluations share nothing) and the
+value is the sum of evaluations over all ranks / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "30q c64 adjoint energy+grad evals/s; HBM GB/s vs peak; batched vs plain"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload(n=30, p=8, seed=3):
+    from paper_2406_17248_gb300 import inputs as I
+    import numpy as np
+    edges = I.random_regular_graph(n, 3, seed)
+    angles = I.uniform_params(2 * p, seed, 0.0, float(np.pi))
+    return edges, angles[:p], angles[p:]
+
+
+def config(n, p, n_edges):
+    return {"workload": f"QAOA MaxCut energy+adjoint gradient, {n} qubits, 3-regular graph (seed 3, {n_edges} edges), "
+                        f"p={p}, complex64 from |+>^{n}",
+            "n_qubits": n, "p": p, "edges": n_edges, "params": 2 * p, "state_dtype": "complex64",
+            "l2": "state 2^30 x 8 B = 8.6 GB > L2; no flush needed", "parallelism": "replicas"}
+
+
+# --------------------------------------------------------------------------- distributed helpers
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(value: float, ws: int) -> float:
+    """Max of a float over ranks (identity for one rank)."""
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- roofline inputs
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_tile.cu", "qsim_internal.h"):
+        with open(os.path.join(ROOT, "paper_2406_17248_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_launch():
+    """DRAM bytes per reverse-pass launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "tile_pass_qaoa.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    if not (m_hash and m_tr) or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_tr.group(1))
+
+
+# --------------------------------------------------------------------------- CPU oracle sample
+
+def oracle_sample(n_small=18, p=8, evals=1):
+    """Time the FP64 oracle on the same recipe at n_small qubits in a child process
+    pinned to one BLAS thread; return (evals/s at n_small, seconds, cores)."""
+    code = (
+        "import sys,time; sys.path.insert(0, %r)\n"
+        "from oracle import qsim_oracle as O\n"
+        "from bench import workload\n"
+        "e,g,b = workload(%d,%d)\n"
+        "t=time.perf_counter()\n"
+        "for _ in range(%d): O.qaoa_expectation_with_grad(%d, e, g, b, 0.5)\n"
+        "print(time.perf_counter()-t)\n" % (ROOT, n_small, p, evals, n_small))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr)
+    sec = float(out.stdout.strip().splitlines()[-1])
+    return evals / sec, sec, 1
+
+
+def cpu_baseline_block(n, n_small, p, evals):
+    rate_small, sec, cores = oracle_sample(n_small, p, evals)
+    scale = 2.0 ** (n_small - n)
+    return {"value": rate_small * scale, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{evals} FP64 oracle eval(s) of the same recipe at {n_small} qubits "
+                      f"({sec:.1f} s, {rate_small:.4g} evals/s), scaled by 2^({n_small}-{n}) to the "
+                      f"{n}-qubit state size (the oracle's cost is linear in 2^n)"}
+
+
+# --------------------------------------------------------------------------- arms
+
+def run_reference(args, ws, rank):
+    """The oracle as it stands on the host cores: each step a bounded sample."""
+    if rank != 0:
+        return
+    n, p = args.n, args.p
+    edges, _, _ = workload(n, p)
+    ns = args.ref_qubits
+    if args.warmup:
+        oracle_sample(ns, p, args.warmup)  # untimed warm-up evaluations
+    rate, sec, cores = oracle_sample(ns, p, args.steps)
+    value = rate * 2.0 ** (ns - n)
+    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(n, p, len(edges)),
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} oracle evals at {ns} qubits ({sec:.1f} s), scaled by "
+                                       f"2^({ns}-{n})"},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+    from paper_2406_17248_gb300 import build
+    build.build()
+    from paper_2406_17248_gb300 import qsim as Q
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    n, p = args.n, args.p
+    edges, gam, bet = workload(n, p)
+    if rank > 0:  # an independent evaluation per replica
+        from paper_2406_17248_gb300 import inputs as I
+        a = I.uniform_params(2 * p, 1000 + rank, 0.0, float(np.pi))
+        gam, bet = a[:p], a[p:]
+    q = Q.QAOA(n, edges, p, gamma_scale=0.5, dtype=Q.C64, tile_bits=args.tile_bits, low_bits=args.low_bits)
+    info = q.info()
+    psi, lam = Q.State(n, Q.C64), Q.State(n, Q.C64)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        q.expectation_with_grad(psi, lam, gam, bet)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: K evaluations, CUDA events on the launching stream
+    clocks = ClockSampler(local)
+    clocks.start()
+    Q.trace_enable(True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        E, dg, db = q.expectation_with_grad(psi, lam, gam, bet)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    Q.trace_enable(False)
+    ms = t0.elapsed_time(t1)
+    clk = clocks.stop()
+    k_ms, k_bytes = Q.trace_read()
+    ms_max = reduce_max(ms, ws)
+    value = ws * args.steps / (ms_max / 1000.0)
+
+    # ---- end to end through the public API with host inputs/outputs, host clock
+    barrier(ws)
+    torch.cuda.synchronize()
+    h0 = time.perf_counter()
+    for _ in range(args.steps):
+        E2, dg2, db2 = q.expectation_with_grad(psi, lam, np.asarray(gam), np.asarray(bet))
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(time.perf_counter() - h0, ws)
+    n_coef = (2 * (len(edges) + 1) + 2) * p
+    h2d = 2 * p * 8 + n_coef * 8
+    d2h = (1 + 2 * p) * 8
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel (tile_pass_kernel): algorithmic bytes / launch time
+    peak, peak_kind = measured_peak_hbm()
+    tile_ms = float(np.sum(k_ms))
+    achieved = float(np.sum(k_bytes)) / (tile_ms / 1000.0) / 1e9 if tile_ms > 0 else None
+    full = k_bytes >= 3.9 * (8 << n)  # reverse passes: load+store of psi and lam
+    full_ach = float(np.sum(k_bytes[full])) / (float(np.sum(k_ms[full])) / 1000.0) / 1e9 if full.any() else None
+    traffic = ncu_traffic_per_launch()
+    launches_per_step = len(k_ms) / max(args.steps, 1) + 2  # + slot reduction and output gather
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(n, p, len(edges)),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs", "kernel": "tile_pass_kernel (all passes of one eval)",
+                     "reverse_pass_achieved": full_ach,
+                     "tile_kernel_share_of_step": tile_ms / ms if ms > 0 else None},
+        "e2e": {"value": ws * args.steps / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "clocks": clk,
+        "plan": info,
+        "energy": E,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_block(n, args.cpu_qubits, p, 1)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=30)
+    ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--tile-bits", type=int, default=0)
+    ap.add_argument("--low-bits", type=int, default=0)
+    ap.add_argument("--cpu-qubits", type=int, default=20)
+    ap.add_argument("--ref-qubits", type=int, default=18)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        import torch.distributed as dist
+        if args.impl == "ours":
+            import torch
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -197,6 +197,18 @@ QS_API qs_status qs_qaoa_expectation(qs_qaoa* q, qs_state* psi, const double* ga
 QS_API qs_status qs_qaoa_expectation_with_grad(qs_qaoa* q, qs_state* psi, qs_state* lam, const double* gamma,
                                         const double* beta, double* energy, double* dgamma, double* dbeta);
 
+/* ----------------------------------------------------------------- tracing */
+
+/* Tracing of the fused tile passes: while enabled, every tile-pass launch is
+ * bracketed by a CUDA event pair recorded on its own stream, together with the
+ * pass's algorithmic HBM bytes (state tiles loaded + stored, plus cut values).
+ * Not part of the paper; it exists to measure the engine.  enable: 1 = start
+ * (clears earlier records), 0 = stop.  At most 65536 launches are kept. */
+QS_API qs_status qs_trace_enable(int enable);
+/* Synchronise the recorded events and copy out up to `max` records: duration in
+ * ms and algorithmic bytes per launch.  *n = number of records copied. */
+QS_API qs_status qs_trace_read(int max, int* n, double* ms, double* bytes);
+
 #ifdef __cplusplus
 }
 #endif

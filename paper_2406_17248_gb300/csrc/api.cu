@@ -380,8 +380,67 @@ qs_status run_passes(const TilePlan& plan, int begin, int end, qs_dtype dt, void
     const bool two = hdr.flags & (PF_LOAD_LAM | PF_STORE_LAM);
     L.grid = (two || hdr.n_slots > 0) ? grid2 : grid1;
     L.stride = grid2;
+    TraceRec* rec = trace_begin(st);
     QS_TRY(launch_tile_pass(dt, plan, i, L, st));
+    if (rec) {
+      const double S = (double)amp_bytes(dt) * (double)(1ull << n);
+      const uint32_t f = hdr.flags;
+      rec->bytes = S * (((f & PF_LOAD_PSI) ? 1 : 0) + ((f & PF_LOAD_LAM) ? 1 : 0) + ((f & PF_STORE_PSI) ? 1 : 0) +
+                        ((f & PF_STORE_LAM) ? 1 : 0)) +
+                   ((f & PF_NEED_CUT) ? (double)(1ull << n) : 0.0);
+      QS_CUDA(cudaEventRecord(rec->end, st));
+    }
   }
+  return QS_OK;
+}
+
+// ---------------------------------------------------------------------------- tracing
+
+static std::mutex g_trace_mu;
+static bool g_trace_on = false;
+static std::vector<TraceRec> g_trace;
+static size_t g_trace_used = 0;
+constexpr size_t kTraceMax = 65536;
+
+TraceRec* trace_begin(cudaStream_t st) {
+  if (!g_trace_on) return nullptr;
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  if (g_trace_used >= kTraceMax) return nullptr;
+  if (g_trace_used == g_trace.size()) {
+    TraceRec r;
+    if (cudaEventCreate(&r.start) != cudaSuccess || cudaEventCreate(&r.end) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return nullptr;
+    }
+    g_trace.push_back(r);
+  }
+  TraceRec* r = &g_trace[g_trace_used++];
+  if (cudaEventRecord(r->start, st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    --g_trace_used;
+    return nullptr;
+  }
+  return r;
+}
+
+qs_status trace_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  g_trace_on = on != 0;
+  if (on) g_trace_used = 0;
+  return QS_OK;
+}
+
+qs_status trace_read(int max, int* n, double* ms, double* bytes) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  const int k = (int)std::min<size_t>(g_trace_used, (size_t)std::max(max, 0));
+  for (int i = 0; i < k; ++i) {
+    QS_CUDA(cudaEventSynchronize(g_trace[i].end));
+    float t = 0;
+    QS_CUDA(cudaEventElapsedTime(&t, g_trace[i].start, g_trace[i].end));
+    if (ms) ms[i] = t;
+    if (bytes) bytes[i] = g_trace[i].bytes;
+  }
+  *n = k;
   return QS_OK;
 }
 
@@ -809,6 +868,13 @@ qs_status qs_expectation_with_grad(qs_state* psi, qs_state* lam, qs_circuit* c, 
   QS_CUDA(cudaStreamSynchronize(st));
   for (int p = c->n_params; p < n_params; ++p) grad[p] = 0.0;
   return QS_OK;
+}
+
+qs_status qs_trace_enable(int enable) { return trace_enable(enable); }
+
+qs_status qs_trace_read(int max, int* n, double* ms, double* bytes) {
+  QS_CHECK(n != nullptr, "n is null");
+  return trace_read(max, n, ms, bytes);
 }
 
 qs_status qs_sample(const qs_state* s_, uint64_t shots, uint64_t seed, uint64_t* out_bits) {

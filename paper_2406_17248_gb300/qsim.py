@@ -62,6 +62,8 @@ SIGNATURES = [
     ("qs_qaoa_evolve", [_VP, _VP, _PD, _PD]),
     ("qs_qaoa_expectation", [_VP, _VP, _PD, _PD, _PD]),
     ("qs_qaoa_expectation_with_grad", [_VP, _VP, _VP, _PD, _PD, _PD, _PD, _PD]),
+    ("qs_trace_enable", [_I]),
+    ("qs_trace_read", [_I, _PI, _PD, _PD]),
 ]
 
 
@@ -283,6 +285,20 @@ def sample(state: State, shots: int, seed: int) -> np.ndarray:
     out = np.zeros(max(shots, 1), dtype=np.uint64)
     _check(lib().qs_sample(state.h, shots, seed, out.ctypes.data_as(_PU64)))
     return out[:shots]
+
+
+def trace_enable(on: bool = True):
+    """Record a CUDA event pair around every tile-pass launch (see qs_trace_enable)."""
+    _check(lib().qs_trace_enable(1 if on else 0))
+
+
+def trace_read(max_records: int = 65536):
+    """(durations in ms, algorithmic bytes) of the recorded tile-pass launches."""
+    ms = np.zeros(max_records)
+    by = np.zeros(max_records)
+    n = C.c_int()
+    _check(lib().qs_trace_read(max_records, C.byref(n), _dptr(ms), _dptr(by)))
+    return ms[: n.value], by[: n.value]
 
 
 # --------------------------------------------------------------------------- QAOA

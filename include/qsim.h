@@ -197,6 +197,28 @@ QS_API qs_status qs_qaoa_expectation(qs_qaoa* q, qs_state* psi, const double* ga
 QS_API qs_status qs_qaoa_expectation_with_grad(qs_qaoa* q, qs_state* psi, qs_state* lam, const double* gamma,
                                         const double* beta, double* energy, double* dgamma, double* dbeta);
 
+/* ------------------------------------------------- allocation-free variant */
+
+/* *energy = <psi|H|psi>, the same Pauli-sum kernel as qs_expectation, for
+ * callers that must not have the library allocate device memory: their device
+ * memory belongs to another allocator (a framework's caching allocator, a pool
+ * reserved at start-up), or they cannot risk the device-wide synchronisation of
+ * cudaFree/cudaMalloc in their loop.  The paper has no counterpart; this is a
+ * deployment variant.
+ *   dev_psi: caller-owned device array of 2^n_qubits amplitudes of `dtype`.
+ *   xmask/zmask/coef: host arrays of n_terms Pauli terms as in qs_ham_create,
+ *   at most 4096 terms (QS_ERR_INVALID_ARG beyond).  energy: host double.
+ * The call allocates no device memory: its working memory is a fixed 256 KiB
+ * array inside the library, held by every device that loads the library until
+ * the process exits.  The first call on a device (with that device current)
+ * looks up the array's device address; make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents;
+ * calls that overlap on the GPU (other host threads, other streams) race on it,
+ * so serialise them.  The call synchronises `cuda_stream` before returning. */
+QS_API qs_status qs_expectation_noalloc(const void* dev_psi, int n_qubits, qs_dtype dtype, int n_terms,
+                                        const uint64_t* xmask, const uint64_t* zmask, const double* coef,
+                                        void* cuda_stream, double* energy);
+
 /* ----------------------------------------------------------------- tracing */
 
 /* Tracing of the fused tile passes: while enabled, every tile-pass launch is

@@ -62,6 +62,7 @@ SIGNATURES = [
     ("qs_qaoa_evolve", [_VP, _VP, _PD, _PD]),
     ("qs_qaoa_expectation", [_VP, _VP, _PD, _PD, _PD]),
     ("qs_qaoa_expectation_with_grad", [_VP, _VP, _VP, _PD, _PD, _PD, _PD, _PD]),
+    ("qs_expectation_noalloc", [_VP, _I, _I, _I, _PU64, _PU64, _PD, _VP, _PD]),
     ("qs_trace_enable", [_I]),
     ("qs_trace_read", [_I, _PI, _PD, _PD]),
 ]
@@ -285,6 +286,20 @@ def sample(state: State, shots: int, seed: int) -> np.ndarray:
     out = np.zeros(max(shots, 1), dtype=np.uint64)
     _check(lib().qs_sample(state.h, shots, seed, out.ctypes.data_as(_PU64)))
     return out[:shots]
+
+
+def expectation_noalloc(state: State, ham: I.PauliSum, stream=None) -> float:
+    """<psi|H|psi> through qs_expectation_noalloc: no device allocation by the
+    library (its working memory is a fixed array inside the library), for callers
+    whose device memory belongs to another allocator."""
+    x = np.ascontiguousarray(ham.xmask, dtype=np.uint64)
+    z = np.ascontiguousarray(ham.zmask, dtype=np.uint64)
+    cf = np.ascontiguousarray(ham.coef, dtype=np.float64)
+    e = C.c_double()
+    _check(lib().qs_expectation_noalloc(C.c_void_p(state.buffer.data_ptr()), state.n, state.dtype, int(cf.size),
+                                        x.ctypes.data_as(_PU64), z.ctypes.data_as(_PU64), _dptr(cf),
+                                        C.c_void_p(_stream_ptr(stream)), C.byref(e)))
+    return e.value
 
 
 def trace_enable(on: bool = True):

@@ -72,27 +72,6 @@ struct qs_ham {
   int n_groups = 0;
 };
 
-struct qs_qaoa {
-  int n = 0, ne = 0, p = 0, n_edges = 0;
-  double gs = 1.0;
-  qs_dtype dt = QS_C64;
-  int m = 0, c = 0;
-  std::vector<int> edges;
-  uint8_t* d_cut = nullptr;
-  int* d_edges = nullptr;
-  TilePlan gplan, eplan;
-  SlotMap gslots, eslots;
-  int n_fwd = 0;  // forward passes before the turnaround pass
-  void* d_coef = nullptr;
-  int n_coef = 0;
-  int *g_row = nullptr, *g_sidx = nullptr, *e_row = nullptr, *e_sidx = nullptr;
-  double *g_w = nullptr, *e_w = nullptr;
-  int grid1 = 1, grid2 = 1;
-  double bytes_per_eval = 0;
-  int rev_passes = 0;
-  std::vector<double> host_coef;
-};
-
 
 namespace qs {
 struct TraceRec {

@@ -22,20 +22,46 @@
 #include <cstring>
 
 #include "handles.h"
+#include "qaoa_pass.h"
 
 using cd = std::complex<double>;
 using namespace qs;
 
+struct qs_qaoa {
+  int n = 0, ne = 0, p = 0, n_edges = 0;
+  double gs = 1.0;
+  qs_dtype dt = QS_C64;
+  int m = 0, c = 0;
+  uint8_t* d_cut = nullptr;
+  int* d_edges = nullptr;
+  std::vector<QPassDesc> gpass, epass;  // gradient plan, energy plan
+  std::vector<int> gns, ens;            // states carried by each pass (1 or 2)
+  QPassDesc* d_gpass = nullptr;
+  QPassDesc* d_epass = nullptr;
+  SlotMap gslots, eslots;
+  int n_fwd = 0, rev_passes = 0;
+  void* d_coef = nullptr;
+  int n_coef = 0;
+  int *g_row = nullptr, *g_sidx = nullptr, *e_row = nullptr, *e_sidx = nullptr;
+  double *g_w = nullptr, *e_w = nullptr;
+  int grid1 = 1, grid2 = 1;
+  double bytes_per_eval = 0;
+  std::vector<double> host_coef;
+};
+
 namespace {
 
-struct SchedOp {
-  int type;  // 0 = RX(layer, bit), 1 = COST(layer)
+// ---------------------------------------------------------------------------- schedule
+
+enum QOpKind { QO_RX, QO_COST, QO_GRAD_RX, QO_GRAD_COST, QO_ENERGY };
+struct QOp {
+  int kind;
   int layer;
   int bit;
 };
 struct SchedPass {
   uint64_t S;
-  std::vector<SchedOp> ops;
+  std::vector<QOp> ops;  // forward ops (QO_RX, QO_COST)
 };
 
 inline int popc(uint64_t x) { return __builtin_popcountll(x); }
@@ -48,12 +74,11 @@ std::vector<SchedPass> make_schedule(int n, int p, int m, int c) {
     for (int q = 0; q < n && popc(S) < m; ++q) S |= 1ull << q;
     return S;
   };
-  // first pass: cost 0 then mixer 0 on the lowest m bits
   SchedPass first;
   first.S = fill(low);
-  first.ops.push_back({1, 0, -1});
+  first.ops.push_back({QO_COST, 0, -1});
   for (int q = 0; q < n; ++q)
-    if ((first.S >> q) & 1) first.ops.push_back({0, 0, q});
+    if ((first.S >> q) & 1) first.ops.push_back({QO_RX, 0, q});
   passes.push_back(first);
   int layer = 0;
   uint64_t done = first.S;
@@ -63,12 +88,12 @@ std::vector<SchedPass> make_schedule(int n, int p, int m, int c) {
     if (popc(U | low) <= m) {
       P.S = fill(U | low);
       for (int q = 0; q < n; ++q)
-        if ((U >> q) & 1) P.ops.push_back({0, layer, q});
+        if ((U >> q) & 1) P.ops.push_back({QO_RX, layer, q});
       if (layer + 1 < p) {
         ++layer;
-        P.ops.push_back({1, layer, -1});
+        P.ops.push_back({QO_COST, layer, -1});
         for (int q = 0; q < n; ++q)
-          if ((P.S >> q) & 1) P.ops.push_back({0, layer, q});
+          if ((P.S >> q) & 1) P.ops.push_back({QO_RX, layer, q});
         done = P.S;
       } else {
         done = all;
@@ -79,7 +104,7 @@ std::vector<SchedPass> make_schedule(int n, int p, int m, int c) {
         if ((U >> q) & 1) S |= 1ull << q;
       P.S = S;
       for (int q = 0; q < n; ++q)
-        if (((U & S) >> q) & 1) P.ops.push_back({0, layer, q});
+        if (((U & S) >> q) & 1) P.ops.push_back({QO_RX, layer, q});
       done |= U & S;
     }
     passes.push_back(P);
@@ -87,15 +112,238 @@ std::vector<SchedPass> make_schedule(int n, int p, int m, int c) {
   return passes;
 }
 
+std::vector<QOp> reverse_ops(const std::vector<QOp>& fwd) {
+  std::vector<QOp> r;
+  for (size_t i = fwd.size(); i-- > 0;) {
+    const QOp& o = fwd[i];
+    r.push_back({o.kind == QO_RX ? QO_GRAD_RX : QO_GRAD_COST, o.layer, o.bit});
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------- pass builder
+
+// Order of the sub-cube bits.  Threads of a half-warp (complex64, 8-byte
+// accesses) or quarter-warp (complex128) take consecutive sub-cubes, so the
+// lowest sub-cube bits should spread their accesses over distinct bank slots:
+// with the chunk swizzle, chunk bit b lands on slot bit b mod 3, and for
+// complex64 local bit 0 picks the half of a chunk.
+std::vector<int> order_q(const std::vector<int>& rest, bool c64) {
+  std::vector<int> q, tail;
+  std::vector<char> used(rest.size(), 0);
+  if (c64)
+    for (size_t i = 0; i < rest.size(); ++i)
+      if (rest[i] == 0) {
+        q.push_back(0);
+        used[i] = 1;
+      }
+  for (int r = 0; r < 3; ++r)
+    for (size_t i = 0; i < rest.size(); ++i) {
+      const int chunk_bit = c64 ? rest[i] - 1 : rest[i];
+      if (!used[i] && chunk_bit >= 0 && chunk_bit % 3 == r) {
+        q.push_back(rest[i]);
+        used[i] = 1;
+        break;
+      }
+    }
+  std::sort(q.begin(), q.end());
+  for (size_t i = 0; i < rest.size(); ++i)
+    if (!used[i]) tail.push_back(rest[i]);
+  q.insert(q.end(), tail.begin(), tail.end());
+  return q;
+}
+
+struct QBuild {
+  int n, m, c, p;
+  double gs;
+  qs_dtype dt;
+};
+
+// Outputs: 0 = E, 1 + l = dgamma_l, 1 + p + l = dbeta_l.
+qs_status build_qpass(const QBuild& B, uint64_t S, const std::vector<QOp>& ops, uint32_t flags, QPassDesc* out,
+                      SlotMap* slots) {
+  QPassDesc D;
+  std::memset(&D, 0, sizeof(D));
+  D.m = B.m;
+  D.c = B.c;
+  D.flags = flags;
+  D.plus_amp = std::pow(2.0, -0.5 * B.n);
+  int local_of[64], global_of[16], k = 0;
+  for (int q = 0; q < 64; ++q) local_of[q] = -1;
+  for (int q = 0; q < B.n; ++q)
+    if ((S >> q) & 1) {
+      local_of[q] = k;
+      global_of[k++] = q;
+    } else {
+      D.comp[D.ncomp++] = (int8_t)q;
+    }
+  for (int i = 0; i < 64; ++i) {
+    uint64_t a = 0, b = 0;
+    for (int j = 0; j < 6; ++j)
+      if ((i >> j) & 1) {
+        if (B.c + j < B.m) a |= 1ull << global_of[B.c + j];
+        if (B.c + 6 + j < B.m) b |= 1ull << global_of[B.c + 6 + j];
+      }
+    D.hiA[i] = a;
+    D.hiB[i] = b;
+  }
+  int lo = 1 << 30, hi = -1;
+  for (const QOp& o : ops) {
+    lo = std::min(lo, o.layer);
+    hi = std::max(hi, o.layer);
+  }
+  if (hi - lo + 1 > kQaoaMaxLayersPerPass) {
+    set_error("qaoa planner: a pass spans more than two layers (internal error)");
+    return QS_ERR_UNSUPPORTED;
+  }
+  D.layer_lo = lo;
+  D.n_layers = hi - lo + 1;
+  std::vector<int> acc_out;
+  std::vector<double> acc_w;
+  auto acc_of = [&](int o, double w) {
+    for (size_t i = 0; i < acc_out.size(); ++i)
+      if (acc_out[i] == o) return (int)i;
+    acc_out.push_back(o);
+    acc_w.push_back(w);
+    return (int)acc_out.size() - 1;
+  };
+  // Phases hold up to 4 distinct RX bits.  A layer's block of RX ops is
+  // reordered (RX on distinct qubits commute) to start with the bits already
+  // held in registers by the current phase.
+  std::vector<std::vector<int>> phase_bits(1);
+  std::vector<std::vector<QStep>> phase_steps(1);
+  size_t i = 0;
+  while (i < ops.size()) {
+    const QOp o = ops[i];
+    if (o.kind == QO_RX || o.kind == QO_GRAD_RX) {
+      size_t j = i;
+      while (j < ops.size() && ops[j].kind == o.kind && ops[j].layer == o.layer) ++j;
+      std::vector<int> block;
+      for (size_t t = i; t < j; ++t) block.push_back(ops[t].bit);
+      const std::vector<int> cur0 = phase_bits.back();
+      std::stable_sort(block.begin(), block.end(), [&](int a, int b) {
+        const bool ia = std::find(cur0.begin(), cur0.end(), a) != cur0.end();
+        const bool ib = std::find(cur0.begin(), cur0.end(), b) != cur0.end();
+        return ia > ib;
+      });
+      const uint8_t ty = o.kind == QO_RX ? QST_RX : QST_GRAD_RX;
+      for (int bit : block) {
+        auto* cur = &phase_bits.back();
+        auto it = std::find(cur->begin(), cur->end(), bit);
+        if (it == cur->end()) {
+          if (cur->size() == 4 || phase_steps.back().size() >= (size_t)kQaoaMaxSteps) {
+            phase_bits.emplace_back();
+            phase_steps.emplace_back();
+            cur = &phase_bits.back();
+          }
+          cur->push_back(bit);
+          it = cur->end() - 1;
+        }
+        const int rb = (int)(it - cur->begin());
+        auto& steps = phase_steps.back();
+        if (!steps.empty() && steps.back().type == ty && steps.back().layer == o.layer - lo &&
+            !(steps.back().mask & (1 << rb))) {
+          steps.back().mask |= (uint8_t)(1 << rb);
+        } else {
+          if (steps.size() >= (size_t)kQaoaMaxSteps) {
+            set_error("qaoa planner: too many steps in a phase (internal error)");
+            return QS_ERR_UNSUPPORTED;
+          }
+          QStep st;
+          std::memset(&st, 0, sizeof(st));
+          st.type = ty;
+          st.mask = (uint8_t)(1 << rb);
+          st.layer = (uint16_t)(o.layer - lo);
+          if (ty == QST_GRAD_RX) {
+            st.acc = (uint8_t)acc_of(1 + B.p + o.layer, 1.0);
+            st.flags = QSF_DAG | QSF_LAM;
+          }
+          steps.push_back(st);
+        }
+      }
+      i = j;
+      continue;
+    }
+    if (phase_steps.back().size() >= (size_t)kQaoaMaxSteps) {
+      phase_bits.emplace_back();
+      phase_steps.emplace_back();
+    }
+    QStep st;
+    std::memset(&st, 0, sizeof(st));
+    st.layer = (uint16_t)(o.layer - lo);
+    if (o.kind == QO_COST) {
+      st.type = QST_COST;
+    } else if (o.kind == QO_GRAD_COST) {
+      st.type = QST_GRAD_COST;
+      st.flags = QSF_LAM;
+      st.acc = (uint8_t)acc_of(1 + o.layer, 2.0 * B.gs);
+    } else {
+      st.type = QST_ENERGY;
+      st.acc = (uint8_t)acc_of(0, 1.0);
+    }
+    phase_steps.back().push_back(st);
+    ++i;
+  }
+  if (acc_out.size() > (size_t)kQaoaMaxAcc || phase_bits.size() > (size_t)kQaoaMaxPhases) {
+    set_error("qaoa planner: pass exceeds accumulator/phase limits (internal error)");
+    return QS_ERR_UNSUPPORTED;
+  }
+  const bool el8 = B.dt == QS_C64;  // 8-byte amplitudes, two per swizzled 16-byte chunk
+  D.n_phases = (int)phase_bits.size();
+  for (int ph = 0; ph < D.n_phases; ++ph) {
+    QPhase& P = D.phases[ph];
+    uint32_t R = 0;
+    int ri = 0;
+    for (int bit : phase_bits[ph]) {
+      P.R[ri++] = (int8_t)local_of[bit];
+      R |= 1u << local_of[bit];
+    }
+    for (int l = 0; l < B.m && ri < 4; ++l)
+      if (!((R >> l) & 1)) {
+        P.R[ri++] = (int8_t)l;
+        R |= 1u << l;
+      }
+    std::vector<int> rest;
+    for (int l = 0; l < B.m; ++l)
+      if (!((R >> l) & 1)) rest.push_back(l);
+    const std::vector<int> q = order_q(rest, el8);
+    P.nq = (int8_t)q.size();
+    for (size_t t = 0; t < q.size(); ++t) {
+      P.Q[t] = (int8_t)q[t];
+      P.sq[t] = (uint16_t)qaoa_swizzle(el8, 1u << q[t]);
+    }
+    for (int r = 0; r < 4; ++r) P.sreg[r] = (uint16_t)qaoa_swizzle(el8, 1u << P.R[r]);
+    P.n_steps = (int8_t)phase_steps[ph].size();
+    P.need_cut = 0;
+    for (size_t t = 0; t < phase_steps[ph].size(); ++t) {
+      P.steps[t] = phase_steps[ph][t];
+      const uint8_t ty = phase_steps[ph][t].type;
+      if (ty == QST_COST || ty == QST_GRAD_COST || ty == QST_ENERGY) P.need_cut = 1;
+    }
+  }
+  D.n_acc = (int)acc_out.size();
+  D.slot_base = (int)slots->out.size();
+  for (size_t a = 0; a < acc_out.size(); ++a) {
+    slots->out.push_back(acc_out[a]);
+    slots->weight.push_back(acc_w[a]);
+  }
+  *out = D;
+  return QS_OK;
+}
+
+uint32_t cut_flag(const std::vector<QOp>& ops) {
+  for (const auto& o : ops)
+    if (o.kind != QO_RX && o.kind != QO_GRAD_RX) return PF_NEED_CUT;
+  return 0;
+}
+
 struct CoefLayout {
   int per_layer, lut, lut_dag, rx, rx_dag;
-  int n_edges;
   int at(int l, int which) const { return l * per_layer + which; }
 };
 
 CoefLayout layout_for(int n_edges) {
   CoefLayout L;
-  L.n_edges = n_edges;
   L.lut = 0;
   L.lut_dag = n_edges + 1;
   L.rx = 2 * (n_edges + 1);
@@ -104,60 +352,10 @@ CoefLayout layout_for(int n_edges) {
   return L;
 }
 
-PlanItem rx_item(int bit, std::vector<ItemOp> ops) {
-  PlanItem it;
-  it.kind = IK_DENSE1;
-  it.nt = 1;
-  it.t[0] = it.t[1] = bit;
-  it.ctrl = 0;
-  it.touched = 1ull << bit;
-  it.ops = std::move(ops);
-  return it;
-}
-
-PlanItem global_item(uint64_t all, std::vector<ItemOp> ops) {
-  PlanItem it;
-  it.kind = IK_GLOBAL_DIAG;
-  it.nt = 0;
-  it.t[0] = it.t[1] = 0;
-  it.ctrl = 0;
-  it.touched = all;
-  it.ops = std::move(ops);
-  return it;
-}
-
-// Forward items of one scheduled pass.
-std::vector<PlanItem> fwd_items(const SchedPass& sp, const CoefLayout& L, uint64_t all) {
-  std::vector<PlanItem> v;
-  for (const SchedOp& o : sp.ops) {
-    if (o.type == 0)
-      v.push_back(rx_item(o.bit, {ItemOp{OP_RX, 0, L.at(o.layer, L.rx), -1, 0}}));
-    else
-      v.push_back(global_item(all, {ItemOp{OP_COST, 0, L.at(o.layer, L.lut), -1, 0}}));
-  }
-  return v;
-}
-
-// Reverse items (adjoint of the pass, with gradient ops) in reverse order.
-// Outputs: 0 = E, 1 + l = dgamma_l, 1 + p + l = dbeta_l.
-std::vector<PlanItem> rev_items(const SchedPass& sp, const CoefLayout& L, uint64_t all, int p, double gs) {
-  std::vector<PlanItem> v;
-  for (size_t i = sp.ops.size(); i-- > 0;) {
-    const SchedOp& o = sp.ops[i];
-    if (o.type == 0)
-      v.push_back(rx_item(o.bit, {ItemOp{OP_GRADX, 0, 0, 1 + p + o.layer, 1.0},
-                                  ItemOp{OP_RX, OPF_LAM, L.at(o.layer, L.rx_dag), -1, 0}}));
-    else
-      v.push_back(global_item(all, {ItemOp{OP_GRADCOST, 0, 0, 1 + o.layer, 2.0 * gs},
-                                    ItemOp{OP_COST, OPF_LAM, L.at(o.layer, L.lut_dag), -1, 0}}));
-  }
-  return v;
-}
-
-uint32_t cut_flag(const SchedPass& sp) {
-  for (const auto& o : sp.ops)
-    if (o.type == 1) return PF_NEED_CUT;
-  return 0;
+double pass_bytes(uint32_t f, double S, double N) {
+  return S * (((f & PF_LOAD_PSI) ? 1 : 0) + ((f & PF_LOAD_LAM) ? 1 : 0) + ((f & PF_STORE_PSI) ? 1 : 0) +
+              ((f & PF_STORE_LAM) ? 1 : 0)) +
+         ((f & PF_NEED_CUT) ? N : 0.0);
 }
 
 }  // namespace
@@ -174,30 +372,33 @@ qs_status qs_qaoa_create(int n_qubits, const int* edges, int n_edges, int p, dou
   QS_CHECK(dtype == QS_C64 || dtype == QS_C128, "invalid dtype");
   std::vector<std::pair<int, int>> es;
   for (int e = 0; e < n_edges; ++e) {
-    int a = edges[2 * e], b = edges[2 * e + 1];
+    const int a = edges[2 * e], b = edges[2 * e + 1];
     QS_CHECK(a >= 0 && a < n_qubits && b >= 0 && b < n_qubits && a != b, "edge endpoint out of range or a self-loop");
     es.push_back({std::min(a, b), std::max(a, b)});
   }
-  std::vector<std::pair<int, int>> sorted = es;
-  std::sort(sorted.begin(), sorted.end());
-  QS_CHECK(std::adjacent_find(sorted.begin(), sorted.end()) == sorted.end(), "repeated edge");
+  std::sort(es.begin(), es.end());
+  QS_CHECK(std::adjacent_find(es.begin(), es.end()) == es.end(), "repeated edge");
+  if (opts) {
+    QS_CHECK(opts->tile_bits == 0 || (opts->tile_bits >= kMinTileBits && opts->tile_bits <= kMaxTileBits),
+             "tile_bits must be 0 or 6..13");
+    QS_CHECK(opts->low_bits >= 0 && opts->low_bits <= kMaxTileBits, "low_bits must be 0..13");
+  }
 
   qs_qaoa* q = new qs_qaoa;
   q->n = n_qubits;
-  q->ne = std::max(n_qubits, kRegBits);
+  q->ne = n_qubits;
   q->p = p;
   q->n_edges = n_edges;
   q->gs = gamma_scale;
   q->dt = dtype;
-  q->edges.assign(edges, edges + 2 * n_edges);
   int mm = (opts && opts->tile_bits) ? opts->tile_bits : (dtype == QS_C64 ? 12 : 11);
-  mm = std::max(kRegBits, std::min({mm, max_tile_bits(dtype), q->ne}));
+  // double-buffered psi + lam tiles must fit twice in shared memory
+  mm = std::max(kRegBits, std::min({mm, dtype == QS_C64 ? 12 : 11, q->n}));
   int cc = (opts && opts->low_bits) ? opts->low_bits : 0;
-  if (cc == 0) {
-    // fewest passes; ties go to more contiguous bits
+  if (cc == 0) {  // fewest passes; ties go to more contiguous bits
     int best = 1 << 30;
     for (int c = 2; c <= std::min(6, mm); ++c) {
-      const int np = (int)make_schedule(q->ne, p, mm, c).size();
+      const int np = (int)make_schedule(q->n, p, mm, c).size();
       if (np <= best) {
         best = np;
         cc = c;
@@ -213,78 +414,82 @@ qs_status qs_qaoa_create(int n_qubits, const int* edges, int n_edges, int p, dou
     qs_qaoa_destroy(q);
     return s;
   };
-  const uint64_t N = 1ull << q->ne;
+  const uint64_t N = 1ull << q->n;
   cudaError_t e = cudaMalloc(&q->d_cut, N);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(cut values)"));
   e = cudaMalloc(&q->d_edges, sizeof(int) * 2 * n_edges);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(edges)"));
   e = cudaMemcpy(q->d_edges, edges, sizeof(int) * 2 * n_edges, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy(edges)"));
-  qs_status s = launch_cut_values(q->d_cut, q->ne, q->d_edges, n_edges, nullptr);
+  qs_status s = launch_cut_values(q->d_cut, q->n, q->d_edges, n_edges, nullptr);
   if (s != QS_OK) return fail(s);
-
   const CoefLayout L = layout_for(n_edges);
   q->n_coef = L.per_layer * p;
   e = cudaMalloc(&q->d_coef, (size_t)q->n_coef * 16);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(coefficients)"));
 
-  const std::vector<SchedPass> sched = make_schedule(q->ne, p, mm, cc);
+  const std::vector<SchedPass> sched = make_schedule(q->n, p, mm, cc);
   const int K = (int)sched.size();
-  const uint64_t all = (1ull << q->ne) - 1;
-  PlanParams pp{q->ne, mm, cc, dtype};
-
-  // gradient plan: forward passes 0..K-2, turnaround K-1, reverse K-2..0
+  const QBuild B{q->n, mm, cc, p, gamma_scale, dtype};
+  QPassDesc D;
+  // gradient plan: forward 0..K-2, turnaround K-1, reverse K-2..0
   for (int i = 0; i < K - 1; ++i) {
-    const uint32_t fl = (i == 0 ? PF_GEN_PLUS : PF_LOAD_PSI) | PF_STORE_PSI | cut_flag(sched[i]);
-    s = plan_single_pass(fwd_items(sched[i], L, all), sched[i].S, pp, fl, &q->gplan, &q->gslots);
-    if (s != QS_OK) return fail(s);
+    const uint32_t fl = (i == 0 ? PF_GEN_PLUS : PF_LOAD_PSI) | PF_STORE_PSI | cut_flag(sched[i].ops);
+    if ((s = build_qpass(B, sched[i].S, sched[i].ops, fl, &D, &q->gslots)) != QS_OK) return fail(s);
+    q->gpass.push_back(D);
+    q->gns.push_back(1);
   }
   {
-    std::vector<PlanItem> items = fwd_items(sched[K - 1], L, all);
-    items.push_back(global_item(all, {ItemOp{OP_ENERGY, 0, 0, 0, 1.0}}));
-    std::vector<PlanItem> r = rev_items(sched[K - 1], L, all, p, gamma_scale);
-    items.insert(items.end(), r.begin(), r.end());
+    std::vector<QOp> ops = sched[K - 1].ops;
+    ops.push_back({QO_ENERGY, sched[K - 1].ops.back().layer, -1});
+    const std::vector<QOp> r = reverse_ops(sched[K - 1].ops);
+    ops.insert(ops.end(), r.begin(), r.end());
     const uint32_t fl = (K == 1 ? PF_GEN_PLUS : PF_LOAD_PSI) | PF_STORE_LAM | PF_NEED_CUT;
-    s = plan_single_pass(items, sched[K - 1].S, pp, fl, &q->gplan, &q->gslots);
-    if (s != QS_OK) return fail(s);
+    if ((s = build_qpass(B, sched[K - 1].S, ops, fl, &D, &q->gslots)) != QS_OK) return fail(s);
+    q->gpass.push_back(D);
+    q->gns.push_back(2);
   }
   for (int i = K - 2; i >= 0; --i) {
+    const std::vector<QOp> r = reverse_ops(sched[i].ops);
     const uint32_t st = i > 0 ? (PF_STORE_PSI | PF_STORE_LAM) : 0;
-    const uint32_t fl = PF_LOAD_PSI | PF_LOAD_LAM | st | cut_flag(sched[i]);
-    s = plan_single_pass(rev_items(sched[i], L, all, p, gamma_scale), sched[i].S, pp, fl, &q->gplan, &q->gslots);
-    if (s != QS_OK) return fail(s);
+    const uint32_t fl = PF_LOAD_PSI | PF_LOAD_LAM | st | cut_flag(r);
+    if ((s = build_qpass(B, sched[i].S, r, fl, &D, &q->gslots)) != QS_OK) return fail(s);
+    q->gpass.push_back(D);
+    q->gns.push_back(2);
   }
   q->n_fwd = K - 1;
   q->rev_passes = K - 1;
-  // energy plan: forward passes with the energy op appended to the last
+  // energy plan: the forward passes with the energy appended to the last
   for (int i = 0; i < K; ++i) {
-    std::vector<PlanItem> items = fwd_items(sched[i], L, all);
-    uint32_t fl = (i == 0 ? PF_GEN_PLUS : PF_LOAD_PSI) | PF_STORE_PSI | cut_flag(sched[i]);
+    std::vector<QOp> ops = sched[i].ops;
+    uint32_t fl = (i == 0 ? PF_GEN_PLUS : PF_LOAD_PSI) | PF_STORE_PSI | cut_flag(ops);
     if (i == K - 1) {
-      items.push_back(global_item(all, {ItemOp{OP_ENERGY, 0, 0, 0, 1.0}}));
+      ops.push_back({QO_ENERGY, ops.back().layer, -1});
       fl |= PF_NEED_CUT;
     }
-    s = plan_single_pass(items, sched[i].S, pp, fl, &q->eplan, &q->eslots);
-    if (s != QS_OK) return fail(s);
+    if ((s = build_qpass(B, sched[i].S, ops, fl, &D, &q->eslots)) != QS_OK) return fail(s);
+    q->epass.push_back(D);
+    q->ens.push_back(1);
   }
-  s = q->gplan.upload(nullptr);
-  if (s == QS_OK) s = q->eplan.upload(nullptr);
-  if (s == QS_OK) s = build_csr(q->gslots, 1 + 2 * p, &q->g_row, &q->g_sidx, &q->g_w, nullptr);
+  e = cudaMalloc(&q->d_gpass, q->gpass.size() * sizeof(QPassDesc));
+  if (e == cudaSuccess) e = cudaMalloc(&q->d_epass, q->epass.size() * sizeof(QPassDesc));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(q->d_gpass, q->gpass.data(), q->gpass.size() * sizeof(QPassDesc), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(q->d_epass, q->epass.data(), q->epass.size() * sizeof(QPassDesc), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "uploading the QAOA plan"));
+  s = build_csr(q->gslots, 1 + 2 * p, &q->g_row, &q->g_sidx, &q->g_w, nullptr);
   if (s == QS_OK) s = build_csr(q->eslots, 1, &q->e_row, &q->e_sidx, &q->e_w, nullptr);
   if (s != QS_OK) return fail(s);
-  const uint64_t n_tiles = 1ull << (q->ne - mm);
-  q->grid1 = tile_grid_size(dtype, mm, 1, (int)std::min<uint64_t>(n_tiles, 1u << 30));
-  q->grid2 = tile_grid_size(dtype, mm, 2, (int)std::min<uint64_t>(n_tiles, 1u << 30));
-  // planned HBM traffic of one gradient evaluation (state reads + writes and cut reads)
-  const double S = (double)amp_bytes(dtype) * (double)N;
-  double bytes = 0;
-  for (const auto& pass : q->gplan.passes) {
-    const uint32_t f = pass.hdr.flags;
-    bytes += S * (((f & PF_LOAD_PSI) ? 1 : 0) + ((f & PF_LOAD_LAM) ? 1 : 0) + ((f & PF_STORE_PSI) ? 1 : 0) +
-                  ((f & PF_STORE_LAM) ? 1 : 0));
-    if (f & PF_NEED_CUT) bytes += (double)N;
+  const uint64_t n_tiles = 1ull << (q->n - mm);
+  q->grid1 = qaoa_grid_size(dtype, mm, 1, n_edges, n_tiles);
+  q->grid2 = qaoa_grid_size(dtype, mm, 2, n_edges, n_tiles);
+  if (q->grid1 < 1 || q->grid2 < 1) {
+    set_error("qaoa: the tile does not fit in shared memory");
+    return fail(QS_ERR_UNSUPPORTED);
   }
-  q->bytes_per_eval = bytes;
+  const double Sb = (double)amp_bytes(dtype) * (double)N;
+  for (const auto& P : q->gpass) q->bytes_per_eval += pass_bytes(P.flags, Sb, (double)N);
   *out = q;
   return QS_OK;
 }
@@ -292,11 +497,11 @@ qs_status qs_qaoa_create(int n_qubits, const int* edges, int n_edges, int p, dou
 qs_status qs_qaoa_destroy(qs_qaoa* q) {
   if (!q) return QS_OK;
   cudaDeviceSynchronize();
-  q->gplan.free_device();
-  q->eplan.free_device();
   if (q->d_cut) cudaFree(q->d_cut);
   if (q->d_edges) cudaFree(q->d_edges);
   if (q->d_coef) cudaFree(q->d_coef);
+  if (q->d_gpass) cudaFree(q->d_gpass);
+  if (q->d_epass) cudaFree(q->d_epass);
   for (int* pi : {q->g_row, q->g_sidx, q->e_row, q->e_sidx})
     if (pi) cudaFree(pi);
   for (double* pd : {q->g_w, q->e_w})
@@ -348,6 +553,30 @@ qs_status qaoa_check(qs_qaoa* q, qs_state* psi, const double* gamma, const doubl
   return QS_OK;
 }
 
+qs_status run_qpasses(qs_qaoa* q, const std::vector<QPassDesc>& passes, const std::vector<int>& ns,
+                      const QPassDesc* d_passes, void* psi, void* lam, double* partials, cudaStream_t st) {
+  for (size_t i = 0; i < passes.size(); ++i) {
+    QaoaLaunch L;
+    L.psi = psi;
+    L.lam = lam;
+    L.coef = q->d_coef;
+    L.cut = q->d_cut;
+    L.partials = partials;
+    L.n = q->n;
+    L.n_edges = q->n_edges;
+    L.stride = q->grid2;
+    L.grid = (ns[i] == 2 || passes[i].n_acc > 0) ? q->grid2 : q->grid1;
+    TraceRec* rec = trace_begin(st);
+    QS_TRY(launch_qaoa_pass(q->dt, d_passes + i, ns[i], q->m, L, st));
+    if (rec) {
+      rec->bytes = pass_bytes(passes[i].flags, (double)amp_bytes(q->dt) * (double)(1ull << q->n),
+                              (double)(1ull << q->n));
+      QS_CUDA(cudaEventRecord(rec->end, st));
+    }
+  }
+  return QS_OK;
+}
+
 qs_status qaoa_energy(qs_qaoa* q, qs_state* psi, const double* gamma, const double* beta, double* energy) {
   QS_TRY(qaoa_check(q, psi, gamma, beta));
   cudaStream_t st = psi->st;
@@ -359,8 +588,7 @@ qs_status qaoa_energy(qs_qaoa* q, qs_state* psi, const double* gamma, const doub
   double* d_part = psi->scratch;
   double* d_slot = d_part + part;
   double* d_out = d_slot + n_slots;
-  QS_TRY(run_passes(q->eplan, 0, (int)q->eplan.passes.size(), q->dt, psi->ptr, nullptr, q->d_coef, q->d_cut, d_part,
-                    q->ne, q->n_edges, q->grid1, q->grid2, st));
+  QS_TRY(run_qpasses(q, q->epass, q->ens, q->d_epass, psi->ptr, nullptr, d_part, st));
   QS_TRY(launch_reduce_slots(d_part, n_slots, q->grid2, nullptr, d_slot, st));
   QS_TRY(launch_param_gather(d_slot, q->e_row, q->e_sidx, q->e_w, 1, d_out, st));
   if (energy) {
@@ -401,8 +629,7 @@ qs_status qs_qaoa_expectation_with_grad(qs_qaoa* q, qs_state* psi, qs_state* lam
   double* d_part = psi->scratch;
   double* d_slot = d_part + part;
   double* d_out = d_slot + n_slots;
-  QS_TRY(run_passes(q->gplan, 0, (int)q->gplan.passes.size(), q->dt, psi->ptr, lam->ptr, q->d_coef, q->d_cut, d_part,
-                    q->ne, q->n_edges, q->grid1, q->grid2, st));
+  QS_TRY(run_qpasses(q, q->gpass, q->gns, q->d_gpass, psi->ptr, lam->ptr, d_part, st));
   QS_TRY(launch_reduce_slots(d_part, n_slots, q->grid2, nullptr, d_slot, st));
   QS_TRY(launch_param_gather(d_slot, q->g_row, q->g_sidx, q->g_w, n_out, d_out, st));
   std::vector<double> h(n_out);

@@ -47,6 +47,10 @@ struct qs_qaoa {
   int grid1 = 1, grid2 = 1;
   double bytes_per_eval = 0;
   std::vector<double> host_coef;
+  // complex64 reverse sweep on interleaved (psi, lam): the lam state's buffer
+  // holds the first half of the amplitudes and this private buffer the second
+  bool il = false;
+  void* d_il_priv = nullptr;
 };
 
 namespace {
@@ -288,7 +292,9 @@ qs_status build_qpass(const QBuild& B, uint64_t S, const std::vector<QOp>& ops, 
     set_error("qaoa planner: pass exceeds accumulator/phase limits (internal error)");
     return QS_ERR_UNSUPPORTED;
   }
-  const bool el8 = B.dt == QS_C64;  // 8-byte amplitudes, two per swizzled 16-byte chunk
+  // shared-memory elements: 8-byte complex64 amplitudes (two per swizzled
+  // 16-byte chunk), or 16 bytes (complex128, or interleaved complex64 psi/lam)
+  const bool el8 = B.dt == QS_C64 && !(flags & PF_LOAD_IL);
   D.n_phases = (int)phase_bits.size();
   for (int ph = 0; ph < D.n_phases; ++ph) {
     QPhase& P = D.phases[ph];
@@ -354,7 +360,7 @@ CoefLayout layout_for(int n_edges) {
 
 double pass_bytes(uint32_t f, double S, double N) {
   return S * (((f & PF_LOAD_PSI) ? 1 : 0) + ((f & PF_LOAD_LAM) ? 1 : 0) + ((f & PF_STORE_PSI) ? 1 : 0) +
-              ((f & PF_STORE_LAM) ? 1 : 0)) +
+              ((f & PF_STORE_LAM) ? 1 : 0) + ((f & PF_LOAD_IL) ? 2 : 0) + ((f & PF_STORE_IL) ? 2 : 0)) +
          ((f & PF_NEED_CUT) ? N : 0.0);
 }
 
@@ -409,6 +415,14 @@ qs_status qs_qaoa_create(int n_qubits, const int* edges, int n_edges, int p, dou
   if (mm - cc > 12) cc = mm - 12;
   q->m = mm;
   q->c = cc;
+  if (dtype == QS_C64 && q->n >= 5 && qaoa_il_grid_size(mm, n_edges, 1ull << (q->n - mm)) > 0) {
+    // the interleaved reverse sweep needs a buffer the size of one state; without
+    // it the engine runs the reverse passes on separate psi and lam tiles
+    if (cudaMalloc(&q->d_il_priv, (size_t)8 << q->n) == cudaSuccess)
+      q->il = true;
+    else
+      (void)cudaGetLastError();
+  }
 
   auto fail = [&](qs_status s) {
     qs_qaoa_destroy(q);
@@ -444,7 +458,8 @@ qs_status qs_qaoa_create(int n_qubits, const int* edges, int n_edges, int p, dou
     ops.push_back({QO_ENERGY, sched[K - 1].ops.back().layer, -1});
     const std::vector<QOp> r = reverse_ops(sched[K - 1].ops);
     ops.insert(ops.end(), r.begin(), r.end());
-    const uint32_t fl = (K == 1 ? PF_GEN_PLUS : PF_LOAD_PSI) | PF_STORE_LAM | PF_NEED_CUT;
+    const uint32_t out = (q->il && K > 1) ? PF_STORE_IL : PF_STORE_LAM;
+    const uint32_t fl = (K == 1 ? PF_GEN_PLUS : PF_LOAD_PSI) | out | PF_NEED_CUT;
     if ((s = build_qpass(B, sched[K - 1].S, ops, fl, &D, &q->gslots)) != QS_OK) return fail(s);
     q->gpass.push_back(D);
     q->gns.push_back(2);
@@ -452,7 +467,8 @@ qs_status qs_qaoa_create(int n_qubits, const int* edges, int n_edges, int p, dou
   for (int i = K - 2; i >= 0; --i) {
     const std::vector<QOp> r = reverse_ops(sched[i].ops);
     const uint32_t st = i > 0 ? (PF_STORE_PSI | PF_STORE_LAM) : 0;
-    const uint32_t fl = PF_LOAD_PSI | PF_LOAD_LAM | st | cut_flag(r);
+    const uint32_t fl = q->il ? (PF_LOAD_IL | (i > 0 ? PF_STORE_IL : 0u) | cut_flag(r))
+                              : (PF_LOAD_PSI | PF_LOAD_LAM | st | cut_flag(r));
     if ((s = build_qpass(B, sched[i].S, r, fl, &D, &q->gslots)) != QS_OK) return fail(s);
     q->gpass.push_back(D);
     q->gns.push_back(2);
@@ -484,6 +500,7 @@ qs_status qs_qaoa_create(int n_qubits, const int* edges, int n_edges, int p, dou
   const uint64_t n_tiles = 1ull << (q->n - mm);
   q->grid1 = qaoa_grid_size(dtype, mm, 1, n_edges, n_tiles);
   q->grid2 = qaoa_grid_size(dtype, mm, 2, n_edges, n_tiles);
+  if (q->il) q->grid2 = std::min(q->grid2, qaoa_il_grid_size(mm, n_edges, n_tiles));
   if (q->grid1 < 1 || q->grid2 < 1) {
     set_error("qaoa: the tile does not fit in shared memory");
     return fail(QS_ERR_UNSUPPORTED);
@@ -502,6 +519,7 @@ qs_status qs_qaoa_destroy(qs_qaoa* q) {
   if (q->d_coef) cudaFree(q->d_coef);
   if (q->d_gpass) cudaFree(q->d_gpass);
   if (q->d_epass) cudaFree(q->d_epass);
+  if (q->d_il_priv) cudaFree(q->d_il_priv);
   for (int* pi : {q->g_row, q->g_sidx, q->e_row, q->e_sidx})
     if (pi) cudaFree(pi);
   for (double* pd : {q->g_w, q->e_w})
@@ -557,6 +575,8 @@ qs_status run_qpasses(qs_qaoa* q, const std::vector<QPassDesc>& passes, const st
                       const QPassDesc* d_passes, void* psi, void* lam, double* partials, cudaStream_t st) {
   for (size_t i = 0; i < passes.size(); ++i) {
     QaoaLaunch L;
+    L.il[0] = lam;  // the interleaved reverse sweep reuses lam's buffer as its first half
+    L.il[1] = q->d_il_priv;
     L.psi = psi;
     L.lam = lam;
     L.coef = q->d_coef;
@@ -567,7 +587,7 @@ qs_status run_qpasses(qs_qaoa* q, const std::vector<QPassDesc>& passes, const st
     L.stride = q->grid2;
     L.grid = (ns[i] == 2 || passes[i].n_acc > 0) ? q->grid2 : q->grid1;
     TraceRec* rec = trace_begin(st);
-    QS_TRY(launch_qaoa_pass(q->dt, d_passes + i, ns[i], q->m, L, st));
+    QS_TRY(launch_qaoa_pass(q->dt, d_passes + i, ns[i], q->m, passes[i].flags, L, st));
     if (rec) {
       rec->bytes = pass_bytes(passes[i].flags, (double)amp_bytes(q->dt) * (double)(1ull << q->n),
                               (double)(1ull << q->n));

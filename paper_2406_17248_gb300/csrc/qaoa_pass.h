@@ -69,7 +69,16 @@ struct QPassDesc {
   QPhase phases[kQaoaMaxPhases];
 };
 
+// complex64 reverse sweep: psi and lam interleaved per amplitude,
+// (psi.re, lam.re, psi.im, lam.im) = 16 bytes, amplitude x stored at
+// il[0] + x for x < 2^(n-1) and il[1] + (x - 2^(n-1)) otherwise.
+enum QPassFlags : uint32_t {
+  PF_LOAD_IL = 1u << 8,   // load psi and lam from the interleaved buffer
+  PF_STORE_IL = 1u << 9   // store psi and lam to the interleaved buffer
+};
+
 struct QaoaLaunch {
+  void* il[2];
   void* psi;
   void* lam;
   const void* coef;  // per layer: lut[E+1], lut_dag[E+1], rx (c, s), rx_dag (c, -s)
@@ -80,7 +89,8 @@ struct QaoaLaunch {
 
 size_t qaoa_smem_bytes(qs_dtype dt, int m, int ns, int n_edges);
 int qaoa_grid_size(qs_dtype dt, int m, int ns, int n_edges, uint64_t n_tiles);
-qs_status launch_qaoa_pass(qs_dtype dt, const QPassDesc* d_pass, int ns, int m, const QaoaLaunch& L,
-                           cudaStream_t st);
+qs_status launch_qaoa_pass(qs_dtype dt, const QPassDesc* d_pass, int ns, int m, uint32_t flags,
+                           const QaoaLaunch& L, cudaStream_t st);
+int qaoa_il_grid_size(int m, int n_edges, uint64_t n_tiles);
 
 }  // namespace qs

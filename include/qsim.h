@@ -197,6 +197,54 @@ QS_API qs_status qs_qaoa_expectation(qs_qaoa* q, qs_state* psi, const double* ga
 QS_API qs_status qs_qaoa_expectation_with_grad(qs_qaoa* q, qs_state* psi, qs_state* lam, const double* gamma,
                                         const double* beta, double* energy, double* dgamma, double* dbeta);
 
+/* ----------------------------------------------------------------- batches */
+
+/* Many independent instances (circuit, Hamiltonian, parameters) evaluated
+ * together: the batch dimension of get_expectation_with_grad (§4.1, output
+ * shapes [n_batch, ...]), here with one circuit and Hamiltonian per instance.
+ * All instances run in ONE persistent launch: each CTA takes instances from a
+ * work queue (largest first) and runs the full adjoint evaluation of one
+ * instance at a time, with psi and lam in shared memory when they fit
+ * (complex64 n <= 13, complex128 n <= 12) and in a per-CTA global slot
+ * otherwise. */
+typedef struct qs_batch qs_batch;
+
+/* One gate of a batched circuit: kind (any qs_gate_kind but QS_GATE_MATRIX),
+ * n_targets / targets as in qs_circuit_add, controls as a bit mask, and the
+ * angle binding angle = constant + coef * params[param] with `param` indexing
+ * the instance's own parameter slice (-1: fixed angle). */
+typedef struct {
+  int32_t kind;
+  int32_t n_targets;
+  int32_t targets[2];
+  uint64_t ctrl_mask;
+  int32_t param;
+  int32_t pad;
+  double coef;
+  double constant;
+} qs_batch_gate;
+
+/* Instance i has n_qubits[i] (1..26) qubits, gates gates[gate_offsets[i] ..
+ * gate_offsets[i+1]), Pauli terms (xmask, zmask, coef)[term_offsets[i] ..
+ * term_offsets[i+1]) and parameters params[param_offsets[i] ..
+ * param_offsets[i+1]).  Offsets arrays have n_inst + 1 entries starting at 0.
+ * Every instance starts from |0...0>.  All arrays are host arrays and copied.
+ * Work is enqueued on cuda_stream. */
+QS_API qs_status qs_batch_create(int n_inst, const int* n_qubits, const int* gate_offsets,
+                                 const qs_batch_gate* gates, const int* term_offsets, const uint64_t* xmask,
+                                 const uint64_t* zmask, const double* coef, const int* param_offsets,
+                                 qs_dtype dtype, void* cuda_stream, qs_batch** out);
+QS_API qs_status qs_batch_destroy(qs_batch* b);
+/* Instances, total parameters and the CTAs of the persistent launch. */
+QS_API qs_status qs_batch_info(const qs_batch* b, int* n_instances, int* n_params, int* grid);
+/* energies[i] = <psi_i|H_i|psi_i> and grads (laid out like params) by the
+ * adjoint method, for every instance.  Host arrays; synchronises the stream. */
+QS_API qs_status qs_batch_expectation_with_grad(qs_batch* b, const double* params, double* energies,
+                                                double* grads);
+/* The same with device arrays (no copies, no synchronisation). */
+QS_API qs_status qs_batch_expectation_with_grad_device(qs_batch* b, const double* dev_params,
+                                                       double* dev_energies, double* dev_grads);
+
 /* ------------------------------------------------- allocation-free variant */
 
 /* *energy = <psi|H|psi>, the same Pauli-sum kernel as qs_expectation, for

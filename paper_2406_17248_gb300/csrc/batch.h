@@ -1,0 +1,50 @@
+// Batched engine: many independent (circuit, Hamiltonian, parameters)
+// instances evaluated (energy + adjoint gradient) in one persistent launch.
+#pragma once
+
+#include "qsim_internal.h"
+
+namespace qs {
+
+// One gate of a batched circuit (device layout, 32 bytes).
+struct BGate {
+  uint8_t kind;   // qs_gate_kind (MATRIX is not supported in batches)
+  uint8_t nt;     // targets (1 or 2)
+  uint8_t t0, t1;
+  int32_t param;  // -1: fixed angle
+  uint64_t cmask;
+  double coef, constant;
+};
+
+struct BInst {
+  int n;
+  int gate_begin, gate_end;
+  int group_begin, group_end;  // Hamiltonian groups (terms sharing an X mask)
+  int param_off, n_params;     // slice of the concatenated parameter / gradient arrays
+  int in_smem;                 // psi and lam fit in the CTA's shared memory
+  int pad;
+  double cost;                 // work estimate used to order the queue
+};
+
+struct BatchArgs {
+  const BInst* inst;
+  const int* order;        // instance indices by decreasing cost
+  int n_inst;
+  const BGate* gates;
+  const DevHamGroup* groups;
+  const DevHamTerm* terms;
+  const double* params;    // concatenated
+  double* energy;          // [n_inst]
+  double* grad;            // concatenated, like params
+  int* queue;              // work counter (zeroed before the launch)
+  void* slots;             // per-CTA global scratch for states too large for shared memory
+  size_t slot_amps;        // amplitudes per state in a slot
+  int smem_amps;           // amplitudes per state in shared memory
+};
+
+qs_status launch_batch(qs_dtype dt, const BatchArgs& a, int grid, cudaStream_t st);
+int batch_grid_size(qs_dtype dt, int smem_amps);
+size_t batch_smem_bytes(qs_dtype dt, int smem_amps);
+constexpr int kBatchThreads = 512;
+
+}  // namespace qs

@@ -1,0 +1,354 @@
+// Batched persistent engine: thousands of small, independent variational
+// instances (the encoder batch of §4.1, here each with its own circuit,
+// Hamiltonian and parameters) evaluated in ONE launch.  CTAs pull instances
+// from an atomic work queue ordered by decreasing cost; an instance is owned by
+// one CTA from start to finish: psi = U|0>, E = <psi|H|psi>, lam = H psi, then
+// the adjoint sweep (the gradient rule of §4.1 / §7.2) gate by gate.  psi and
+// lam live in the CTA's shared memory when both fit, otherwise in a per-CTA
+// global slot.  Gate matrices are formed on the device from the angle (the
+// definitions of §2.3.2 / §2.3.3); every reduction has a fixed order.
+#include <cmath>
+
+#include "batch.h"
+
+namespace qs {
+
+namespace {
+
+template <class T>
+struct BV;
+template <>
+struct BV<float> {
+  using V = float2;
+};
+template <>
+struct BV<double> {
+  using V = double2;
+};
+
+template <class V>
+__device__ __forceinline__ V bmul(V a, V b) {
+  V r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+template <class V>
+__device__ __forceinline__ V badd(V a, V b) {
+  a.x += b.x;
+  a.y += b.y;
+  return a;
+}
+template <class V, class T>
+__device__ __forceinline__ V bmk(T re, T im) {
+  V v;
+  v.x = re;
+  v.y = im;
+  return v;
+}
+// Re(conj(a) b)
+template <class V>
+__device__ __forceinline__ auto bre(V a, V b) -> decltype(a.x) {
+  return a.x * b.x + a.y * b.y;
+}
+
+__device__ __forceinline__ void bsincos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void bsincos(double x, double* s, double* c) { sincos(x, s, c); }
+
+__device__ __forceinline__ uint64_t bins0(uint64_t i, int q) {
+  return ((i >> q) << (q + 1)) | (i & ((1ull << q) - 1));
+}
+
+constexpr int kMaxBatchWarps = kBatchThreads / 32;
+
+// Gate classes (what the kernel does with the matrix)
+__device__ __forceinline__ bool bdiag(int k) {
+  return k == QS_GATE_I || k == QS_GATE_Z || k == QS_GATE_S || k == QS_GATE_SDG || k == QS_GATE_T ||
+         k == QS_GATE_TDG || k == QS_GATE_RZ || k == QS_GATE_PS || k == QS_GATE_RZZ;
+}
+
+// U of a gate (row-major, basis index bit(t0) + 2 bit(t1)); dim 2 or 4.
+template <class V, class T>
+__device__ void bgate_matrix(int kind, T th, V (&U)[16]) {
+  T s, c;
+  bsincos(th * (T)0.5, &s, &c);
+  const T r2 = (T)0.70710678118654752440;
+  for (int i = 0; i < 16; ++i) U[i] = bmk<V, T>(0, 0);
+  switch (kind) {
+    case QS_GATE_I: U[0] = U[3] = bmk<V, T>(1, 0); break;
+    case QS_GATE_X: U[1] = U[2] = bmk<V, T>(1, 0); break;
+    case QS_GATE_Y: U[1] = bmk<V, T>(0, -1); U[2] = bmk<V, T>(0, 1); break;
+    case QS_GATE_Z: U[0] = bmk<V, T>(1, 0); U[3] = bmk<V, T>(-1, 0); break;
+    case QS_GATE_H: U[0] = U[1] = U[2] = bmk<V, T>(r2, 0); U[3] = bmk<V, T>(-r2, 0); break;
+    case QS_GATE_S: U[0] = bmk<V, T>(1, 0); U[3] = bmk<V, T>(0, 1); break;
+    case QS_GATE_SDG: U[0] = bmk<V, T>(1, 0); U[3] = bmk<V, T>(0, -1); break;
+    case QS_GATE_T: U[0] = bmk<V, T>(1, 0); U[3] = bmk<V, T>(r2, r2); break;
+    case QS_GATE_TDG: U[0] = bmk<V, T>(1, 0); U[3] = bmk<V, T>(r2, -r2); break;
+    case QS_GATE_RX: U[0] = U[3] = bmk<V, T>(c, 0); U[1] = U[2] = bmk<V, T>(0, -s); break;
+    case QS_GATE_RY: U[0] = U[3] = bmk<V, T>(c, 0); U[1] = bmk<V, T>(-s, 0); U[2] = bmk<V, T>(s, 0); break;
+    case QS_GATE_RZ: U[0] = bmk<V, T>(c, -s); U[3] = bmk<V, T>(c, s); break;
+    case QS_GATE_PS: {
+      T s2, c2;
+      bsincos(th, &s2, &c2);
+      U[0] = bmk<V, T>(1, 0);
+      U[3] = bmk<V, T>(c2, s2);
+      break;
+    }
+    case QS_GATE_SWAP: U[0] = U[6] = U[9] = U[15] = bmk<V, T>(1, 0); break;
+    case QS_GATE_RXX:
+      for (int b = 0; b < 4; ++b) {
+        U[b * 5] = bmk<V, T>(c, 0);
+        U[b * 4 + 3 - b] = bmk<V, T>(0, -s);
+      }
+      break;
+    case QS_GATE_RYY:
+      for (int b = 0; b < 4; ++b) U[b * 5] = bmk<V, T>(c, 0);
+      U[3] = bmk<V, T>(0, s);
+      U[6] = bmk<V, T>(0, -s);
+      U[9] = bmk<V, T>(0, -s);
+      U[12] = bmk<V, T>(0, s);
+      break;
+    case QS_GATE_RZZ:
+      U[0] = U[15] = bmk<V, T>(c, -s);
+      U[5] = U[10] = bmk<V, T>(c, s);
+      break;
+    default: break;
+  }
+}
+
+// A = (dU/dtheta) U^dag of the parametric gates: -i P / 2 for the rotations,
+// diag(0, i) for PS (independent of the angle).
+template <class V, class T>
+__device__ void bgate_generator(int kind, V (&A)[16]) {
+  for (int i = 0; i < 16; ++i) A[i] = bmk<V, T>(0, 0);
+  const T h = (T)0.5;
+  switch (kind) {
+    case QS_GATE_RX: A[1] = A[2] = bmk<V, T>(0, -h); break;
+    case QS_GATE_RY: A[1] = bmk<V, T>(-h, 0); A[2] = bmk<V, T>(h, 0); break;
+    case QS_GATE_RZ: A[0] = bmk<V, T>(0, -h); A[3] = bmk<V, T>(0, h); break;
+    case QS_GATE_PS: A[3] = bmk<V, T>(0, 1); break;
+    case QS_GATE_RXX:
+      for (int b = 0; b < 4; ++b) A[b * 4 + 3 - b] = bmk<V, T>(0, -h);
+      break;
+    case QS_GATE_RYY:  // -i/2 Y(x)Y
+      A[3] = bmk<V, T>(0, h);
+      A[6] = bmk<V, T>(0, -h);
+      A[9] = bmk<V, T>(0, -h);
+      A[12] = bmk<V, T>(0, h);
+      break;
+    case QS_GATE_RZZ:
+      A[0] = A[15] = bmk<V, T>(0, -h);
+      A[5] = A[10] = bmk<V, T>(0, h);
+      break;
+    default: break;
+  }
+}
+
+// Fixed-order block sum (all threads get the result).
+template <class T>
+__device__ double bsum(T v, double* sh) {
+  double d = (double)v;
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = d;
+  __syncthreads();
+  double s = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+  return s;
+}
+
+// Apply one gate to psi; with BOTH also to lam, and with GRAD first accumulate
+// 2 Re <lam|A|psi> over the pairs the gate touches.
+template <class T, bool BOTH, bool GRAD>
+__device__ T bapply(typename BV<T>::V* psi, typename BV<T>::V* lam, int n, const BGate& g, const typename BV<T>::V (&M)[16],
+                    const typename BV<T>::V (&A)[16]) {
+  using V = typename BV<T>::V;
+  T acc = 0;
+  const uint64_t cm = g.cmask;
+  if (bdiag(g.kind)) {
+    const uint64_t N = 1ull << n;
+    for (uint64_t x = threadIdx.x; x < N; x += blockDim.x) {
+      if ((x & cm) != cm) continue;
+      int b = (int)((x >> g.t0) & 1);
+      if (g.nt == 2) b |= (int)((x >> g.t1) & 1) << 1;
+      const int d = g.nt == 2 ? 4 : 2;
+      const V u = M[b * d + b];
+      if (GRAD) acc += 2 * bre(lam[x], bmul(A[b * d + b], psi[x]));
+      if (BOTH) lam[x] = bmul(u, lam[x]);
+      psi[x] = bmul(u, psi[x]);
+    }
+  } else if (g.nt == 1) {
+    const uint64_t P = 1ull << (n - 1);
+    for (uint64_t i = threadIdx.x; i < P; i += blockDim.x) {
+      const uint64_t x0 = bins0(i, g.t0);
+      if ((x0 & cm) != cm) continue;
+      const uint64_t x1 = x0 | (1ull << g.t0);
+      const V a0 = psi[x0], a1 = psi[x1];
+      if (BOTH) {
+        const V l0 = lam[x0], l1 = lam[x1];
+        if (GRAD)
+          acc += 2 * (bre(l0, badd(bmul(A[0], a0), bmul(A[1], a1))) + bre(l1, badd(bmul(A[2], a0), bmul(A[3], a1))));
+        lam[x0] = badd(bmul(M[0], l0), bmul(M[1], l1));
+        lam[x1] = badd(bmul(M[2], l0), bmul(M[3], l1));
+      }
+      psi[x0] = badd(bmul(M[0], a0), bmul(M[1], a1));
+      psi[x1] = badd(bmul(M[2], a0), bmul(M[3], a1));
+    }
+  } else {
+    const int lo = g.t0 < g.t1 ? g.t0 : g.t1, hi = g.t0 < g.t1 ? g.t1 : g.t0;
+    const uint64_t Q = 1ull << (n - 2);
+    for (uint64_t i = threadIdx.x; i < Q; i += blockDim.x) {
+      const uint64_t base = bins0(bins0(i, lo), hi);
+      if ((base & cm) != cm) continue;
+      uint64_t idx[4];
+      for (int b = 0; b < 4; ++b)
+        idx[b] = base | ((uint64_t)(b & 1) << g.t0) | ((uint64_t)((b >> 1) & 1) << g.t1);
+      V a[4], l[4];
+      for (int b = 0; b < 4; ++b) a[b] = psi[idx[b]];
+      if (BOTH) {
+        for (int b = 0; b < 4; ++b) l[b] = lam[idx[b]];
+        if (GRAD)
+          for (int r = 0; r < 4; ++r) {
+            V y = bmk<V, T>(0, 0);
+            for (int k = 0; k < 4; ++k) y = badd(y, bmul(A[r * 4 + k], a[k]));
+            acc += 2 * bre(l[r], y);
+          }
+        for (int r = 0; r < 4; ++r) {
+          V y = bmk<V, T>(0, 0);
+          for (int k = 0; k < 4; ++k) y = badd(y, bmul(M[r * 4 + k], l[k]));
+          lam[idx[r]] = y;
+        }
+      }
+      for (int r = 0; r < 4; ++r) {
+        V y = bmk<V, T>(0, 0);
+        for (int k = 0; k < 4; ++k) y = badd(y, bmul(M[r * 4 + k], a[k]));
+        psi[idx[r]] = y;
+      }
+    }
+  }
+  return acc;
+}
+
+template <class T>
+__device__ void run_instance(const BatchArgs& a, const BInst& I, typename BV<T>::V* psi, typename BV<T>::V* lam,
+                             double* sh) {
+  using V = typename BV<T>::V;
+  const int n = I.n;
+  const uint64_t N = 1ull << n;
+  const double* params = a.params + I.param_off;
+  double* grad = a.grad + I.param_off;
+  for (int p = threadIdx.x; p < I.n_params; p += blockDim.x) grad[p] = 0.0;
+  for (uint64_t x = threadIdx.x; x < N; x += blockDim.x) psi[x] = bmk<V, T>(x == 0 ? 1 : 0, 0);
+  __syncthreads();
+  V M[16], A[16];
+  // forward: psi = U_N ... U_1 |0>
+  for (int gi = I.gate_begin; gi < I.gate_end; ++gi) {
+    const BGate g = a.gates[gi];
+    const double th = g.param < 0 ? g.constant : g.constant + g.coef * params[g.param];
+    bgate_matrix<V, T>(g.kind, (T)th, M);
+    bapply<T, false, false>(psi, lam, n, g, M, A);
+    __syncthreads();
+  }
+  // lam = H psi and E = <psi|lam>
+  T e = 0;
+  for (uint64_t y = threadIdx.x; y < N; y += blockDim.x) {
+    T lr = 0, li = 0;
+    for (int gg = I.group_begin; gg < I.group_end; ++gg) {
+      const DevHamGroup G = a.groups[gg];
+      const uint64_t x = y ^ G.xmask;
+      const V v = psi[x];
+      T fr = 0, fi = 0;
+      for (int k = G.begin; k < G.end; ++k) {
+        const DevHamTerm t = a.terms[k];
+        const T sg = (__popcll(x & t.zmask) & 1) ? (T)-1 : (T)1;
+        fr += sg * (T)t.re;
+        fi += sg * (T)t.im;
+      }
+      lr += fr * v.x - fi * v.y;
+      li += fr * v.y + fi * v.x;
+    }
+    lam[y] = bmk<V, T>(lr, li);
+    const V p = psi[y];
+    e += p.x * lr + p.y * li;
+  }
+  const double E = bsum(e, sh);
+  if (threadIdx.x == 0) a.energy[&I - a.inst] = E;
+  __syncthreads();
+  // reverse: gradient of every gate, psi and lam undone gate by gate
+  for (int gi = I.gate_end - 1; gi >= I.gate_begin; --gi) {
+    const BGate g = a.gates[gi];
+    const double th = g.param < 0 ? g.constant : g.constant + g.coef * params[g.param];
+    bgate_matrix<V, T>(g.kind, (T)th, M);
+    // U^dag
+    const int d = g.nt == 2 ? 4 : 2;
+    V Md[16];
+    for (int r = 0; r < d; ++r)
+      for (int c2 = 0; c2 < d; ++c2) Md[r * d + c2] = bmk<V, T>(M[c2 * d + r].x, -M[c2 * d + r].y);
+    if (g.param >= 0) {
+      bgate_generator<V, T>(g.kind, A);
+      const T part = bapply<T, true, true>(psi, lam, n, g, Md, A);
+      const double gsum = bsum(part, sh);
+      if (threadIdx.x == 0) grad[g.param] += g.coef * gsum;
+    } else {
+      bapply<T, true, false>(psi, lam, n, g, Md, A);
+    }
+    __syncthreads();
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a) {
+  using V = typename BV<T>::V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sh[kMaxBatchWarps];
+  __shared__ int s_next;
+  V* s_psi = reinterpret_cast<V*>(smem);
+  V* s_lam = s_psi + a.smem_amps;
+  V* g_psi = reinterpret_cast<V*>(a.slots) + (size_t)blockIdx.x * 2 * a.slot_amps;
+  V* g_lam = g_psi + a.slot_amps;
+  while (true) {
+    if (threadIdx.x == 0) s_next = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int i = s_next;
+    __syncthreads();
+    if (i >= a.n_inst) break;
+    const BInst& I = a.inst[a.order[i]];
+    if (I.in_smem)
+      run_instance<T>(a, I, s_psi, s_lam, sh);
+    else
+      run_instance<T>(a, I, g_psi, g_lam, sh);
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+size_t batch_smem_bytes(qs_dtype dt, int smem_amps) { return 2 * (size_t)smem_amps * (dt == QS_C64 ? 8 : 16); }
+
+int batch_grid_size(qs_dtype dt, int smem_amps) {
+  const size_t smem = batch_smem_bytes(dt, smem_amps);
+  const void* fn = dt == QS_C64 ? (const void*)batch_kernel<float> : (const void*)batch_kernel<double>;
+  int occ = 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBatchThreads, smem) != cudaSuccess || occ < 1) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return (sms > 0 ? sms : 1) * occ;
+}
+
+qs_status launch_batch(qs_dtype dt, const BatchArgs& a, int grid, cudaStream_t st) {
+  const size_t smem = batch_smem_bytes(dt, a.smem_amps);
+  if (dt == QS_C64)
+    batch_kernel<float><<<grid, kBatchThreads, smem, st>>>(a);
+  else
+    batch_kernel<double><<<grid, kBatchThreads, smem, st>>>(a);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+}  // namespace qs

@@ -62,6 +62,11 @@ SIGNATURES = [
     ("qs_qaoa_evolve", [_VP, _VP, _PD, _PD]),
     ("qs_qaoa_expectation", [_VP, _VP, _PD, _PD, _PD]),
     ("qs_qaoa_expectation_with_grad", [_VP, _VP, _VP, _PD, _PD, _PD, _PD, _PD]),
+    ("qs_batch_create", [_I, _PI, _PI, _VP, _PI, _PU64, _PU64, _PD, _PI, _I, _VP, _PVP]),
+    ("qs_batch_destroy", [_VP]),
+    ("qs_batch_info", [_VP, _PI, _PI, _PI]),
+    ("qs_batch_expectation_with_grad", [_VP, _PD, _PD, _PD]),
+    ("qs_batch_expectation_with_grad_device", [_VP, _VP, _VP, _VP]),
     ("qs_expectation_noalloc", [_VP, _I, _I, _I, _PU64, _PU64, _PD, _VP, _PD]),
     ("qs_trace_enable", [_I]),
     ("qs_trace_read", [_I, _PI, _PD, _PD]),
@@ -286,6 +291,90 @@ def sample(state: State, shots: int, seed: int) -> np.ndarray:
     out = np.zeros(max(shots, 1), dtype=np.uint64)
     _check(lib().qs_sample(state.h, shots, seed, out.ctypes.data_as(_PU64)))
     return out[:shots]
+
+
+class BatchGate(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_targets", C.c_int32), ("targets", C.c_int32 * 2),
+                ("ctrl_mask", C.c_uint64), ("param", C.c_int32), ("pad", C.c_int32),
+                ("coef", C.c_double), ("constant", C.c_double)]
+
+
+class Batch:
+    """Independent (circuit, Hamiltonian, parameters) instances evaluated in one
+    persistent launch (qs_batch_*)."""
+
+    def __init__(self, instances, dtype: int = C64, stream=None):
+        n_inst = len(instances)
+        nq = np.array([it.circuit.n_qubits for it in instances], dtype=np.int32)
+        g_off, t_off, p_off = [0], [0], [0]
+        gates, xs, zs, cs = [], [], [], []
+        for it in instances:
+            for g in it.circuit.gates:
+                if g.kind == "MATRIX":
+                    raise ValueError("MATRIX gates are not batched")
+                bg = BatchGate()
+                bg.kind = KIND[g.kind]
+                bg.n_targets = len(g.targets)
+                bg.targets[0] = g.targets[0]
+                bg.targets[1] = g.targets[1] if len(g.targets) > 1 else g.targets[0]
+                bg.ctrl_mask = sum(1 << q for q in g.ctrls)
+                bg.param, bg.pad, bg.coef, bg.constant = g.param, 0, g.coef, g.const
+                gates.append(bg)
+            g_off.append(len(gates))
+            xs.extend(int(v) for v in it.ham.xmask)
+            zs.extend(int(v) for v in it.ham.zmask)
+            cs.extend(float(v) for v in it.ham.coef)
+            t_off.append(len(cs))
+            p_off.append(p_off[-1] + it.circuit.n_params)
+        self.n_inst, self.dtype = n_inst, dtype
+        self.param_offsets = np.array(p_off, dtype=np.int32)
+        arr = (BatchGate * max(len(gates), 1))(*gates)
+        x = np.array(xs or [0], dtype=np.uint64)
+        z = np.array(zs or [0], dtype=np.uint64)
+        cf = np.array(cs or [0.0], dtype=np.float64)
+        go, to = np.array(g_off, dtype=np.int32), np.array(t_off, dtype=np.int32)
+        h = C.c_void_p()
+        _check(lib().qs_batch_create(n_inst, nq.ctypes.data_as(_PI), go.ctypes.data_as(_PI), C.cast(arr, C.c_void_p),
+                                     to.ctypes.data_as(_PI), x.ctypes.data_as(_PU64), z.ctypes.data_as(_PU64),
+                                     _dptr(cf), self.param_offsets.ctypes.data_as(_PI), dtype,
+                                     C.c_void_p(_stream_ptr(stream)), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qs_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().qs_batch_info(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return {"instances": a.value, "params": b.value, "grid": c.value}
+
+    def expectation_with_grad(self, params):
+        """params: concatenated (instance order) or a list of per-instance arrays.
+        Returns (energies[n_inst], list of per-instance gradient arrays)."""
+        if isinstance(params, (list, tuple)):
+            params = np.concatenate([np.asarray(p, dtype=np.float64) for p in params]) if params else np.zeros(0)
+        pr = np.ascontiguousarray(params, dtype=np.float64)
+        if pr.size != self.param_offsets[-1]:
+            raise ValueError("wrong number of parameters")
+        e = np.zeros(self.n_inst)
+        g = np.zeros(max(pr.size, 1))
+        _check(lib().qs_batch_expectation_with_grad(self.h, _dptr(pr) if pr.size else None, _dptr(e), _dptr(g)))
+        po = self.param_offsets
+        return e, [g[po[i]:po[i + 1]] for i in range(self.n_inst)]
+
+    def expectation_with_grad_device(self, params, energies, grads):
+        """Device (torch float64 CUDA tensor) variant: no copies, no synchronisation."""
+        _check(lib().qs_batch_expectation_with_grad_device(self.h, C.c_void_p(params.data_ptr()),
+                                                           C.c_void_p(energies.data_ptr()),
+                                                           C.c_void_p(grads.data_ptr())))
 
 
 def expectation_noalloc(state: State, ham: I.PauliSum, stream=None) -> float:

@@ -269,15 +269,26 @@ QS_API qs_status qs_expectation_noalloc(const void* dev_psi, int n_qubits, qs_dt
 
 /* ----------------------------------------------------------------- tracing */
 
-/* Tracing of the fused tile passes: while enabled, every tile-pass launch is
- * bracketed by a CUDA event pair recorded on its own stream, together with the
- * pass's algorithmic HBM bytes (state tiles loaded + stored, plus cut values).
- * Not part of the paper; it exists to measure the engine.  enable: 1 = start
- * (clears earlier records), 0 = stop.  At most 65536 launches are kept. */
+/* Kernel of a traced launch. */
+typedef enum {
+  QS_TRACE_TILE = 0,      /* generic fused tile pass (circuits) */
+  QS_TRACE_QAOA_FWD = 1,  /* QAOA pass on psi alone */
+  QS_TRACE_QAOA_TWO = 2,  /* QAOA pass on separate psi and lam tiles (turnaround) */
+  QS_TRACE_QAOA_IL = 3,   /* QAOA reverse pass on interleaved psi/lam */
+  QS_TRACE_BATCH = 4      /* batched persistent launch */
+} qs_trace_kind;
+
+/* Tracing of the engine's launches: while enabled, every tile-pass or batch
+ * launch is bracketed by a CUDA event pair recorded on its own stream, together
+ * with the pass's algorithmic HBM bytes (state tiles loaded + stored, plus cut
+ * values; 0 for batch launches) and its kernel kind.  Not part of the paper; it
+ * exists to measure the engine.  enable: 1 = start (clears earlier records),
+ * 0 = stop.  At most 65536 launches are kept. */
 QS_API qs_status qs_trace_enable(int enable);
 /* Synchronise the recorded events and copy out up to `max` records: duration in
- * ms and algorithmic bytes per launch.  *n = number of records copied. */
-QS_API qs_status qs_trace_read(int max, int* n, double* ms, double* bytes);
+ * ms, algorithmic bytes and qs_trace_kind per launch (any output may be NULL).
+ * *n = number of records copied. */
+QS_API qs_status qs_trace_read(int max, int* n, double* ms, double* bytes, int* kinds);
 
 #ifdef __cplusplus
 }

@@ -388,6 +388,7 @@ qs_status run_passes(const TilePlan& plan, int begin, int end, qs_dtype dt, void
       rec->bytes = S * (((f & PF_LOAD_PSI) ? 1 : 0) + ((f & PF_LOAD_LAM) ? 1 : 0) + ((f & PF_STORE_PSI) ? 1 : 0) +
                         ((f & PF_STORE_LAM) ? 1 : 0)) +
                    ((f & PF_NEED_CUT) ? (double)(1ull << n) : 0.0);
+      rec->kind = QS_TRACE_TILE;
       QS_CUDA(cudaEventRecord(rec->end, st));
     }
   }
@@ -430,7 +431,7 @@ qs_status trace_enable(int on) {
   return QS_OK;
 }
 
-qs_status trace_read(int max, int* n, double* ms, double* bytes) {
+qs_status trace_read(int max, int* n, double* ms, double* bytes, int* kinds) {
   std::lock_guard<std::mutex> lk(g_trace_mu);
   const int k = (int)std::min<size_t>(g_trace_used, (size_t)std::max(max, 0));
   for (int i = 0; i < k; ++i) {
@@ -439,6 +440,7 @@ qs_status trace_read(int max, int* n, double* ms, double* bytes) {
     QS_CUDA(cudaEventElapsedTime(&t, g_trace[i].start, g_trace[i].end));
     if (ms) ms[i] = t;
     if (bytes) bytes[i] = g_trace[i].bytes;
+    if (kinds) kinds[i] = g_trace[i].kind;
   }
   *n = k;
   return QS_OK;
@@ -872,9 +874,9 @@ qs_status qs_expectation_with_grad(qs_state* psi, qs_state* lam, qs_circuit* c, 
 
 qs_status qs_trace_enable(int enable) { return trace_enable(enable); }
 
-qs_status qs_trace_read(int max, int* n, double* ms, double* bytes) {
+qs_status qs_trace_read(int max, int* n, double* ms, double* bytes, int* kinds) {
   QS_CHECK(n != nullptr, "n is null");
-  return trace_read(max, n, ms, bytes);
+  return trace_read(max, n, ms, bytes, kinds);
 }
 
 qs_status qs_sample(const qs_state* s_, uint64_t shots, uint64_t seed, uint64_t* out_bits) {

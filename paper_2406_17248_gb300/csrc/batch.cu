@@ -232,6 +232,7 @@ qs_status qs_batch_expectation_with_grad_device(qs_batch* b, const double* dev_p
   QS_TRY(launch_batch(b->dt, a, b->grid, b->st));
   if (rec) {
     rec->bytes = 0;
+    rec->kind = QS_TRACE_BATCH;
     QS_CUDA(cudaEventRecord(rec->end, b->st));
   }
   return QS_OK;

@@ -77,11 +77,12 @@ namespace qs {
 struct TraceRec {
   cudaEvent_t start, end;
   double bytes;
+  int kind;  // qs_trace_kind
 };
 // Event pair for the next launch on `st` when tracing is on, else nullptr.
 TraceRec* trace_begin(cudaStream_t st);
 qs_status trace_enable(int on);
-qs_status trace_read(int max, int* n, double* ms, double* bytes);
+qs_status trace_read(int max, int* n, double* ms, double* bytes, int* kinds);
 qs_status ensure_scratch(qs_state* s, size_t ndoubles);
 qs_status upload_table(const std::vector<double>& tab, qs_dtype dt, void* d_dst, cudaStream_t st,
                        std::vector<double>& staging);

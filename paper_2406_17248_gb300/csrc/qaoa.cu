@@ -591,6 +591,7 @@ qs_status run_qpasses(qs_qaoa* q, const std::vector<QPassDesc>& passes, const st
     if (rec) {
       rec->bytes = pass_bytes(passes[i].flags, (double)amp_bytes(q->dt) * (double)(1ull << q->n),
                               (double)(1ull << q->n));
+      rec->kind = (passes[i].flags & PF_LOAD_IL) ? QS_TRACE_QAOA_IL : ns[i] == 2 ? QS_TRACE_QAOA_TWO : QS_TRACE_QAOA_FWD;
       QS_CUDA(cudaEventRecord(rec->end, st));
     }
   }

@@ -69,7 +69,7 @@ SIGNATURES = [
     ("qs_batch_expectation_with_grad_device", [_VP, _VP, _VP, _VP]),
     ("qs_expectation_noalloc", [_VP, _I, _I, _I, _PU64, _PU64, _PD, _VP, _PD]),
     ("qs_trace_enable", [_I]),
-    ("qs_trace_read", [_I, _PI, _PD, _PD]),
+    ("qs_trace_read", [_I, _PI, _PD, _PD, _PI]),
 ]
 
 
@@ -396,13 +396,18 @@ def trace_enable(on: bool = True):
     _check(lib().qs_trace_enable(1 if on else 0))
 
 
+TRACE_KINDS = {0: "tile_pass_kernel", 1: "qaoa_pass_kernel (psi)", 2: "qaoa_pass_kernel (psi, lam)",
+               3: "qaoa_il_kernel (interleaved reverse)", 4: "batch_kernel"}
+
+
 def trace_read(max_records: int = 65536):
-    """(durations in ms, algorithmic bytes) of the recorded tile-pass launches."""
+    """(durations in ms, algorithmic bytes, kernel kinds) of the recorded launches."""
     ms = np.zeros(max_records)
     by = np.zeros(max_records)
+    kinds = np.zeros(max_records, dtype=np.int32)
     n = C.c_int()
-    _check(lib().qs_trace_read(max_records, C.byref(n), _dptr(ms), _dptr(by)))
-    return ms[: n.value], by[: n.value]
+    _check(lib().qs_trace_read(max_records, C.byref(n), _dptr(ms), _dptr(by), kinds.ctypes.data_as(_PI)))
+    return ms[: n.value], by[: n.value], kinds[: n.value]
 
 
 # --------------------------------------------------------------------------- QAOA

@@ -295,3 +295,58 @@ def random_state(n: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     v = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
     return v / np.linalg.norm(v)
+
+
+# --------------------------------------------------------------------------- graph sets (learned QAOA initialiser)
+
+def graph_set(count: int, seed: int, n_range=(16, 26), er_p: float = 0.3) -> List[Tuple[int, List[Tuple[int, int]]]]:
+    """`count` graphs: even positions random 3-regular (pairing model), odd
+    positions Erdos-Renyi G(n, er_p); n ~ U{n_range} (3-regular graphs take the
+    next even n when n is odd).  Returns [(n, edges)]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        s = int(rng.integers(0, 2**31 - 1))
+        if i % 2 == 0:
+            if n % 2:
+                n = n + 1 if n + 1 <= n_range[1] else n - 1
+            out.append((n, random_regular_graph(n, 3, s)))
+        else:
+            out.append((n, erdos_renyi(n, er_p, s)))
+    return out
+
+
+def pack_graphs(graphs: Sequence[Tuple[int, Sequence[Tuple[int, int]]]]):
+    """CSR batch of undirected graphs: node_off[G+1] (graph g owns global nodes
+    node_off[g] .. node_off[g+1]-1), adj_off[N+1] and adj[2E] (neighbours of
+    global node v are adj[adj_off[v] .. adj_off[v+1]), as LOCAL indices within
+    v's graph, in increasing order).  int32 numpy arrays."""
+    node_off = [0]
+    adj_off = [0]
+    adj: List[int] = []
+    for n, edges in graphs:
+        nb: List[List[int]] = [[] for _ in range(n)]
+        for a, b in edges:
+            nb[a].append(b)
+            nb[b].append(a)
+        for v in range(n):
+            adj.extend(sorted(nb[v]))
+            adj_off.append(len(adj))
+        node_off.append(node_off[-1] + n)
+    return (np.array(node_off, dtype=np.int32), np.array(adj_off, dtype=np.int32),
+            np.array(adj if adj else [0], dtype=np.int32)[: len(adj)])
+
+
+def gnn_init_weights(n_weights_layout, seed: int) -> np.ndarray:
+    """Glorot-uniform weights and zero biases for a flat parameter vector
+    described by [(kind, rows, cols)] blocks ('W' or 'b'), float32."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for kind, rows, cols in n_weights_layout:
+        if kind == "W":
+            lim = np.sqrt(6.0 / (rows + cols))
+            parts.append(rng.uniform(-lim, lim, size=rows * cols))
+        else:
+            parts.append(np.zeros(rows))
+    return np.concatenate(parts).astype(np.float32)

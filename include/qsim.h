@@ -186,6 +186,10 @@ QS_API qs_status qs_qaoa_create(int n_qubits, const int* edges, int n_edges, int
 QS_API qs_status qs_qaoa_destroy(qs_qaoa* q);
 /* Forward passes and planned HBM traffic of one energy+gradient evaluation. */
 QS_API qs_status qs_qaoa_info(const qs_qaoa* q, int* fwd_passes, int* rev_passes, double* bytes_per_eval);
+/* *max_cut = max over x of cut(x), the MaxCut optimum by exhaustive search over
+ * the engine's cut-value array (the brute-force maximum §5.2 compares against).
+ * Host output; synchronises. */
+QS_API qs_status qs_qaoa_max_cut(qs_qaoa* q, int* max_cut);
 /* psi <- U(gamma, beta)|+>^n (QuPack evolution()). */
 QS_API qs_status qs_qaoa_evolve(qs_qaoa* q, qs_state* psi, const double* gamma, const double* beta);
 /* *energy = <psi(gamma,beta)|C|psi(gamma,beta)>; psi is overwritten with the final state. */
@@ -244,6 +248,68 @@ QS_API qs_status qs_batch_expectation_with_grad(qs_batch* b, const double* param
 /* The same with device arrays (no copies, no synchronisation). */
 QS_API qs_status qs_batch_expectation_with_grad_device(qs_batch* b, const double* dev_params,
                                                        double* dev_energies, double* dev_grads);
+
+/* ------------------------------------------- learned QAOA initialiser (GNN) */
+
+/* A graph network that maps a MaxCut graph to 2p QAOA angles, trained on
+ * angles the simulator optimised.  The paper trains QAOA angles by gradient
+ * descent from a fixed start (§5.2) and motivates slowly varying schedules by
+ * adiabatic evolution (§5.4); the network is this library's own:
+ *   node features h0[v] = (1, deg(v) / 3);
+ *   `layers` message-passing layers of width `hidden`:
+ *     a[v] = mean of h[u] over the neighbours u of v (0 without neighbours),
+ *     h'[v] = relu(Ws h[v] + Wn a[v] + b);
+ *   readout r = mean over nodes of h_L (0 for an empty graph),
+ *   y = W2 relu(W1 r + b1) + b2, out_dim outputs.
+ * Parameters: one float32 vector, blocks in this order: per layer Ws [hidden x d],
+ * Wn [hidden x d], b [hidden] (d = 2 for the first layer, hidden after), then
+ * W1 [hidden x hidden], b1 [hidden], W2 [out_dim x hidden], b2 [out_dim];
+ * matrices row-major (output, input).  The kernels compute with the weights
+ * rounded to bfloat16 (nearest, ties to even) and float32 activations and sums;
+ * Adam keeps the float32 master copy. */
+typedef struct qs_gnn qs_gnn;
+typedef struct qs_graphs qs_graphs;
+
+/* A batch of undirected graphs, validated and copied to the device.
+ * node_off[n_graphs + 1]: graph g owns global nodes node_off[g] .. node_off[g+1]-1
+ * (at most 64 nodes per graph); adj_off[N + 1] (N = node_off[n_graphs]) and adj:
+ * the neighbours of global node v are adj[adj_off[v] .. adj_off[v+1]), given as
+ * indices LOCAL to v's graph.  The adjacency must be symmetric, without self
+ * loops or repeats, at most 4096 entries per graph.  Host arrays; violations
+ * return QS_ERR_INVALID_ARG. */
+QS_API qs_status qs_graphs_create(int n_graphs, const int* node_off, const int* adj_off, const int* adj,
+                                  qs_graphs** out);
+QS_API qs_status qs_graphs_destroy(qs_graphs* g);
+/* *n = number of float32 parameters for these dimensions (hidden even, 2..64;
+ * layers 1..4; out_dim 1..64). */
+QS_API qs_status qs_gnn_n_weights(int hidden, int layers, int out_dim, int* n);
+/* A network with zero weights and zero Adam state; work goes on cuda_stream. */
+QS_API qs_status qs_gnn_create(int hidden, int layers, int out_dim, void* cuda_stream, qs_gnn** out);
+QS_API qs_status qs_gnn_destroy(qs_gnn* g);
+/* Replace the float32 weights (host or device array of n_weights floats), form
+ * the bfloat16 copy and reset the Adam moments and step count. */
+QS_API qs_status qs_gnn_set_weights(qs_gnn* g, const float* w, int on_device);
+/* Copy out the float32 master weights and/or their bfloat16 bit patterns
+ * (either pointer may be NULL).  Host copies synchronise the stream. */
+QS_API qs_status qs_gnn_get_weights(qs_gnn* g, float* w, uint16_t* w_bf16, int on_device);
+/* dev_out[g * out_dim + o] = y_o of graph g, device float32.  Asynchronous. */
+QS_API qs_status qs_gnn_forward(qs_gnn* g, const qs_graphs* graphs, float* dev_out);
+/* dev_grad[n_weights] = sum over graphs of dL/dw given dev_dout[g * out_dim + o]
+ * = dL/dy (device float32), recomputing the forward pass.  Gradients are summed
+ * in a fixed order: bitwise reproducible for a given batch.  Asynchronous. */
+QS_API qs_status qs_gnn_backward(qs_gnn* g, const qs_graphs* graphs, const float* dev_dout, float* dev_grad);
+/* One Adam step (Kingma & Ba 2015, with bias correction; the step count is kept
+ * by the network) on the float32 weights, then refresh the bfloat16 copy. */
+QS_API qs_status qs_gnn_adam_step(qs_gnn* g, const float* dev_grad, float lr, float beta1, float beta2, float eps);
+/* *dev_loss = mean of (y - t)^2 over n entries and dev_dy = 2 (y - t) / n (either
+ * output may be NULL).  Device float32 arrays, one CTA, fixed summation order. */
+QS_API qs_status qs_mse(int n, const float* dev_y, const float* dev_target, float* dev_loss, float* dev_dy,
+                        void* cuda_stream);
+/* One Adam step on n float64 parameters in place (device arrays), step count t
+ * >= 1 given by the caller; maximize = 1 ascends (uses -grad).  Used to optimise
+ * batches of circuit angles without leaving the device. */
+QS_API qs_status qs_adam_f64(int n, double* dev_w, double* dev_m, double* dev_v, const double* dev_grad, int t,
+                             double lr, double beta1, double beta2, double eps, int maximize, void* cuda_stream);
 
 /* ------------------------------------------------- allocation-free variant */
 

@@ -154,3 +154,19 @@ def adam(w, m, v, g, t: int, lr: float, b1: float = 0.9, b2: float = 0.999, eps:
     mh = m / (1.0 - b1 ** t)
     vh = v / (1.0 - b2 ** t)
     return w - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def min_abs_preactivation(w_bf16: np.ndarray, node_off, adj_off, adj, layers: int = 3, **dims) -> float:
+    """Smallest |pre-activation| of any ReLU in the batch (message-passing layers
+    and the readout MLP).  Tests use it to keep inputs away from the kink, where
+    float32 and float64 may take different branches of the derivative."""
+    P = unpack(w_bf16, layers=layers, **dims)
+    best = np.inf
+    for n, nb in _graph_lists(node_off, adj_off, adj):
+        hs, as_, r, zpre, y = _forward_graph(P, n, nb, layers)
+        for l in range(layers):
+            if n:
+                pre = hs[l] @ P[f"Ws{l}"].T + as_[l] @ P[f"Wn{l}"].T + P[f"bl{l}"]
+                best = min(best, float(np.min(np.abs(pre))))
+        best = min(best, float(np.min(np.abs(zpre))))
+    return best

@@ -271,6 +271,23 @@ __global__ void cut_values_kernel(uint8_t* cut, int n, const int* __restrict__ e
   }
 }
 
+// *out = max over x of cut(x) (the maximum cut), 16 bytes per thread step
+__global__ void max_u8_kernel(const uint8_t* __restrict__ v, uint64_t n, int* out) {
+  int m = 0;
+  const uint64_t n16 = n / 16;
+  const uint4* v16 = reinterpret_cast<const uint4*>(v);
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n16; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint4 w = v16[i];
+    for (uint32_t word : {w.x, w.y, w.z, w.w})
+      for (int b = 0; b < 4; ++b) m = max(m, (int)((word >> (8 * b)) & 0xffu));
+  }
+  for (uint64_t i = n16 * 16 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    m = max(m, (int)v[i]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
 // --------------------------------------------------------------- sampling
 constexpr int kChunkBits = 12;  // probabilities are summed in chunks of 4096 amplitudes
 
@@ -537,6 +554,15 @@ qs_status launch_cut_values(uint8_t* cut, int n, const int* d_edges, int n_edges
   const int grid = blocks_for(1ull << n);
   const int g = grid > 65535 * 8 ? 65535 * 8 : grid;
   cut_values_kernel<<<g, kThreads, 2 * n_edges * sizeof(int), st>>>(cut, n, d_edges, n_edges);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_max_u8(const uint8_t* v, uint64_t n, int* d_out, cudaStream_t st) {
+  QS_CUDA(cudaMemsetAsync(d_out, 0, sizeof(int), st));
+  const uint64_t want = (n / 16 + kThreads - 1) / kThreads;
+  const int g = (int)(want < 1 ? 1 : (want > 4096 ? 4096 : want));
+  max_u8_kernel<<<g, kThreads, 0, st>>>(v, n, d_out);
   QS_CUDA(cudaGetLastError());
   return QS_OK;
 }

@@ -51,6 +51,7 @@ struct qs_qaoa {
   // holds the first half of the amplitudes and this private buffer the second
   bool il = false;
   void* d_il_priv = nullptr;
+  int* d_max = nullptr;  // qs_qaoa_max_cut result
 };
 
 namespace {
@@ -515,6 +516,7 @@ qs_status qs_qaoa_destroy(qs_qaoa* q) {
   if (!q) return QS_OK;
   cudaDeviceSynchronize();
   if (q->d_cut) cudaFree(q->d_cut);
+  if (q->d_max) cudaFree(q->d_max);
   if (q->d_edges) cudaFree(q->d_edges);
   if (q->d_coef) cudaFree(q->d_coef);
   if (q->d_gpass) cudaFree(q->d_gpass);
@@ -533,6 +535,14 @@ qs_status qs_qaoa_info(const qs_qaoa* q, int* fwd_passes, int* rev_passes, doubl
   if (fwd_passes) *fwd_passes = q->n_fwd + 1;
   if (rev_passes) *rev_passes = q->rev_passes;
   if (bytes_per_eval) *bytes_per_eval = q->bytes_per_eval;
+  return QS_OK;
+}
+
+qs_status qs_qaoa_max_cut(qs_qaoa* q, int* max_cut) {
+  QS_CHECK(q != nullptr && max_cut != nullptr, "null argument");
+  if (!q->d_max) QS_CUDA(cudaMalloc(&q->d_max, sizeof(int)));
+  QS_TRY(launch_max_u8(q->d_cut, 1ull << q->n, q->d_max, nullptr));
+  QS_CUDA(cudaMemcpy(max_cut, q->d_max, sizeof(int), cudaMemcpyDeviceToHost));
   return QS_OK;
 }
 

@@ -178,6 +178,8 @@ qs_status launch_param_gather(const double* gate_grad, const int* row_ptr, const
 
 // QAOA
 qs_status launch_cut_values(uint8_t* cut, int n, const int* d_edges, int n_edges, cudaStream_t st);
+// *d_out = max of v[0..n) (bytes); v 16-byte aligned
+qs_status launch_max_u8(const uint8_t* v, uint64_t n, int* d_out, cudaStream_t st);
 
 // Sampling
 qs_status launch_sample(qs_dtype dt, const void* psi, int n, uint64_t shots, uint64_t seed,

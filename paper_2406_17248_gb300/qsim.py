@@ -59,6 +59,7 @@ SIGNATURES = [
     ("qs_qaoa_create", [_I, _PI, _I, _I, _D, _I, _VP, _PVP]),
     ("qs_qaoa_destroy", [_VP]),
     ("qs_qaoa_info", [_VP, _PI, _PI, _PD]),
+    ("qs_qaoa_max_cut", [_VP, _PI]),
     ("qs_qaoa_evolve", [_VP, _VP, _PD, _PD]),
     ("qs_qaoa_expectation", [_VP, _VP, _PD, _PD, _PD]),
     ("qs_qaoa_expectation_with_grad", [_VP, _VP, _VP, _PD, _PD, _PD, _PD, _PD]),
@@ -67,6 +68,18 @@ SIGNATURES = [
     ("qs_batch_info", [_VP, _PI, _PI, _PI]),
     ("qs_batch_expectation_with_grad", [_VP, _PD, _PD, _PD]),
     ("qs_batch_expectation_with_grad_device", [_VP, _VP, _VP, _VP]),
+    ("qs_graphs_create", [_I, _PI, _PI, _PI, _PVP]),
+    ("qs_graphs_destroy", [_VP]),
+    ("qs_gnn_n_weights", [_I, _I, _I, _PI]),
+    ("qs_gnn_create", [_I, _I, _I, _VP, _PVP]),
+    ("qs_gnn_destroy", [_VP]),
+    ("qs_gnn_set_weights", [_VP, _VP, _I]),
+    ("qs_gnn_get_weights", [_VP, _VP, _VP, _I]),
+    ("qs_gnn_forward", [_VP, _VP, _VP]),
+    ("qs_gnn_backward", [_VP, _VP, _VP, _VP]),
+    ("qs_gnn_adam_step", [_VP, _VP, C.c_float, C.c_float, C.c_float, C.c_float]),
+    ("qs_mse", [_I, _VP, _VP, _VP, _VP, _VP]),
+    ("qs_adam_f64", [_I, _VP, _VP, _VP, _VP, _I, _D, _D, _D, _D, _I, _VP]),
     ("qs_expectation_noalloc", [_VP, _I, _I, _I, _PU64, _PU64, _PD, _VP, _PD]),
     ("qs_trace_enable", [_I]),
     ("qs_trace_read", [_I, _PI, _PD, _PD, _PI]),
@@ -299,6 +312,12 @@ class BatchGate(C.Structure):
                 ("coef", C.c_double), ("constant", C.c_double)]
 
 
+# numpy twin of qs_batch_gate (same field order, sizes and offsets)
+BATCH_GATE_DTYPE = np.dtype([("kind", "<i4"), ("n_targets", "<i4"), ("targets", "<i4", (2,)), ("ctrl_mask", "<u8"),
+                             ("param", "<i4"), ("pad", "<i4"), ("coef", "<f8"), ("constant", "<f8")])
+assert BATCH_GATE_DTYPE.itemsize == C.sizeof(BatchGate) == 48
+
+
 class Batch:
     """Independent (circuit, Hamiltonian, parameters) instances evaluated in one
     persistent launch (qs_batch_*)."""
@@ -307,20 +326,15 @@ class Batch:
         n_inst = len(instances)
         nq = np.array([it.circuit.n_qubits for it in instances], dtype=np.int32)
         g_off, t_off, p_off = [0], [0], [0]
-        gates, xs, zs, cs = [], [], [], []
+        rows, xs, zs, cs = [], [], [], []
         for it in instances:
             for g in it.circuit.gates:
                 if g.kind == "MATRIX":
                     raise ValueError("MATRIX gates are not batched")
-                bg = BatchGate()
-                bg.kind = KIND[g.kind]
-                bg.n_targets = len(g.targets)
-                bg.targets[0] = g.targets[0]
-                bg.targets[1] = g.targets[1] if len(g.targets) > 1 else g.targets[0]
-                bg.ctrl_mask = sum(1 << q for q in g.ctrls)
-                bg.param, bg.pad, bg.coef, bg.constant = g.param, 0, g.coef, g.const
-                gates.append(bg)
-            g_off.append(len(gates))
+                t1 = g.targets[1] if len(g.targets) > 1 else g.targets[0]
+                rows.append((KIND[g.kind], len(g.targets), (g.targets[0], t1), sum(1 << q for q in g.ctrls),
+                             g.param, 0, g.coef, g.const))
+            g_off.append(len(rows))
             xs.extend(int(v) for v in it.ham.xmask)
             zs.extend(int(v) for v in it.ham.zmask)
             cs.extend(float(v) for v in it.ham.coef)
@@ -328,15 +342,16 @@ class Batch:
             p_off.append(p_off[-1] + it.circuit.n_params)
         self.n_inst, self.dtype = n_inst, dtype
         self.param_offsets = np.array(p_off, dtype=np.int32)
-        arr = (BatchGate * max(len(gates), 1))(*gates)
+        gates = np.array(rows or [(0, 1, (0, 0), 0, -1, 0, 0.0, 0.0)], dtype=BATCH_GATE_DTYPE)
         x = np.array(xs or [0], dtype=np.uint64)
         z = np.array(zs or [0], dtype=np.uint64)
         cf = np.array(cs or [0.0], dtype=np.float64)
         go, to = np.array(g_off, dtype=np.int32), np.array(t_off, dtype=np.int32)
         h = C.c_void_p()
-        _check(lib().qs_batch_create(n_inst, nq.ctypes.data_as(_PI), go.ctypes.data_as(_PI), C.cast(arr, C.c_void_p),
-                                     to.ctypes.data_as(_PI), x.ctypes.data_as(_PU64), z.ctypes.data_as(_PU64),
-                                     _dptr(cf), self.param_offsets.ctypes.data_as(_PI), dtype,
+        _check(lib().qs_batch_create(n_inst, nq.ctypes.data_as(_PI), go.ctypes.data_as(_PI),
+                                     gates.ctypes.data_as(C.c_void_p), to.ctypes.data_as(_PI),
+                                     x.ctypes.data_as(_PU64), z.ctypes.data_as(_PU64), _dptr(cf),
+                                     self.param_offsets.ctypes.data_as(_PI), dtype,
                                      C.c_void_p(_stream_ptr(stream)), C.byref(h)))
         self.h = h
 
@@ -467,3 +482,117 @@ class QAOA:
         _check(lib().qs_qaoa_expectation_with_grad(self.h, psi.h, lam.h, _dptr(g), _dptr(b), C.byref(e),
                                                    _dptr(dg), _dptr(db)))
         return e.value, dg, db
+
+    def max_cut(self) -> int:
+        """MaxCut optimum by exhaustive search over the device cut-value array."""
+        m = C.c_int()
+        _check(lib().qs_qaoa_max_cut(self.h, C.byref(m)))
+        return m.value
+
+
+# --------------------------------------------------------------------------- learned initialiser (GNN)
+
+def _dev(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr())
+
+
+class Graphs:
+    """A validated device copy of a CSR batch of graphs (qs_graphs_create)."""
+
+    def __init__(self, node_off, adj_off, adj):
+        no = np.ascontiguousarray(node_off, dtype=np.int32)
+        ao = np.ascontiguousarray(adj_off, dtype=np.int32)
+        a = np.ascontiguousarray(adj, dtype=np.int32)
+        if a.size == 0:
+            a = np.zeros(1, dtype=np.int32)
+        self.n_graphs = int(no.size - 1)
+        h = C.c_void_p()
+        _check(lib().qs_graphs_create(self.n_graphs, no.ctypes.data_as(_PI), ao.ctypes.data_as(_PI),
+                                      a.ctypes.data_as(_PI), C.byref(h)))
+        self.h = h
+
+    @classmethod
+    def from_graphs(cls, graphs):
+        return cls(*I.pack_graphs(graphs))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qs_graphs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gnn_n_weights(hidden: int = 64, layers: int = 3, out_dim: int = 8) -> int:
+    n = C.c_int()
+    _check(lib().qs_gnn_n_weights(hidden, layers, out_dim, C.byref(n)))
+    return n.value
+
+
+class GNN:
+    """The graph network of qs_gnn_* (bfloat16 weights, float32 arithmetic)."""
+
+    def __init__(self, hidden: int = 64, layers: int = 3, out_dim: int = 8, stream=None):
+        self.hidden, self.layers, self.out_dim = hidden, layers, out_dim
+        self.n_weights = gnn_n_weights(hidden, layers, out_dim)
+        h = C.c_void_p()
+        _check(lib().qs_gnn_create(hidden, layers, out_dim, C.c_void_p(_stream_ptr(stream)), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qs_gnn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_weights(self, w):
+        if isinstance(w, np.ndarray):
+            a = np.ascontiguousarray(w, dtype=np.float32)
+            if a.size != self.n_weights:
+                raise ValueError("wrong number of weights")
+            _check(lib().qs_gnn_set_weights(self.h, a.ctypes.data_as(C.c_void_p), 0))
+        else:
+            if w.numel() != self.n_weights:
+                raise ValueError("wrong number of weights")
+            _check(lib().qs_gnn_set_weights(self.h, _dev(w), 1))
+
+    def get_weights(self):
+        """(float32 master weights, bfloat16 bit patterns as uint16) on the host."""
+        w = np.zeros(self.n_weights, dtype=np.float32)
+        wb = np.zeros(self.n_weights, dtype=np.uint16)
+        _check(lib().qs_gnn_get_weights(self.h, w.ctypes.data_as(C.c_void_p), wb.ctypes.data_as(C.c_void_p), 0))
+        return w, wb
+
+    def forward(self, graphs: Graphs, out):
+        """out: device float32 tensor [n_graphs, out_dim] (written asynchronously)."""
+        _check(lib().qs_gnn_forward(self.h, graphs.h, _dev(out)))
+        return out
+
+    def backward(self, graphs: Graphs, dout, grad):
+        _check(lib().qs_gnn_backward(self.h, graphs.h, _dev(dout), _dev(grad)))
+        return grad
+
+    def adam_step(self, grad, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        _check(lib().qs_gnn_adam_step(self.h, _dev(grad), lr, beta1, beta2, eps))
+
+
+def mse(y, target, loss=None, dy=None, stream=None):
+    """Device float32 tensors: loss (1 element) and dy may be None."""
+    _check(lib().qs_mse(int(y.numel()), _dev(y), _dev(target), _dev(loss) if loss is not None else None,
+                        _dev(dy) if dy is not None else None, C.c_void_p(_stream_ptr(stream))))
+
+
+def adam_f64(w, m, v, grad, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+             maximize: bool = False, stream=None):
+    """One in-place Adam step on device float64 tensors."""
+    _check(lib().qs_adam_f64(int(w.numel()), _dev(w), _dev(m), _dev(v), _dev(grad), t, lr, beta1, beta2, eps,
+                             1 if maximize else 0, C.c_void_p(_stream_ptr(stream))))

@@ -427,9 +427,144 @@ def run_random_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def gnn_flops(graphs, H=64, L=3, O=8):
+    """Algorithmic FP32 flops of one forward and one backward launch over
+    `graphs` (multiply-add = 2): neighbour means, the two H x d products per
+    node and layer, readout and MLP; the backward recomputes the forward and
+    adds the weight-gradient and input-gradient products."""
+    fwd = bwd = 0.0
+    for n, e in graphs:
+        adj = 2 * len(e)
+        f = n * H + 2 * H * H + 2 * O * H
+        b = 2 * O * H + 4 * H * H
+        d = 2
+        for l in range(L):
+            f += adj * d + 4 * n * H * d
+            b += adj * d + 4 * n * H * d + (4 * n * H * H + adj * H if l > 0 else 0)
+            d = H
+        fwd += f
+        bwd += f + b
+    return fwd, bwd
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    """FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x SM clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def run_gnn_workload(args):
+    """Learned-initialiser network: 256 graphs of 26 nodes (half 3-regular, half
+    Erdos-Renyi G(26, 0.3), seed 5), hidden 64, 3 layers, 8 outputs; one training
+    step = forward + MSE + backward + Adam, all device kernels."""
+    import numpy as np
+    import torch
+    from paper_2406_17248_gb300 import build, inputs as I
+    build.build()
+    from paper_2406_17248_gb300 import qsim as Q
+    from paper_2406_17248_gb300.qaoa_init import Initialiser
+    graphs = I.graph_set(256, 5, (26, 26))
+    gb = Q.Graphs.from_graphs(graphs)
+    init = Initialiser(p=4, seed=5)
+    net = init.net
+    y = torch.zeros(len(graphs), 8, dtype=torch.float32, device="cuda")
+    t = torch.randn_like(y)
+    dy = torch.zeros_like(y)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    grad = torch.zeros(net.n_weights, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def step():
+        net.forward(gb, y)
+        Q.mse(y, t, loss, dy)
+        net.backward(gb, dy, grad)
+        net.adam_step(grad, 1e-4)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    reps = max(args.steps, 10) * 200
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    clocks = ClockSampler()
+    clocks.start()
+    ev[0].record(st)
+    for _ in range(reps):
+        net.forward(gb, y)
+    ev[1].record(st)
+    for _ in range(reps):
+        net.backward(gb, dy, grad)
+    ev[2].record(st)
+    for _ in range(reps):
+        step()
+    ev[3].record(st)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    fwd_us = 1e3 * ev[0].elapsed_time(ev[1]) / reps
+    bwd_us = 1e3 * ev[1].elapsed_time(ev[2]) / reps
+    step_us = 1e3 * ev[2].elapsed_time(ev[3]) / reps
+    f_fl, b_fl = gnn_flops(graphs)
+    sm = ck.get("sm_max_mhz") or 2070
+    peak = fp32_alu_peak_tflops(sm)
+    dom = "backward" if bwd_us >= fwd_us else "forward"
+    ach = (b_fl / (bwd_us * 1e-6) if dom == "backward" else f_fl / (fwd_us * 1e-6)) / 1e12
+    # end to end through the public API: graphs and targets from the host, loss back
+    tgt_h = torch.randn(len(graphs), 8, dtype=torch.float32).pin_memory()
+    loss_h = torch.zeros(1, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    h0 = time.perf_counter()
+    e2e_reps = 20
+    for _ in range(e2e_reps):
+        gbh = Q.Graphs.from_graphs(graphs)
+        t.copy_(tgt_h, non_blocking=True)
+        net.forward(gbh, y)
+        Q.mse(y, t, loss, dy)
+        net.backward(gbh, dy, grad)
+        net.adam_step(grad, 1e-4)
+        loss_h.copy_(loss, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - h0) / e2e_reps
+    no, ao, adj = I.pack_graphs(graphs)
+    line = {"metric": "GNN initialiser training step (forward+MSE+backward+Adam), graphs/s",
+            "value": len(graphs) / (step_us * 1e-6), "unit": "graphs/s", "n_gpus": 1, "steps": reps,
+            "warmup": max(3, args.warmup), "ms_per_step": step_us / 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 weights, f32 arithmetic", "data": "synthetic",
+            "config": {"workload": "256 graphs x 26 nodes (3-regular / G(26,0.3)), hidden 64, 3 layers, 8 outputs, "
+                                   "seed 5", "l2": "inputs (1 MB) are L2-resident; latency-bound launches"},
+            "forward_us": fwd_us, "backward_us": bwd_us, "step_us": step_us,
+            "roofline": {"bound": "alu", "kernel": f"gnn_{dom}_kernel", "achieved": ach, "peak": peak,
+                         "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                         "peak_note": f"FP32 FMA: 152 SMs x 128 lanes x 2 x {sm} MHz"},
+            "e2e": {"value": len(graphs) / e2e_s, "unit": "graphs/s",
+                    "h2d_bytes_per_step": int(4 * (no.size + ao.size + adj.size) + tgt_h.numel() * 4),
+                    "d2h_bytes_per_step": 4},
+            "gpu_launches": reps * (1 + 2 + 5), "clocks": ck}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = gnn_cpu_baseline(graphs, net)
+    print(json.dumps(line), flush=True)
+
+
+def gnn_cpu_baseline(graphs, net):
+    """The FP64 oracle's forward+backward on a bounded sample of the same graphs."""
+    import numpy as np
+    from oracle import gnn_oracle as G
+    from paper_2406_17248_gb300 import inputs as I
+    _, wb = net.get_weights()
+    w = (wb.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    sample = graphs[:16]
+    batch = I.pack_graphs(sample)
+    t0 = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t0 < 10.0:
+        y = G.forward(w, *batch)
+        _, dy = G.mse(y, np.zeros_like(y))
+        G.backward(w, *batch, dy)
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": k * len(sample) / dt, "unit": "graphs/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k} x {len(sample)} graphs of 26 nodes, forward + MSE + backward (no Adam)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="qaoa30", choices=["qaoa30", "batch", "random28"])
+    ap.add_argument("--workload", default="qaoa30", choices=["qaoa30", "batch", "random28", "gnn"])
     ap.add_argument("--instances", type=int, default=2048)
     ap.add_argument("--plain-instances", type=int, default=2048)
     ap.add_argument("--gpus", type=int, default=1)
@@ -446,6 +581,8 @@ def main():
     args = ap.parse_args()
     if args.workload == "batch":
         return run_batch_workload(args)
+    if args.workload == "gnn":
+        return run_gnn_workload(args)
     if args.workload == "random28":
         if args.n == 30:
             args.n = 28

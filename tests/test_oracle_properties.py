@@ -199,3 +199,28 @@ def test_sampling_inverse_cdf_brute_force_and_chi_square():
     assert np.all(counts[~keep] == 0)
     stat = chisquare(counts[keep], p[keep] / p[keep].sum() * shots)
     assert stat.pvalue > 1e-4
+
+
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+def test_dense_block_appliers_agree_and_factorise(k):
+    """k-target unitaries (dense fused blocks): the axis applier against explicit
+    Kronecker products, and a product of single-qubit unitaries U_{k-1} (x) ... (x)
+    U_0 (basis index sum_b bit(targets[b]) 2^b) against applying each factor on its
+    own target."""
+    rng = np.random.default_rng(k)
+    n = 8
+    targets = list(rng.permutation(n)[:k])
+    z = rng.normal(size=(1 << k, 1 << k)) + 1j * rng.normal(size=(1 << k, 1 << k))
+    U, _ = np.linalg.qr(z)
+    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    a = O.apply_gate(psi, n, U, targets)
+    b = O.dense_gate_unitary(n, U, targets) @ psi
+    assert np.max(np.abs(a - b)) < 1e-12
+    singles = [np.linalg.qr(rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2)))[0] for _ in range(k)]
+    K = np.eye(1, dtype=complex)
+    for s in reversed(singles):
+        K = np.kron(K, s)
+    want = psi.copy()
+    for t, s in zip(targets, singles):
+        want = O.apply_gate(want, n, s, [t])
+    assert np.max(np.abs(O.apply_gate(psi, n, K, targets) - want)) < 1e-12

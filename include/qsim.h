@@ -141,6 +141,18 @@ QS_API qs_status qs_circuit_info(const qs_circuit* c, int* n_gates, int* n_param
  * params[n_params] on the host, n_params >= the circuit's parameter count. */
 QS_API qs_status qs_apply_circuit(qs_state* s, qs_circuit* c, const double* params, int n_params);
 
+/* psi <- U psi for a dense 2^k x 2^k complex matrix on k target qubits (a
+ * custom gate, §2.3.4; equally the product of a run of gates fused into k
+ * qubits).  matrix: host, row-major, (re, im) doubles, 2^k x 2^k; basis index
+ * sum_b bit(targets[b]) 2^b.  k = 1..6, distinct targets < n.
+ * engine: 0 = automatic, 1 = CUDA cores (the state's precision), 2 = tensor
+ * cores (tcgen05 TF32 with head/tail operand splitting, float32 accuracy;
+ * complex64, k = 4 or 5 and n - k >= 7 only, else QS_ERR_INVALID_ARG).  The
+ * automatic choice takes the tensor cores where they apply.  Tensor-core calls
+ * synchronise the stream and return QS_ERR_TIMEOUT if the MMA completion wait
+ * gave up; CUDA-core calls are asynchronous. */
+QS_API qs_status qs_apply_matrix(qs_state* s, int k, const int* targets, const double* matrix, int engine);
+
 /* ------------------------------------------------------------ Hamiltonians */
 
 /* H = sum_k coef[k] P_k with real coefficients (§2.5.1), P_k given by masks:
@@ -341,7 +353,9 @@ typedef enum {
   QS_TRACE_QAOA_FWD = 1,  /* QAOA pass on psi alone */
   QS_TRACE_QAOA_TWO = 2,  /* QAOA pass on separate psi and lam tiles (turnaround) */
   QS_TRACE_QAOA_IL = 3,   /* QAOA reverse pass on interleaved psi/lam */
-  QS_TRACE_BATCH = 4      /* batched persistent launch */
+  QS_TRACE_BATCH = 4,     /* batched persistent launch */
+  QS_TRACE_DENSE_TC = 5,  /* dense k-qubit block on the tensor cores */
+  QS_TRACE_DENSE_CC = 6   /* dense k-qubit block on the CUDA cores */
 } qs_trace_kind;
 
 /* Tracing of the engine's launches: while enabled, every tile-pass or batch

@@ -29,6 +29,8 @@ from __future__ import annotations
 import dataclasses
 from typing import List, Optional, Sequence, Tuple
 
+import math
+
 import numpy as np
 
 # Gate kinds understood by both sides (names follow §2.3; CNOT = X with one
@@ -350,3 +352,25 @@ def gnn_init_weights(n_weights_layout, seed: int) -> np.ndarray:
         else:
             parts.append(np.zeros(rows))
     return np.concatenate(parts).astype(np.float32)
+
+
+# --------------------------------------------------------------------------- large states by formula
+
+def hashed_amplitudes(idx: np.ndarray, seed: int, n: int) -> np.ndarray:
+    """Amplitudes of a seeded pseudo-random state given index by index, so that
+    states too large to hold on the host can be generated in chunks and any
+    amplitude recomputed: a_x = (u - 1/2 + i (v - 1/2)) * 2^{(1 - n)/2} * sqrt(3),
+    u, v the top 53 bits of two splitmix64 outputs of the counter (seed, x).
+    The squared norm is close to 1 (the mean of |a_x|^2 is 2^-n)."""
+    x = np.asarray(idx, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        def mix(z):
+            z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+            z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+            return z ^ (z >> np.uint64(31))
+        g = np.uint64(0x9E3779B97F4A7C15)
+        base = np.uint64(seed) * np.uint64(0xD1B54A32D192ED03) + x * np.uint64(2) * g
+        u = (mix(base + g) >> np.uint64(11)).astype(np.float64) * 2.0**-53
+        v = (mix(base + g + g) >> np.uint64(11)).astype(np.float64) * 2.0**-53
+    s = math.sqrt(3.0) * 2.0 ** ((1 - n) / 2)
+    return ((u - 0.5) + 1j * (v - 0.5)) * s

@@ -49,6 +49,7 @@ SIGNATURES = [
     ("qs_circuit_finalize", [_VP, _I, _VP]),
     ("qs_circuit_info", [_VP, _PI, _PI, _PI]),
     ("qs_apply_circuit", [_VP, _VP, _PD, _I]),
+    ("qs_apply_matrix", [_VP, _I, _PI, _PD, _I]),
     ("qs_ham_create", [_I, _I, _PU64, _PU64, _PD, _PVP]),
     ("qs_ham_destroy", [_VP]),
     ("qs_apply_hamiltonian", [_VP, _VP, _VP]),
@@ -392,6 +393,19 @@ class Batch:
                                                            C.c_void_p(grads.data_ptr())))
 
 
+def apply_matrix(state: State, targets, matrix, engine: int = 0) -> State:
+    """psi <- U psi for a dense 2^k x 2^k complex matrix on `targets` (qs_apply_matrix);
+    engine 0 automatic, 1 CUDA cores, 2 tensor cores."""
+    t = np.ascontiguousarray(targets, dtype=np.int32)
+    U = np.ascontiguousarray(np.asarray(matrix, dtype=np.complex128))
+    k = int(t.size)
+    if U.shape != (1 << k, 1 << k):
+        raise ValueError("matrix must be 2^k x 2^k")
+    m = np.ascontiguousarray(U.view(np.float64).reshape(-1))
+    _check(lib().qs_apply_matrix(state.h, k, t.ctypes.data_as(_PI), _dptr(m), engine))
+    return state
+
+
 def expectation_noalloc(state: State, ham: I.PauliSum, stream=None) -> float:
     """<psi|H|psi> through qs_expectation_noalloc: no device allocation by the
     library (its working memory is a fixed array inside the library), for callers
@@ -412,7 +426,8 @@ def trace_enable(on: bool = True):
 
 
 TRACE_KINDS = {0: "tile_pass_kernel", 1: "qaoa_pass_kernel (psi)", 2: "qaoa_pass_kernel (psi, lam)",
-               3: "qaoa_il_kernel (interleaved reverse)", 4: "batch_kernel"}
+               3: "qaoa_il_kernel (interleaved reverse)", 4: "batch_kernel", 5: "dense_tc_kernel (tcgen05)",
+               6: "dense_cc_kernel"}
 
 
 def trace_read(max_records: int = 65536):

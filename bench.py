@@ -562,9 +562,94 @@ def gnn_cpu_baseline(graphs, net):
             "sample": f"{k} x {len(sample)} graphs of 26 nodes, forward + MSE + backward (no Adam)"}
 
 
+def run_dense_workload(args):
+    """Dense k-qubit blocks on 28 qubits complex64 (2 GiB): a seeded random
+    unitary on spread targets, tensor cores (tcgen05) vs CUDA cores."""
+    import numpy as np
+    import torch
+    from paper_2406_17248_gb300 import build, inputs as I
+    build.build()
+    from paper_2406_17248_gb300 import qsim as Q
+    n = args.n if args.n != 30 else 28
+    k = args.block_k
+    targets = [0, 9, 17, 22, n - 1, 13][:k]
+    rng = np.random.default_rng(k)
+    U = np.linalg.qr(rng.normal(size=(1 << k, 1 << k)) + 1j * rng.normal(size=(1 << k, 1 << k)))[0]
+    s = Q.State(n, Q.C64).set_plus()
+    st = torch.cuda.current_stream()
+    res = {}
+    clocks = ClockSampler()
+    for eng, name in ((2, "tensor"), (1, "cuda_core")):
+        for _ in range(max(3, args.warmup)):
+            Q.apply_matrix(s, targets, U, eng)
+        torch.cuda.synchronize()
+        if eng == 2:
+            clocks.start()
+        Q.trace_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            Q.apply_matrix(s, targets, U, eng)
+        e1.record(st)
+        torch.cuda.synchronize()
+        Q.trace_enable(False)
+        if eng == 2:
+            ck = clocks.stop()
+        k_ms, k_by, _ = Q.trace_read()
+        res[name] = {"ms_per_block": e0.elapsed_time(e1) / args.steps, "kernel_ms": float(np.mean(k_ms)),
+                     "kernel_GBps": float(np.mean(k_by) / (np.mean(k_ms) / 1e3) / 1e9)}
+    peak, peak_kind = measured_peak_hbm()
+    tc = res["tensor"]
+    tflops = 3 * 8 * (1 << k) * (1 << n) / (tc["kernel_ms"] / 1e3) / 1e12
+    # end to end: the state from pinned host memory, the block, the state back
+    h = torch.empty(1 << n, dtype=torch.complex64).pin_memory()
+    h.copy_(s.amplitudes, non_blocking=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(2):
+        s.amplitudes.copy_(h, non_blocking=True)
+        Q.apply_matrix(s, targets, U, 2)
+        h.copy_(s.amplitudes, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / 2
+    line = {"metric": f"dense {k}-qubit block applications/s, {n} qubits complex64 (tcgen05 tensor cores)",
+            "value": 1e3 / tc["ms_per_block"], "unit": "blocks/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": tc["ms_per_block"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (tf32 head/tail split)", "data": "synthetic",
+            "config": {"workload": f"{n}-qubit complex64 state, seeded random {k}-qubit unitary on qubits {targets}",
+                       "l2": "state 2 GiB > L2, no flush needed"},
+            "roofline": {"bound": "hbm", "kernel": "dense_tc_kernel", "achieved": tc["kernel_GBps"], "peak": peak,
+                         "unit": "GB/s", "frac": tc["kernel_GBps"] / peak, "traffic": None,
+                         "peak_kind": f"{peak_kind} hbm_gbs", "tensor_tflops": tflops},
+            "cuda_core": res["cuda_core"], "tensor": tc,
+            "e2e": {"value": 1.0 / e2e_s, "unit": "blocks/s", "h2d_bytes_per_step": 8 << n,
+                    "d2h_bytes_per_step": 8 << n},
+            "gpu_launches": 2 * args.steps, "clocks": ck}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = dense_cpu_baseline(k, U, targets, n)
+    print(json.dumps(line), flush=True)
+
+
+def dense_cpu_baseline(k, U, targets, n, n_small=20):
+    """The oracle's block applier on a 20-qubit state, scaled by 2^(20 - n)."""
+    import numpy as np
+    from oracle import qsim_oracle as O
+    from paper_2406_17248_gb300 import inputs as I
+    psi = I.random_state(n_small, 1)
+    tg = [t % n_small for t in targets]
+    t0 = time.perf_counter()
+    reps = 0
+    while time.perf_counter() - t0 < 10.0:
+        psi = O.apply_gate(psi, n_small, U, tg)
+        reps += 1
+    dt = time.perf_counter() - t0
+    return {"value": reps / dt * 2.0 ** (n_small - n), "unit": "blocks/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} applications at {n_small} qubits (complex128 numpy), scaled by 2^({n_small}-{n})"}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="qaoa30", choices=["qaoa30", "batch", "random28", "gnn"])
+    ap.add_argument("--workload", default="qaoa30", choices=["qaoa30", "batch", "random28", "gnn", "dense28"])
     ap.add_argument("--instances", type=int, default=2048)
     ap.add_argument("--plain-instances", type=int, default=2048)
     ap.add_argument("--gpus", type=int, default=1)
@@ -578,9 +663,12 @@ def main():
     ap.add_argument("--cpu-qubits", type=int, default=20)
     ap.add_argument("--ref-qubits", type=int, default=18)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--block-k", type=int, default=5)
     args = ap.parse_args()
     if args.workload == "batch":
         return run_batch_workload(args)
+    if args.workload == "dense28":
+        return run_dense_workload(args)
     if args.workload == "gnn":
         return run_gnn_workload(args)
     if args.workload == "random28":

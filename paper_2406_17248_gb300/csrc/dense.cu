@@ -187,13 +187,21 @@ __global__ void __launch_bounds__(kTcThreads) dense_tc_kernel(float2* __restrict
   const uint32_t a_hi_s = smem_u32(a_hi), a_lo_s = smem_u32(a_lo), b_hi_s = smem_u32(b_hi), b_lo_s = smem_u32(b_lo);
   uint32_t phase = 0;
 
-  for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    // gather this thread's row, split into tf32 head and tail
-    const uint64_t base = deposit_other(G, tile * kTcRows + tid);
-#pragma unroll 4
+  // Software pipeline: the rows of the next tile are loaded into registers
+  // while the tensor cores work on this one and its results are stored.
+  uint64_t tile = blockIdx.x;
+  float2 x[KB];
+  uint64_t base = 0;
+  if (tile < n_tiles) {
+    base = deposit_other(G, tile * kTcRows + tid);
+#pragma unroll
+    for (int j = 0; j < KB; ++j) x[j] = psi[base | G.tgt_off[j]];
+  }
+  for (; tile < n_tiles; tile += gridDim.x) {
+    // split this thread's row into tf32 head and tail, K-major core-matrix layout
+#pragma unroll
     for (int c = 0; c < KB / 2; ++c) {
-      const float2 p0 = psi[base | G.tgt_off[2 * c]];
-      const float2 p1 = psi[base | G.tgt_off[2 * c + 1]];
+      const float2 p0 = x[2 * c], p1 = x[2 * c + 1];
       float4 h, t;
       h.x = tf32_round(p0.x);
       h.y = tf32_round(p0.y);
@@ -223,6 +231,18 @@ __global__ void __launch_bounds__(kTcThreads) dense_tc_kernel(float2* __restrict
       }
       mma_commit(smem_u32(mbar));
     }
+    // next tile's rows in flight during the MMAs and the stores below
+    const uint64_t next = tile + gridDim.x;
+    uint64_t nbase = 0;
+    float2 xn[KB];
+    if (next < n_tiles) {
+      nbase = deposit_other(G, next * kTcRows + tid);
+#pragma unroll
+      for (int j = 0; j < KB; ++j) xn[j] = psi[nbase | G.tgt_off[j]];
+    } else {
+#pragma unroll
+      for (int j = 0; j < KB; ++j) xn[j] = make_float2(0.f, 0.f);
+    }
     // every thread waits for the MMAs (bounded)
     bool ok = false;
     for (long long it = 0; it < kWaitLimit; ++it)
@@ -249,7 +269,11 @@ __global__ void __launch_bounds__(kTcThreads) dense_tc_kernel(float2* __restrict
     }
     tc_fence_before();
     __syncthreads();
+    base = nbase;
+#pragma unroll
+    for (int j = 0; j < KB; ++j) x[j] = xn[j];
   }
+  tc_fence_after();
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),

@@ -456,3 +456,27 @@ def sample(psi: np.ndarray, shots: int, seed: int) -> np.ndarray:
     total = cdf[-1]
     u = np.array([shot_uniform(seed, s) for s in range(shots)], dtype=np.float64)
     return np.searchsorted(cdf, u * total, side="right").astype(np.uint64)
+
+
+def qaoa_p1_energy_closed_form(n: int, edges, gamma: float, beta: float, gamma_scale: float = 1.0) -> float:
+    """<sum_E Z_u Z_v> of depth-1 MaxCut QAOA in closed form (Wang, Hadfield,
+    Jiang & Rieffel 2018, Theorem 1), valid for any n: for the state
+    exp(-i b B) exp(-i g C)|+>^n with C = sum (1 - Z_u Z_v)/2 and B = sum X,
+      <C_uv> = 1/2 + sin(4b) sin(g) (cos^du g + cos^dv g)/4
+                   - sin^2(2b) cos^(du + dv - 2f) g (1 - cos^f 2g)/4,
+    du = deg(u) - 1, dv = deg(v) - 1, f = triangles on the edge.  This
+    module's layer exp(-i gamma_scale gamma sum ZZ) then RX(beta) is that state
+    with g = -2 gamma_scale gamma and b = beta / 2 (global phases aside)."""
+    g = -2.0 * gamma_scale * gamma
+    b = beta / 2.0
+    nb = [set() for _ in range(n)]
+    for a, c in edges:
+        nb[a].add(c)
+        nb[c].add(a)
+    total = 0.0
+    for u, v in edges:
+        du, dv, f = len(nb[u]) - 1, len(nb[v]) - 1, len(nb[u] & nb[v])
+        cuv = (0.5 + 0.25 * math.sin(4 * b) * math.sin(g) * (math.cos(g) ** du + math.cos(g) ** dv)
+               - 0.25 * math.sin(2 * b) ** 2 * math.cos(g) ** (du + dv - 2 * f) * (1 - math.cos(2 * g) ** f))
+        total += 1.0 - 2.0 * cuv
+    return total

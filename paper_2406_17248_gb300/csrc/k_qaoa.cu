@@ -50,6 +50,7 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 constexpr int QRN = 16;
 
@@ -72,19 +73,20 @@ __device__ __forceinline__ void rx_bit(V (&a)[QRN], T c, T s) {
 }
 
 // sum over pairs of Im(conj(b0) a1 + conj(b1) a0) = Im <b| X_RB |a> on the sub-cube
+// (four independent partial sums: the FMA chains stay short)
 template <int RB, class V, class T>
 __device__ __forceinline__ T gradx_bit(const V (&a)[QRN], const V (&b)[QRN]) {
-  T acc = 0;
+  T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
 #pragma unroll
   for (int j = 0; j < QRN; ++j) {
     if (j & (1 << RB)) continue;
     const int j1 = j | (1 << RB);
-    acc = qfma(b[j].x, a[j1].y, acc);
-    acc = qfma(-b[j].y, a[j1].x, acc);
-    acc = qfma(b[j1].x, a[j].y, acc);
-    acc = qfma(-b[j1].y, a[j].x, acc);
+    s0 = qfma(b[j].x, a[j1].y, s0);
+    s1 = qfma(-b[j].y, a[j1].x, s1);
+    s2 = qfma(b[j1].x, a[j].y, s2);
+    s3 = qfma(-b[j1].y, a[j].x, s3);
   }
-  return acc;
+  return (s0 + s1) + (s2 + s3);
 }
 
 template <class V>
@@ -395,28 +397,32 @@ __global__ void __launch_bounds__(kTileThreads, (sizeof(T) == 4 && NS == 1) ? 2 
               // cost gradient C(x) Im(conj(lam) psi), then (optionally) cost^dag on both
               if (NS == 2) {
                 const V* lut = lay + E1;
+                T gq[4] = {0, 0, 0, 0};
 #pragma unroll
                 for (int j = 0; j < QRN; ++j) {
                   const int k = QCUT(j);
                   const T C = (T)(n_edges - 2 * k);
-                  g = qfma(C, qfma(b[j].x, a[j].y, -b[j].y * a[j].x), g);
+                  gq[j & 3] = qfma(C, qfma(b[j].x, a[j].y, -b[j].y * a[j].x), gq[j & 3]);
                   if (st.flags & QSF_LAM) {
                     const V d = lut[k];
                     a[j] = qcmul(d, a[j]);
                     b[j] = qcmul(d, b[j]);
                   }
                 }
+                g = (gq[0] + gq[1]) + (gq[2] + gq[3]);
               }
               break;
             }
             case QST_ENERGY: {
+              T gq[4] = {0, 0, 0, 0};
 #pragma unroll
               for (int j = 0; j < QRN; ++j) {
                 const T C = (T)(n_edges - 2 * QCUT(j));
-                g = qfma(C, qfma(a[j].x, a[j].x, a[j].y * a[j].y), g);
+                gq[j & 3] = qfma(C, qfma(a[j].x, a[j].x, a[j].y * a[j].y), gq[j & 3]);
                 b[j].x = C * a[j].x;
                 b[j].y = C * a[j].y;
               }
+              g = (gq[0] + gq[1]) + (gq[2] + gq[3]);
               break;
             }
             default:
@@ -525,19 +531,20 @@ __device__ __forceinline__ void rx2_bit(float2 (&RE)[QRN], float2 (&IM)[QRN], fl
 }
 
 // Im <lam| X_RB |psi>: lam0.re psi1.im - lam0.im psi1.re + lam1.re psi0.im - lam1.im psi0.re
+// (four independent partial sums: the FMA chains stay short)
 template <int RB>
 __device__ __forceinline__ float gradx2_bit(const float2 (&RE)[QRN], const float2 (&IM)[QRN]) {
-  float acc = 0.f;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
   for (int j = 0; j < QRN; ++j) {
     if (j & (1 << RB)) continue;
     const int j1 = j | (1 << RB);
-    acc = __fmaf_rn(RE[j].y, IM[j1].x, acc);
-    acc = __fmaf_rn(-IM[j].y, RE[j1].x, acc);
-    acc = __fmaf_rn(RE[j1].y, IM[j].x, acc);
-    acc = __fmaf_rn(-IM[j1].y, RE[j].x, acc);
+    s0 = __fmaf_rn(RE[j].y, IM[j1].x, s0);
+    s1 = __fmaf_rn(-IM[j].y, RE[j1].x, s1);
+    s2 = __fmaf_rn(RE[j1].y, IM[j].x, s2);
+    s3 = __fmaf_rn(-IM[j1].y, RE[j].x, s3);
   }
-  return acc;
+  return (s0 + s1) + (s2 + s3);
 }
 
 __device__ __forceinline__ void cmul2(float2 d, float2& RE, float2& IM) {
@@ -566,6 +573,20 @@ __device__ __forceinline__ void issue_tile_il(const QPassDesc& P, uint64_t toff,
   if (P.flags & PF_NEED_CUT) issue_cut(P, toff, A, args.cut, b_cut);
 }
 
+// Tile buffers of the interleaved reverse kernel: one CTA per SM with the next
+// kIlBufs - 1 tiles' copies in flight.  Measured at 30 qubits: 2 buffers 284 ms
+// per evaluation in this kernel, 3 buffers 304 ms, and two single-buffered CTAs
+// per SM at <= 128 registers 378 ms (spills, exposed load latency).
+#ifndef QS_IL_NBUF
+#define QS_IL_NBUF 2
+#endif
+constexpr int kIlBufs = QS_IL_NBUF;
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 __global__ void __launch_bounds__(kTileThreads, 1) qaoa_il_kernel(QArgs args) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ QPassDesc P;
@@ -591,7 +612,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) qaoa_il_kernel(QArgs args) {
   const size_t buf_bytes = ((size_t)tile_n * 16 + tile_n + 127) & ~(size_t)127;
   auto buf_el = [&](int b) { return reinterpret_cast<float4*>(base + b * buf_bytes); };
   auto buf_cut = [&](int b) { return reinterpret_cast<uint8_t*>(buf_el(b) + tile_n); };
-  double* s_red = reinterpret_cast<double*>(base + 2 * buf_bytes);
+  double* s_red = reinterpret_cast<double*>(base + kIlBufs * buf_bytes);
   double* s_accd = s_red + kTileWarps;
   uint32_t* s_base = reinterpret_cast<uint32_t*>(s_accd + kQaoaMaxAcc * kTileThreads);
 
@@ -621,16 +642,23 @@ __global__ void __launch_bounds__(kTileThreads, 1) qaoa_il_kernel(QArgs args) {
   float acc_hi[kQaoaMaxAcc] = {0.f, 0.f, 0.f, 0.f}, acc_lo[kQaoaMaxAcc] = {0.f, 0.f, 0.f, 0.f};
   const int n_acc = P.n_acc;
 
+  // ring of kIlBufs buffers: tile it + j lives in buffer (it + j) % kIlBufs
   uint64_t tile = blockIdx.x;
-  if (tile < n_tiles) issue_tile_il(P, tile_offset(P, tile), args, A, s_gk, s_pk, buf_el(0), buf_cut(0));
-  cp_async_commit();
-  for (int it = 0; tile < n_tiles; ++it, tile += gridDim.x) {
-    const int cur = it & 1;
-    const uint64_t next = tile + gridDim.x;
-    if (next < n_tiles)
-      issue_tile_il(P, tile_offset(P, next), args, A, s_gk, s_pk, buf_el(cur ^ 1), buf_cut(cur ^ 1));
+#pragma unroll
+  for (int j = 0; j < kIlBufs - 1; ++j) {
+    const uint64_t t = tile + (uint64_t)j * gridDim.x;
+    if (t < n_tiles) issue_tile_il(P, tile_offset(P, t), args, A, s_gk, s_pk, buf_el(j), buf_cut(j));
     cp_async_commit();
-    cp_async_wait1();
+  }
+  for (int it = 0; tile < n_tiles; ++it, tile += gridDim.x) {
+    const int cur = it % kIlBufs;
+    {
+      const uint64_t t = tile + (uint64_t)(kIlBufs - 1) * gridDim.x;
+      const int b = (it + kIlBufs - 1) % kIlBufs;
+      if (t < n_tiles) issue_tile_il(P, tile_offset(P, t), args, A, s_gk, s_pk, buf_el(b), buf_cut(b));
+      cp_async_commit();
+    }
+    cp_async_wait_n<kIlBufs - 1>();  // this tile's copies have landed
     __syncthreads();
     float4* const be = buf_el(cur);
     const uint8_t* const bc = buf_cut(cur);
@@ -683,13 +711,15 @@ __global__ void __launch_bounds__(kTileThreads, 1) qaoa_il_kernel(QArgs args) {
             }
           } else if (st.type == QST_GRAD_COST) {
             const float2* lut = lay + E1;
+            float gq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int j = 0; j < QRN; ++j) {
               const int k = QCUT(j);
               const float C = (float)(n_edges - 2 * k);
-              g = __fmaf_rn(C, __fmaf_rn(RE[j].y, IM[j].x, -IM[j].y * RE[j].x), g);
+              gq[j & 3] = __fmaf_rn(C, __fmaf_rn(RE[j].y, IM[j].x, -IM[j].y * RE[j].x), gq[j & 3]);
               if (st.flags & QSF_LAM) cmul2(lut[k], RE[j], IM[j]);
             }
+            g = (gq[0] + gq[1]) + (gq[2] + gq[3]);
           }
 #pragma unroll
           for (int k = 0; k < kQaoaMaxAcc; ++k)
@@ -720,7 +750,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) qaoa_il_kernel(QArgs args) {
     }
     __syncthreads();
   }
-  cp_async_wait1();
+  cp_async_wait0();
 #pragma unroll
   for (int k = 0; k < kQaoaMaxAcc; ++k) s_accd[k * kTileThreads + tid] = (double)acc_hi[k] + (double)acc_lo[k];
 
@@ -743,7 +773,7 @@ size_t qaoa_il_smem_bytes(int m, int n_edges) {
   const size_t coef = ((size_t)(2 * (n_edges + 1) + 2) * kQaoaMaxLayersPerPass * 8 + 127) & ~(size_t)127;
   const size_t tile = (size_t)1 << m;
   const size_t buf = (tile * 16 + tile + 127) & ~(size_t)127;
-  return coef + 2 * buf + kTileWarps * 8 + (size_t)kQaoaMaxAcc * kTileThreads * 8 +
+  return coef + kIlBufs * buf + kTileWarps * 8 + (size_t)kQaoaMaxAcc * kTileThreads * 8 +
          (size_t)kQaoaMaxPhases * (tile >> 4) * 4;
 }
 

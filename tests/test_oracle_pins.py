@@ -146,3 +146,15 @@ def test_qaoa_5node_p4_optimum_cut():
         best = max(best, (len(edges) - r.fun) / 2)
     assert abs(best - g["cut"]) < g["print_precision"]
     assert O.maxcut_brute_force(n, edges) == 5
+
+
+@pytest.mark.parametrize("gs", [0.5, 1.0])
+def test_qaoa_p1_closed_form_matches_simulation(gs):
+    """The published depth-1 MaxCut formula (any n, triangles included) against
+    the simulated energy; the GPU tests use the same formula at 30 qubits."""
+    graphs = [(8, I.random_regular_graph(8, 3, 1)), (9, I.erdos_renyi(9, 0.5, 2)), (7, I.complete_graph(7)),
+              (10, I.erdos_renyi(10, 0.4, 5))]
+    for n, e in graphs:
+        for g, b in [(0.7, 0.3), (-1.1, 2.0), (2.5, -0.4)]:
+            E = O.qaoa_expectation_with_grad(n, e, [g], [b], gamma_scale=gs)[0]
+            assert abs(E - O.qaoa_p1_energy_closed_form(n, e, g, b, gs)) < 1e-12

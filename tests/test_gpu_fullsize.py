@@ -1,0 +1,129 @@
+"""Parity at the benchmark sizes, in the launch configuration bench.py times,
+where the oracle cannot simulate the whole problem: exact results that hold at
+any size (the depth-1 QAOA closed form, itself pinned against the oracle),
+symmetries of the QAOA energy, a circuit followed by its inverse, and sampled
+instances of the batched workload checked one by one against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import qsim_oracle as O
+from paper_2406_17248_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 5e-5, 1: 1e-11}
+
+
+@pytest.fixture(scope="module")
+def Q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_17248_gb300 import build
+    build.build()
+    from paper_2406_17248_gb300 import qsim
+    return qsim
+
+
+def _bench_graph(n=30, seed=3):
+    return I.random_regular_graph(n, 3, seed)
+
+
+def test_qaoa30_depth1_against_closed_form(Q):
+    """30 qubits, complex64, the benchmark graph, p = 1, RZZ(gamma) per edge:
+    energy against the closed form and gradients against its central
+    differences (the formula is smooth; h = 1e-5 in float64)."""
+    n, edges = 30, _bench_graph()
+    q = Q.QAOA(n, edges, 1, 0.5, Q.C64)
+    psi, lam = Q.State(n, Q.C64), Q.State(n, Q.C64)
+    sc = max(1.0, len(edges))
+    for g, b in [(0.61, 0.37), (-1.3, 2.2), (2.9, -0.8)]:
+        E, dg, db = q.expectation_with_grad(psi, lam, [g], [b])
+        Ec = O.qaoa_p1_energy_closed_form(n, edges, g, b, 0.5)
+        h = 1e-5
+        dgc = (O.qaoa_p1_energy_closed_form(n, edges, g + h, b, 0.5) -
+               O.qaoa_p1_energy_closed_form(n, edges, g - h, b, 0.5)) / (2 * h)
+        dbc = (O.qaoa_p1_energy_closed_form(n, edges, g, b + h, 0.5) -
+               O.qaoa_p1_energy_closed_form(n, edges, g, b - h, 0.5)) / (2 * h)
+        assert abs(E - Ec) <= TOL[0] * sc
+        assert abs(dg[0] - dgc) <= TOL[0] * sc
+        assert abs(db[0] - dbc) <= TOL[0] * sc
+
+
+def test_qaoa30_depth8_symmetries_and_determinism(Q):
+    """The benchmark workload (p = 8, angles U[0, pi] seed 3): E(-theta) = E(theta)
+    with negated gradients (complex conjugation of a real-start circuit);
+    shifting one mixer angle by 2 pi (RX(b + 2 pi) = -RX(b)) changes nothing;
+    two identical calls agree bit for bit."""
+    n, p, edges = 30, 8, _bench_graph()
+    a = I.uniform_params(2 * p, 3, 0.0, float(np.pi))
+    g, b = a[:p], a[p:]
+    q = Q.QAOA(n, edges, p, 0.5, Q.C64)
+    psi, lam = Q.State(n, Q.C64), Q.State(n, Q.C64)
+    sc = float(len(edges))
+    E0, dg0, db0 = q.expectation_with_grad(psi, lam, g, b)
+    E1, dg1, db1 = q.expectation_with_grad(psi, lam, g, b)
+    assert E0 == E1 and np.array_equal(dg0, dg1) and np.array_equal(db0, db1)
+    assert abs(E0) <= sc
+    Em, dgm, dbm = q.expectation_with_grad(psi, lam, -g, -b)
+    assert abs(Em - E0) <= TOL[0] * sc
+    assert np.max(np.abs(dgm + dg0)) <= TOL[0] * sc and np.max(np.abs(dbm + db0)) <= TOL[0] * sc
+    b2 = b.copy()
+    b2[3] += 2 * math.pi
+    Es, dgs, dbs = q.expectation_with_grad(psi, lam, g, b2)
+    assert abs(Es - E0) <= TOL[0] * sc
+    assert np.max(np.abs(dgs - dg0)) <= TOL[0] * sc and np.max(np.abs(dbs - db0)) <= TOL[0] * sc
+
+
+def _inverse(circ):
+    inv = []
+    for gt in reversed(circ.gates):
+        if gt.kind in ("RX", "RY", "RZ"):
+            inv.append(I.Gate(gt.kind, gt.targets, gt.ctrls, gt.param, -gt.coef, -gt.const))
+        else:  # H, X, Z (with or without controls) are their own inverses
+            inv.append(gt)
+    return I.Circuit(circ.n_qubits, inv, circ.n_params)
+
+
+@pytest.mark.parametrize("dt,fuse", [(0, 0), (0, -1), (1, 0)])
+def test_random28_then_inverse_returns_to_zero(Q, dt, fuse):
+    """The 28-qubit, 500-gate random circuit (seed 2): the norm stays 1 and the
+    circuit followed by its inverse returns |0...0> (fused passes and one kernel
+    per gate, both precisions)."""
+    n = 28
+    circ = I.random_circuit(n, 500, 2)
+    s = Q.State(n, dt).set_basis(0)
+    c = Q.circuit_from(circ).finalize(dt, fuse=fuse)
+    c.apply(s)
+    assert abs(s.norm2() - 1.0) <= (1e-5 if dt == 0 else 1e-11)
+    ci = Q.circuit_from(_inverse(circ)).finalize(dt, fuse=fuse)
+    ci.apply(s)
+    amp = s.amplitudes
+    a0 = complex(amp[0].item())
+    assert abs(a0 - 1.0) <= (2e-4 if dt == 0 else 1e-10)
+    rest = float(s.norm2() - abs(a0) ** 2)
+    assert rest <= (1e-6 if dt == 0 else 1e-20)
+
+
+def test_batched_vqe_workload_sampled_instances(Q):
+    """The 2048-instance batched workload (seed 4) in one persistent launch;
+    six sampled instances (the largest qubit count among them) against the
+    oracle's adjoint gradient."""
+    inst = I.batched_vqe(2048, seed=4)
+    b = Q.Batch(inst, Q.C64)
+    e, g = b.expectation_with_grad([it.params for it in inst])
+    nq = np.array([it.circuit.n_qubits for it in inst])
+    depth = np.array([it.circuit.n_params // (2 * it.circuit.n_qubits) for it in inst])
+    picks = [int(np.argmin(nq)), 7, 100, 1500]
+    big = np.where(nq == nq.max())[0]
+    picks.append(int(big[np.argmin(depth[big])]))
+    picks.append(int(np.where(nq == 16)[0][0]))
+    for i in picks:
+        it = inst[i]
+        psi0 = O.zero_state(it.circuit.n_qubits)
+        E, G = O.adjoint_gradient(it.circuit, it.ham, it.params, psi0)
+        sc = max(1.0, float(np.abs(it.ham.coef).sum()))
+        assert abs(e[i] - E) <= TOL[0] * sc
+        assert np.max(np.abs(g[i] - G)) <= TOL[0] * sc

@@ -182,3 +182,33 @@ def test_steps_to_ratio_engines_agree(Q):
     for i, (n, e) in enumerate(gs):
         E = O.qaoa_expectation_with_grad(n, e, init[i, :p], init[i, p:], gamma_scale=0.5)[0]
         assert abs(r2[0, i] - (len(e) - E) / 2 / O.maxcut_brute_force(n, e)) < 1e-5
+
+
+def test_gnn_bench_batch_forward_and_sampled_backward(Q):
+    """The benchmark batch (256 graphs of 26 nodes, hidden 64, 3 layers, seed 5)
+    in the launch configuration bench.py times: the forward pass of every graph
+    against the oracle; the backward pass on 24 sampled graphs whose ReLU inputs
+    keep a margin from the kink."""
+    from paper_2406_17248_gb300.qaoa_init import Initialiser
+    graphs = I.graph_set(256, 5, (26, 26))
+    init = Initialiser(p=4, seed=5)
+    _, wb = init.net.get_weights()
+    w64 = _bf16_bits_to_f64(wb)
+    gb = Q.Graphs.from_graphs(graphs)
+    y = torch.zeros(len(graphs), 8, dtype=torch.float32, device="cuda")
+    init.net.forward(gb, y)
+    y_or = G.forward(w64, *I.pack_graphs(graphs))
+    assert np.max(np.abs(y.cpu().numpy() - y_or)) <= 1e-4 * max(1.0, np.max(np.abs(y_or)))
+    sample = []
+    for i in range(len(graphs)):
+        if G.min_abs_preactivation(w64, *I.pack_graphs([graphs[i]])) > 1e-5:
+            sample.append(graphs[i])
+        if len(sample) == 24:
+            break
+    assert len(sample) == 24
+    batch = I.pack_graphs(sample)
+    dy = np.random.default_rng(3).normal(size=(len(sample), 8)).astype(np.float32)
+    grad = torch.zeros(init.net.n_weights, dtype=torch.float32, device="cuda")
+    init.net.backward(Q.Graphs(*batch), torch.as_tensor(dy).cuda(), grad)
+    g_or = G.backward(w64, *batch, dy.astype(np.float64))
+    assert np.max(np.abs(grad.cpu().numpy() - g_or)) <= 1e-4 * max(1.0, np.max(np.abs(g_or)))

@@ -9,10 +9,35 @@
 
 using namespace qs;
 
+// An instance too large for shared memory: it runs on the fused tile passes of
+// its own circuit plan, on one of the batch's lanes.
+struct BLarge {
+  int inst = 0;
+  int param_off = 0, n_params = 0;
+  qs_circuit* c = nullptr;
+  qs_ham* h = nullptr;
+};
+
+// A lane: a stream with its own psi, lam and scratch, so that large instances
+// on different lanes overlap.
+struct BLane {
+  cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr;
+  void* psi = nullptr;
+  void* lam = nullptr;
+  double* scratch = nullptr;
+};
+
 struct qs_batch {
   qs_dtype dt = QS_C64;
   cudaStream_t st = nullptr;
   int n_inst = 0;
+  int n_small = 0;                 // instances run by the persistent kernel (shared memory)
+  std::vector<BLarge> large;       // instances run on fused tile passes
+  std::vector<BLane> lanes;
+  BCoefGate* d_cg = nullptr;       // coefficient-table entries of the large instances' gates
+  int n_cg = 0;
+  cudaEvent_t ev_fill = nullptr;
   int n_params_total = 0;
   BInst* d_inst = nullptr;
   int* d_order = nullptr;
@@ -23,8 +48,6 @@ struct qs_batch {
   double* d_energy = nullptr;
   double* d_grad = nullptr;
   int* d_queue = nullptr;
-  void* d_slots = nullptr;
-  size_t slot_amps = 0;
   int smem_amps = 0;
   int grid = 0;
 };
@@ -39,8 +62,20 @@ bool batch_param_ok(int k) { return k >= QS_GATE_RX && k <= QS_GATE_RZZ; }
 
 void free_batch(qs_batch* b) {
   if (!b) return;
+  for (BLarge& L : b->large) {
+    if (L.c) qs_circuit_destroy(L.c);
+    if (L.h) qs_ham_destroy(L.h);
+  }
+  for (BLane& L : b->lanes) {
+    if (L.st) cudaStreamDestroy(L.st);
+    if (L.done) cudaEventDestroy(L.done);
+    for (void* p : {L.psi, L.lam, (void*)L.scratch})
+      if (p) cudaFree(p);
+  }
+  if (b->d_cg) cudaFree(b->d_cg);
+  if (b->ev_fill) cudaEventDestroy(b->ev_fill);
   for (void* p : {(void*)b->d_inst, (void*)b->d_order, (void*)b->d_gates, (void*)b->d_groups, (void*)b->d_terms,
-                  (void*)b->d_params, (void*)b->d_energy, (void*)b->d_grad, (void*)b->d_queue, b->d_slots})
+                  (void*)b->d_params, (void*)b->d_energy, (void*)b->d_grad, (void*)b->d_queue})
     if (p) cudaFree(p);
   delete b;
 }
@@ -50,6 +85,33 @@ qs_status upload(X** dst, const std::vector<X>& v) {
   const size_t n = std::max<size_t>(v.size(), 1);
   QS_CUDA(cudaMalloc(dst, n * sizeof(X)));
   if (!v.empty()) QS_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice));
+  return QS_OK;
+}
+
+// Energy and adjoint gradient of one large instance on a lane: psi = U|0> by
+// the forward passes, lam = H psi with E, then the reverse passes with the
+// gradient slots gathered into the instance's slice of the outputs.
+qs_status run_large(const qs_batch* b, const BLarge& I, const BLane& L, double* energies, double* grads) {
+  const CircuitPlan& P = I.c->plan;
+  const qs_ham* h = I.h;
+  const int ne = P.ne;
+  const int n_slots = (int)P.rev_slots.out.size();
+  const size_t part = (size_t)std::max(n_slots, 1) * P.grid2;
+  double* d_part = L.scratch;
+  double* d_slot = d_part + part;
+  double* d_hpart = d_slot + n_slots + 1;
+  const int hgrid = ham_grid_size(ne);
+  QS_TRY(launch_set_basis(b->dt, L.psi, ne, 0, L.st));
+  QS_TRY(run_passes(P.fwd, 0, (int)P.fwd.passes.size(), b->dt, L.psi, nullptr, P.d_coef, nullptr, d_part, ne, 0,
+                    P.grid1, P.grid2, L.st));
+  QS_TRY(launch_ham_apply(b->dt, L.psi, L.lam, ne, h->d_groups, h->n_groups, h->d_terms, d_hpart, hgrid, L.st));
+  QS_TRY(launch_reduce_slots(d_hpart, 1, hgrid, nullptr, energies + I.inst, L.st));
+  QS_TRY(run_passes(P.rev, 0, (int)P.rev.passes.size(), b->dt, L.psi, L.lam, P.d_coef, nullptr, d_part, ne, 0,
+                    P.grid1, P.grid2, L.st));
+  if (I.n_params > 0) {
+    QS_TRY(launch_reduce_slots(d_part, n_slots, P.grid2, nullptr, d_slot, L.st));
+    QS_TRY(launch_param_gather(d_slot, P.d_row, P.d_sidx, P.d_w, I.n_params, grads + I.param_off, L.st));
+  }
   return QS_OK;
 }
 
@@ -150,9 +212,12 @@ qs_status qs_batch_create(int n_inst, const int* n_qubits, const int* gate_offse
   b->n_inst = n_inst;
   b->n_params_total = param_offsets[n_inst];
   b->smem_amps = 1 << smem_n;
-  std::vector<int> order(n_inst);
-  std::iota(order.begin(), order.end(), 0);
+  // the persistent kernel's queue holds the shared-memory instances, largest first
+  std::vector<int> order;
+  for (int i = 0; i < n_inst; ++i)
+    if (inst[i].in_smem) order.push_back(i);
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return inst[a].cost > inst[c].cost; });
+  b->n_small = (int)order.size();
   qs_status s = QS_OK;
   b->grid = batch_grid_size(dtype, b->smem_amps);
   if (b->grid < 1) {
@@ -161,18 +226,77 @@ qs_status qs_batch_create(int n_inst, const int* n_qubits, const int* gate_offse
     return QS_ERR_UNSUPPORTED;
   }
   if (big_n) {
-    // per-CTA slots for psi and lam of the largest instance kept in global memory;
-    // fewer CTAs if the slots would take more than a quarter of the free memory
-    b->slot_amps = 1ull << big_n;
-    const size_t per_cta = 2 * b->slot_amps * (dtype == QS_C64 ? 8 : 16);
-    size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
-    const size_t cap = std::max<size_t>(1, (free_b / 4) / per_cta);
-    if ((size_t)b->grid > cap) b->grid = (int)cap;
-    cudaError_t e = cudaMalloc(&b->d_slots, per_cta * b->grid);
-    if (e != cudaSuccess) {
+    // instances beyond shared memory: a circuit plan and a Hamiltonian each, run
+    // on fused tile passes; their matrices are formed on the device per call
+    std::vector<BCoefGate> cg;
+    size_t need = 16;
+    int max_ne = kRegBits;
+    for (int i = 0; i < n_inst; ++i) {
+      if (inst[i].in_smem) continue;
+      BLarge L;
+      L.inst = i;
+      L.param_off = param_offsets[i];
+      L.n_params = param_offsets[i + 1] - param_offsets[i];
+      b->large.push_back(L);
+      BLarge& B = b->large.back();
+      const int n = inst[i].n;
+      if ((s = qs_circuit_create(n, &B.c)) != QS_OK) break;
+      for (int k = gate_offsets[i]; k < gate_offsets[i + 1] && s == QS_OK; ++k) {
+        const qs_batch_gate& g = gates[k];
+        int ctrls[64], nc = 0;
+        for (int q = 0; q < n; ++q)
+          if ((g.ctrl_mask >> q) & 1ull) ctrls[nc++] = q;
+        s = qs_circuit_add(B.c, g.kind, g.targets, g.n_targets, ctrls, nc, g.param, g.coef, g.constant, nullptr);
+      }
+      if (s == QS_OK) B.c->n_params = std::max(B.c->n_params, param_offsets[i + 1] - param_offsets[i]);
+      if (s == QS_OK) s = qs_circuit_finalize(B.c, dtype, nullptr);
+      if (s == QS_OK) {
+        const int t0 = term_offsets[i], nt = term_offsets[i + 1] - t0;
+        s = qs_ham_create(n, nt, nt ? xmask + t0 : nullptr, nt ? zmask + t0 : nullptr, nt ? coef + t0 : nullptr, &B.h);
+      }
+      if (s != QS_OK) break;
+      const CircuitPlan& P = B.c->plan;
+      for (size_t gi = 0; gi < B.c->gates.size(); ++gi) {
+        const HostGate& hg = B.c->gates[gi];
+        BCoefGate d;
+        d.table = P.d_coef;
+        d.off_u = P.off_u[gi];
+        d.off_ud = P.off_ud[gi];
+        d.off_a = hg.param >= 0 ? P.off_a[gi] : -1;
+        d.kind = (uint8_t)hg.kind;
+        d.nt = (uint8_t)hg.nt;
+        d.diag = (uint8_t)(P.gclass[gi] == GC_DIAG1 || P.gclass[gi] == GC_DIAG2);
+        d.pad = 0;
+        d.param = hg.param >= 0 ? param_offsets[i] + hg.param : -1;
+        d.coef = hg.coef;
+        d.constant = hg.constant;
+        cg.push_back(d);
+      }
+      const size_t n_slots = P.rev_slots.out.size();
+      need = std::max(need, std::max<size_t>(n_slots, 1) * P.grid2 + n_slots + 1 +
+                                (size_t)ham_grid_size(P.ne) + 16);
+      max_ne = std::max(max_ne, P.ne);
+    }
+    if (s == QS_OK) s = upload(&b->d_cg, cg);
+    b->n_cg = (int)cg.size();
+    if (s == QS_OK) {
+      const int n_lanes = std::min<int>(8, (int)b->large.size());
+      const size_t state_bytes = amp_bytes(dtype) << max_ne;
+      cudaError_t e = cudaEventCreateWithFlags(&b->ev_fill, cudaEventDisableTiming);
+      for (int l = 0; l < n_lanes && e == cudaSuccess; ++l) {
+        b->lanes.emplace_back();
+        BLane& L = b->lanes.back();
+        e = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMalloc(&L.psi, state_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&L.lam, state_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&L.scratch, need * sizeof(double));
+      }
+      if (e != cudaSuccess) s = cuda_fail(e, "batch lanes");
+    }
+    if (s != QS_OK) {
       free_batch(b);
-      return cuda_fail(e, "cudaMalloc(batch slots)");
+      return s;
     }
   }
   if ((s = upload(&b->d_inst, inst)) != QS_OK || (s = upload(&b->d_order, order)) != QS_OK ||
@@ -213,28 +337,42 @@ qs_status qs_batch_expectation_with_grad_device(qs_batch* b, const double* dev_p
                                                 double* dev_grads) {
   QS_CHECK(b != nullptr, "null batch");
   QS_CHECK(dev_energies != nullptr && (b->n_params_total == 0 || (dev_params && dev_grads)), "null argument");
-  QS_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(int), b->st));
-  BatchArgs a;
-  a.inst = b->d_inst;
-  a.order = b->d_order;
-  a.n_inst = b->n_inst;
-  a.gates = b->d_gates;
-  a.groups = b->d_groups;
-  a.terms = b->d_terms;
-  a.params = dev_params;
-  a.energy = dev_energies;
-  a.grad = dev_grads;
-  a.queue = b->d_queue;
-  a.slots = b->d_slots;
-  a.slot_amps = b->slot_amps;
-  a.smem_amps = b->smem_amps;
-  TraceRec* rec = trace_begin(b->st);
-  QS_TRY(launch_batch(b->dt, a, b->grid, b->st));
-  if (rec) {
-    rec->bytes = 0;
-    rec->kind = QS_TRACE_BATCH;
-    QS_CUDA(cudaEventRecord(rec->end, b->st));
+  // large instances: matrices from the device parameters, then each instance's
+  // fused passes on a lane (lanes run concurrently with each other and with the
+  // persistent kernel)
+  if (!b->large.empty()) {
+    QS_TRY(launch_batch_coef(b->dt, b->d_cg, b->n_cg, dev_params, b->st));
+    QS_CUDA(cudaEventRecord(b->ev_fill, b->st));
+    for (BLane& L : b->lanes) QS_CUDA(cudaStreamWaitEvent(L.st, b->ev_fill, 0));
+    for (size_t k = 0; k < b->large.size(); ++k)
+      QS_TRY(run_large(b, b->large[k], b->lanes[k % b->lanes.size()], dev_energies, dev_grads));
+    for (BLane& L : b->lanes) QS_CUDA(cudaEventRecord(L.done, L.st));
   }
+  if (b->n_small > 0) {
+    QS_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(int), b->st));
+    BatchArgs a;
+    a.inst = b->d_inst;
+    a.order = b->d_order;
+    a.n_inst = b->n_small;
+    a.gates = b->d_gates;
+    a.groups = b->d_groups;
+    a.terms = b->d_terms;
+    a.params = dev_params;
+    a.energy = dev_energies;
+    a.grad = dev_grads;
+    a.queue = b->d_queue;
+    a.slots = nullptr;
+    a.slot_amps = 0;
+    a.smem_amps = b->smem_amps;
+    TraceRec* rec = trace_begin(b->st);
+    QS_TRY(launch_batch(b->dt, a, b->grid, b->st));
+    if (rec) {
+      rec->bytes = 0;
+      rec->kind = QS_TRACE_BATCH;
+      QS_CUDA(cudaEventRecord(rec->end, b->st));
+    }
+  }
+  for (BLane& L : b->lanes) QS_CUDA(cudaStreamWaitEvent(b->st, L.done, 0));
   return QS_OK;
 }
 

@@ -43,6 +43,18 @@ struct BatchArgs {
 };
 
 qs_status launch_batch(qs_dtype dt, const BatchArgs& a, int grid, cudaStream_t st);
+
+// One gate of an instance that runs on fused tile passes: where its matrices go
+// in that instance's coefficient table (the layout the tile planner assigned).
+struct BCoefGate {
+  void* table;    // the instance's coefficient table (complex of the batch dtype)
+  int off_u, off_ud, off_a;  // U, U^dag and (parametric gates) A = dU U^dag; -1 = none
+  uint8_t kind, nt, diag, pad;
+  int param;      // index into the concatenated parameters, -1 = fixed angle
+  double coef, constant;
+};
+// Fill the tables of every such gate from the device parameters.
+qs_status launch_batch_coef(qs_dtype dt, const BCoefGate* g, int n, const double* params, cudaStream_t st);
 int batch_grid_size(qs_dtype dt, int smem_amps);
 size_t batch_smem_bytes(qs_dtype dt, int smem_amps);
 constexpr int kBatchThreads = 512;

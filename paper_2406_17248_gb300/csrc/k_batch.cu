@@ -322,7 +322,64 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a) {
   }
 }
 
+// Coefficient tables of the instances that run on fused tile passes, formed on
+// the device from the device parameters (the same layout the host fills for a
+// single circuit: diagonal gates store their diagonal, RX stores (cos, sin) of
+// the half angle, other gates the full matrix; U^dag and A = dU U^dag beside).
+template <class V>
+__global__ void batch_coef_kernel(const BCoefGate* __restrict__ gates, int n, const double* __restrict__ params) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const BCoefGate g = gates[i];
+  const double th = g.param < 0 ? g.constant : g.constant + g.coef * params[g.param];
+  double2 U[16], A[16];
+  bgate_matrix<double2, double>(g.kind, th, U);
+  V* tab = reinterpret_cast<V*>(g.table);
+  auto put = [&](int off, int k, double re, double im) {
+    V v;
+    v.x = (decltype(v.x))re;
+    v.y = (decltype(v.x))im;
+    tab[off + k] = v;
+  };
+  const int d = g.nt == 2 ? 4 : 2;
+  if (g.diag) {
+    for (int k = 0; k < d; ++k) {
+      put(g.off_u, k, U[k * d + k].x, U[k * d + k].y);
+      put(g.off_ud, k, U[k * d + k].x, -U[k * d + k].y);
+    }
+  } else if (g.kind == QS_GATE_RX) {
+    double s, c;
+    sincos(0.5 * th, &s, &c);
+    put(g.off_u, 0, c, s);
+    put(g.off_ud, 0, c, -s);
+  } else {
+    for (int r = 0; r < d; ++r)
+      for (int col = 0; col < d; ++col) {
+        put(g.off_u, r * d + col, U[r * d + col].x, U[r * d + col].y);
+        put(g.off_ud, r * d + col, U[col * d + r].x, -U[col * d + r].y);
+      }
+  }
+  if (g.off_a >= 0) {
+    bgate_generator<double2, double>(g.kind, A);
+    if (g.diag)
+      for (int k = 0; k < d; ++k) put(g.off_a, k, A[k * d + k].x, A[k * d + k].y);
+    else
+      for (int k = 0; k < d * d; ++k) put(g.off_a, k, A[k].x, A[k].y);
+  }
+}
+
 }  // namespace
+
+qs_status launch_batch_coef(qs_dtype dt, const BCoefGate* g, int n, const double* params, cudaStream_t st) {
+  if (n <= 0) return QS_OK;
+  const int threads = 128, blocks = (n + threads - 1) / threads;
+  if (dt == QS_C64)
+    batch_coef_kernel<float2><<<blocks, threads, 0, st>>>(g, n, params);
+  else
+    batch_coef_kernel<double2><<<blocks, threads, 0, st>>>(g, n, params);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
 
 size_t batch_smem_bytes(qs_dtype dt, int smem_amps) { return 2 * (size_t)smem_amps * (dt == QS_C64 ? 8 : 16); }
 

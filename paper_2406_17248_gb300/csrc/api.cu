@@ -403,6 +403,8 @@ static std::vector<TraceRec> g_trace;
 static size_t g_trace_used = 0;
 constexpr size_t kTraceMax = 65536;
 
+bool trace_active() { return g_trace_on; }
+
 TraceRec* trace_begin(cudaStream_t st) {
   if (!g_trace_on) return nullptr;
   std::lock_guard<std::mutex> lk(g_trace_mu);

@@ -20,6 +20,10 @@ struct BLarge {
 
 // A lane: a stream with its own psi, lam and scratch, so that large instances
 // on different lanes overlap.
+#ifndef QS_BATCH_LANES
+#define QS_BATCH_LANES 32
+#endif
+constexpr int kBatchLanes = QS_BATCH_LANES;
 struct BLane {
   cudaStream_t st = nullptr;
   cudaEvent_t done = nullptr;
@@ -38,6 +42,12 @@ struct qs_batch {
   BCoefGate* d_cg = nullptr;       // coefficient-table entries of the large instances' gates
   int n_cg = 0;
   cudaEvent_t ev_fill = nullptr;
+  // the whole call (coefficients, lanes, persistent kernel) captured once as a
+  // CUDA graph on the batch's own parameter/output buffers and replayed
+  cudaGraphExec_t graph = nullptr;
+  bool graph_failed = false;
+  cudaStream_t cap_st = nullptr;   // the graph's stream (capture needs a non-default stream)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int n_params_total = 0;
   BInst* d_inst = nullptr;
   int* d_order = nullptr;
@@ -74,6 +84,10 @@ void free_batch(qs_batch* b) {
   }
   if (b->d_cg) cudaFree(b->d_cg);
   if (b->ev_fill) cudaEventDestroy(b->ev_fill);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap_st) cudaStreamDestroy(b->cap_st);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
   for (void* p : {(void*)b->d_inst, (void*)b->d_order, (void*)b->d_gates, (void*)b->d_groups, (void*)b->d_terms,
                   (void*)b->d_params, (void*)b->d_energy, (void*)b->d_grad, (void*)b->d_queue})
     if (p) cudaFree(p);
@@ -116,6 +130,48 @@ qs_status run_large(const qs_batch* b, const BLarge& I, const BLane& L, double* 
 }
 
 }  // namespace
+
+// Enqueue one evaluation of every instance on st (lanes forked and joined).
+static qs_status issue_all(qs_batch* b, cudaStream_t st, const double* dev_params, double* dev_energies,
+                           double* dev_grads) {
+  // large instances: matrices from the device parameters, then each instance's
+  // fused passes on a lane (lanes run concurrently with each other and with the
+  // persistent kernel)
+  if (!b->large.empty()) {
+    QS_TRY(launch_batch_coef(b->dt, b->d_cg, b->n_cg, dev_params, st));
+    QS_CUDA(cudaEventRecord(b->ev_fill, st));
+    for (BLane& L : b->lanes) QS_CUDA(cudaStreamWaitEvent(L.st, b->ev_fill, 0));
+    for (size_t k = 0; k < b->large.size(); ++k)
+      QS_TRY(run_large(b, b->large[k], b->lanes[k % b->lanes.size()], dev_energies, dev_grads));
+    for (BLane& L : b->lanes) QS_CUDA(cudaEventRecord(L.done, L.st));
+  }
+  if (b->n_small > 0) {
+    QS_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(int), st));
+    BatchArgs a;
+    a.inst = b->d_inst;
+    a.order = b->d_order;
+    a.n_inst = b->n_small;
+    a.gates = b->d_gates;
+    a.groups = b->d_groups;
+    a.terms = b->d_terms;
+    a.params = dev_params;
+    a.energy = dev_energies;
+    a.grad = dev_grads;
+    a.queue = b->d_queue;
+    a.slots = nullptr;
+    a.slot_amps = 0;
+    a.smem_amps = b->smem_amps;
+    TraceRec* rec = trace_begin(st);
+    QS_TRY(launch_batch(b->dt, a, b->grid, st));
+    if (rec) {
+      rec->bytes = 0;
+      rec->kind = QS_TRACE_BATCH;
+      QS_CUDA(cudaEventRecord(rec->end, st));
+    }
+  }
+  for (BLane& L : b->lanes) QS_CUDA(cudaStreamWaitEvent(st, L.done, 0));
+  return QS_OK;
+}
 
 extern "C" {
 
@@ -280,7 +336,11 @@ qs_status qs_batch_create(int n_inst, const int* n_qubits, const int* gate_offse
     if (s == QS_OK) s = upload(&b->d_cg, cg);
     b->n_cg = (int)cg.size();
     if (s == QS_OK) {
-      const int n_lanes = std::min<int>(8, (int)b->large.size());
+      // instances of 14-17 qubits have only 4-32 tiles per pass: many lanes in
+      // flight keep the SMs busy; the largest instances are dealt out first
+      std::stable_sort(b->large.begin(), b->large.end(),
+                       [&](const BLarge& x, const BLarge& y) { return inst[x.inst].cost > inst[y.inst].cost; });
+      const int n_lanes = std::min<int>(kBatchLanes, (int)b->large.size());
       const size_t state_bytes = amp_bytes(dtype) << max_ne;
       cudaError_t e = cudaEventCreateWithFlags(&b->ev_fill, cudaEventDisableTiming);
       for (int l = 0; l < n_lanes && e == cudaSuccess; ++l) {
@@ -337,43 +397,49 @@ qs_status qs_batch_expectation_with_grad_device(qs_batch* b, const double* dev_p
                                                 double* dev_grads) {
   QS_CHECK(b != nullptr, "null batch");
   QS_CHECK(dev_energies != nullptr && (b->n_params_total == 0 || (dev_params && dev_grads)), "null argument");
-  // large instances: matrices from the device parameters, then each instance's
-  // fused passes on a lane (lanes run concurrently with each other and with the
-  // persistent kernel)
-  if (!b->large.empty()) {
-    QS_TRY(launch_batch_coef(b->dt, b->d_cg, b->n_cg, dev_params, b->st));
-    QS_CUDA(cudaEventRecord(b->ev_fill, b->st));
-    for (BLane& L : b->lanes) QS_CUDA(cudaStreamWaitEvent(L.st, b->ev_fill, 0));
-    for (size_t k = 0; k < b->large.size(); ++k)
-      QS_TRY(run_large(b, b->large[k], b->lanes[k % b->lanes.size()], dev_energies, dev_grads));
-    for (BLane& L : b->lanes) QS_CUDA(cudaEventRecord(L.done, L.st));
-  }
-  if (b->n_small > 0) {
-    QS_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(int), b->st));
-    BatchArgs a;
-    a.inst = b->d_inst;
-    a.order = b->d_order;
-    a.n_inst = b->n_small;
-    a.gates = b->d_gates;
-    a.groups = b->d_groups;
-    a.terms = b->d_terms;
-    a.params = dev_params;
-    a.energy = dev_energies;
-    a.grad = dev_grads;
-    a.queue = b->d_queue;
-    a.slots = nullptr;
-    a.slot_amps = 0;
-    a.smem_amps = b->smem_amps;
-    TraceRec* rec = trace_begin(b->st);
-    QS_TRY(launch_batch(b->dt, a, b->grid, b->st));
-    if (rec) {
-      rec->bytes = 0;
-      rec->kind = QS_TRACE_BATCH;
-      QS_CUDA(cudaEventRecord(rec->end, b->st));
+  // Many large instances mean tens of thousands of small launches: capture the
+  // call once as a graph on the batch's own buffers and replay it (not while
+  // launches are being traced, whose events must stay per launch).
+  if (!b->large.empty() && !trace_active() && !b->graph_failed) {
+    if (!b->graph) {
+      cudaGraph_t g = nullptr;
+      qs_status s = QS_OK;
+      if (cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+          cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        s = QS_ERR_CUDA;
+      } else {
+        s = issue_all(b, b->cap_st, b->d_params, b->d_energy, b->d_grad);
+        if (cudaStreamEndCapture(b->cap_st, &g) != cudaSuccess) s = QS_ERR_CUDA;
+      }
+      if (s == QS_OK && cudaGraphInstantiate(&b->graph, g, 0) != cudaSuccess) s = QS_ERR_CUDA;
+      if (g) cudaGraphDestroy(g);
+      if (s != QS_OK) {
+        (void)cudaGetLastError();
+        b->graph = nullptr;
+        b->graph_failed = true;  // fall back to direct launches from now on
+      }
+    }
+    if (b->graph) {
+      // ordered after the caller's stream, and the caller's stream after it
+      const size_t np = (size_t)b->n_params_total * sizeof(double);
+      QS_CUDA(cudaEventRecord(b->ev_in, b->st));
+      QS_CUDA(cudaStreamWaitEvent(b->cap_st, b->ev_in, 0));
+      if (np && dev_params != b->d_params)
+        QS_CUDA(cudaMemcpyAsync(b->d_params, dev_params, np, cudaMemcpyDeviceToDevice, b->cap_st));
+      QS_CUDA(cudaGraphLaunch(b->graph, b->cap_st));
+      if (dev_energies != b->d_energy)
+        QS_CUDA(cudaMemcpyAsync(dev_energies, b->d_energy, (size_t)b->n_inst * sizeof(double),
+                                cudaMemcpyDeviceToDevice, b->cap_st));
+      if (np && dev_grads != b->d_grad)
+        QS_CUDA(cudaMemcpyAsync(dev_grads, b->d_grad, np, cudaMemcpyDeviceToDevice, b->cap_st));
+      QS_CUDA(cudaEventRecord(b->ev_out, b->cap_st));
+      QS_CUDA(cudaStreamWaitEvent(b->st, b->ev_out, 0));
+      return QS_OK;
     }
   }
-  for (BLane& L : b->lanes) QS_CUDA(cudaStreamWaitEvent(b->st, L.done, 0));
-  return QS_OK;
+  return issue_all(b, b->st, dev_params, dev_energies, dev_grads);
 }
 
 qs_status qs_batch_expectation_with_grad(qs_batch* b, const double* params, double* energies, double* grads) {

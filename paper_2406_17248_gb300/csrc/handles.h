@@ -81,6 +81,7 @@ struct TraceRec {
 };
 // Event pair for the next launch on `st` when tracing is on, else nullptr.
 TraceRec* trace_begin(cudaStream_t st);
+bool trace_active();
 qs_status trace_enable(int on);
 qs_status trace_read(int max, int* n, double* ms, double* bytes, int* kinds);
 qs_status ensure_scratch(qs_state* s, size_t ndoubles);

@@ -81,6 +81,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 constexpr int RN = 1 << kRegBits;
+constexpr int kTileOpStage = 256;  // ops of a pass staged in shared memory (more: read from global)
 
 struct TileKArgs {
   void* psi;
@@ -105,14 +106,16 @@ __device__ __forceinline__ uint32_t off_of(const uint32_t (&rm)[kRegBits]) {
   return o;
 }
 
-template <class V, int RB>
+// JC: the op has controls among the register bits (mask jc over the register
+// index); without them the whole loop is predicated by `ok` alone.
+template <class V, int RB, bool JC>
 __device__ __forceinline__ void op_dense1(V (&a)[RN], const V* M, uint32_t jc, bool ok) {
   const V m00 = M[0], m01 = M[1], m10 = M[2], m11 = M[3];
 #pragma unroll
   for (int j = 0; j < RN; ++j) {
     if (j & (1 << RB)) continue;
     const int j1 = j | (1 << RB);
-    if (ok && ((uint32_t)j & jc) == jc) {
+    if (ok && (!JC || ((uint32_t)j & jc) == jc)) {
       V x0 = a[j], x1 = a[j1];
       a[j] = cfma(m01, x1, cmul(m00, x0));
       a[j1] = cfma(m11, x1, cmul(m10, x0));
@@ -120,7 +123,7 @@ __device__ __forceinline__ void op_dense1(V (&a)[RN], const V* M, uint32_t jc, b
   }
 }
 
-template <class V, int RB>
+template <class V, int RB, bool JC>
 __device__ __forceinline__ void op_rx(V (&a)[RN], V cs, uint32_t jc, bool ok) {
   // [[c, -is], [-is, c]]: out0 = c x0 - i s x1, out1 = c x1 - i s x0
   const auto c = cs.x, s = cs.y;
@@ -128,7 +131,7 @@ __device__ __forceinline__ void op_rx(V (&a)[RN], V cs, uint32_t jc, bool ok) {
   for (int j = 0; j < RN; ++j) {
     if (j & (1 << RB)) continue;
     const int j1 = j | (1 << RB);
-    if (ok && ((uint32_t)j & jc) == jc) {
+    if (ok && (!JC || ((uint32_t)j & jc) == jc)) {
       V x0 = a[j], x1 = a[j1], y0, y1;
       y0.x = fmaT(c, x0.x, s * x1.y);
       y0.y = fmaT(c, x0.y, -s * x1.x);
@@ -140,12 +143,12 @@ __device__ __forceinline__ void op_rx(V (&a)[RN], V cs, uint32_t jc, bool ok) {
   }
 }
 
-template <class V, int RB0, int RB1>
+template <class V, int RB0, int RB1, bool JC>
 __device__ __forceinline__ void op_dense2(V (&a)[RN], const V* M, uint32_t jc, bool ok) {
 #pragma unroll
   for (int j = 0; j < RN; ++j) {
     if (j & ((1 << RB0) | (1 << RB1))) continue;
-    if (!(ok && ((uint32_t)j & jc) == jc)) continue;
+    if (!(ok && (!JC || ((uint32_t)j & jc) == jc))) continue;
     const int idx[4] = {j, j | (1 << RB0), j | (1 << RB1), j | (1 << RB0) | (1 << RB1)};
     V x[4] = {a[idx[0]], a[idx[1]], a[idx[2]], a[idx[3]]};
 #pragma unroll
@@ -159,7 +162,7 @@ __device__ __forceinline__ void op_dense2(V (&a)[RN], const V* M, uint32_t jc, b
   }
 }
 
-template <class V, int RB>
+template <class V, int RB, bool JC>
 __device__ __forceinline__ auto grad_dense1(const V (&a)[RN], const V (&b)[RN], const V* A, uint32_t jc,
                                             bool ok) -> decltype(V::x) {
   decltype(V::x) acc = 0;
@@ -168,7 +171,7 @@ __device__ __forceinline__ auto grad_dense1(const V (&a)[RN], const V (&b)[RN], 
   for (int j = 0; j < RN; ++j) {
     if (j & (1 << RB)) continue;
     const int j1 = j | (1 << RB);
-    if (ok && ((uint32_t)j & jc) == jc) {
+    if (ok && (!JC || ((uint32_t)j & jc) == jc)) {
       V y0 = cfma(a01, a[j1], cmul(a00, a[j]));
       V y1 = cfma(a11, a[j1], cmul(a10, a[j]));
       acc += re_conj_mul(b[j], y0) + re_conj_mul(b[j1], y1);
@@ -177,14 +180,14 @@ __device__ __forceinline__ auto grad_dense1(const V (&a)[RN], const V (&b)[RN], 
   return 2 * acc;
 }
 
-template <class V, int RB0, int RB1>
+template <class V, int RB0, int RB1, bool JC>
 __device__ __forceinline__ auto grad_dense2(const V (&a)[RN], const V (&b)[RN], const V* M, uint32_t jc,
                                             bool ok) -> decltype(V::x) {
   decltype(V::x) acc = 0;
 #pragma unroll
   for (int j = 0; j < RN; ++j) {
     if (j & ((1 << RB0) | (1 << RB1))) continue;
-    if (!(ok && ((uint32_t)j & jc) == jc)) continue;
+    if (!(ok && (!JC || ((uint32_t)j & jc) == jc))) continue;
     const int idx[4] = {j, j | (1 << RB0), j | (1 << RB1), j | (1 << RB0) | (1 << RB1)};
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -198,7 +201,7 @@ __device__ __forceinline__ auto grad_dense2(const V (&a)[RN], const V (&b)[RN], 
   return 2 * acc;
 }
 
-template <class V, int RB>
+template <class V, int RB, bool JC>
 __device__ __forceinline__ auto grad_x(const V (&a)[RN], const V (&b)[RN], uint32_t jc, bool ok)
     -> decltype(V::x) {
   decltype(V::x) acc = 0;
@@ -206,7 +209,7 @@ __device__ __forceinline__ auto grad_x(const V (&a)[RN], const V (&b)[RN], uint3
   for (int j = 0; j < RN; ++j) {
     if (j & (1 << RB)) continue;
     const int j1 = j | (1 << RB);
-    if (ok && ((uint32_t)j & jc) == jc) acc += im_conj_mul(b[j], a[j1]) + im_conj_mul(b[j1], a[j]);
+    if (ok && (!JC || ((uint32_t)j & jc) == jc)) acc += im_conj_mul(b[j], a[j1]) + im_conj_mul(b[j1], a[j]);
   }
   return acc;
 }
@@ -235,8 +238,11 @@ __device__ __forceinline__ auto grad_x(const V (&a)[RN], const V (&b)[RN], uint3
     default: CALL(3, 2); break;          \
   }
 
+#ifndef QS_TILE_C64_MINB
+#define QS_TILE_C64_MINB 2
+#endif
 template <class T, int NS>
-__global__ void __launch_bounds__(kTileThreads) tile_pass_kernel(TileKArgs args) {
+__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? QS_TILE_C64_MINB : 1) tile_pass_kernel(TileKArgs args) {
   using V = typename VecT<T>::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
 
@@ -252,10 +258,33 @@ __global__ void __launch_bounds__(kTileThreads) tile_pass_kernel(TileKArgs args)
   uint8_t* s_cut = reinterpret_cast<uint8_t*>(s_psi + NS * tile_n);
   double* s_acc = reinterpret_cast<double*>(s_cut + ((flags & PF_NEED_CUT) ? tile_n : 0));
   uint64_t* s_hi = reinterpret_cast<uint64_t*>(s_acc + P.n_slots * kTileWarps);  // hiA[64], hiB[64]
+  DevOp* s_ops = reinterpret_cast<DevOp*>(s_hi + 128);  // the pass's ops, when they fit
 
   for (int i = tid; i < 64; i += blockDim.x) {
     s_hi[i] = P.hiA[i];
     s_hi[64 + i] = P.hiB[i];
+  }
+  // Sub-cube bases of every phase: the local index l0 of sub-cube u deposits u's
+  // bits into the phase's Q bits; split u = lo (4 bits) | hi (up to 5 bits) and
+  // tabulate each half, so l0 = tab[lo] | tab[16 + hi].
+  uint32_t* s_l0 = reinterpret_cast<uint32_t*>(s_ops + kTileOpStage);  // [phase][48]
+  for (int e = tid; e < P.n_phases * 48; e += blockDim.x) {
+    const int ph = e / 48, k = e % 48;
+    const DevPhase& PH = args.phases[P.phase_begin + ph];
+    const int first = k < 16 ? 0 : 4;
+    const uint32_t bits = k < 16 ? (uint32_t)k : (uint32_t)(k - 16);
+    uint32_t v = 0;
+    for (int i = 0; i < 5 && first + i < PH.nq; ++i)
+      if ((bits >> i) & 1u) v |= 1u << PH.Q[first + i];
+    s_l0[e] = (k < 16 || bits < 32) ? v : 0u;
+  }
+  const int op_lo = P.n_phases ? args.phases[P.phase_begin].op_begin : 0;
+  const int op_hi = P.n_phases ? args.phases[P.phase_begin + P.n_phases - 1].op_end : 0;
+  const bool ops_staged = op_hi - op_lo <= kTileOpStage;
+  if (ops_staged) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(args.ops + op_lo);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(s_ops);
+    for (int i = tid; i < (op_hi - op_lo) * (int)(sizeof(DevOp) / 4); i += blockDim.x) dst[i] = src[i];
   }
   for (int i = tid; i < P.n_slots * kTileWarps; i += blockDim.x) s_acc[i] = 0.0;
   __syncthreads();
@@ -327,31 +356,30 @@ __global__ void __launch_bounds__(kTileThreads) tile_pass_kernel(TileKArgs args)
     // ---------------------------------------------------------------- phases
     for (int ph = 0; ph < P.n_phases; ++ph) {
       const DevPhase& PH = args.phases[P.phase_begin + ph];
-      uint32_t rm[kRegBits];
+      uint32_t rm[kRegBits], sm[kRegBits];
 #pragma unroll
-      for (int i = 0; i < kRegBits; ++i) rm[i] = 1u << PH.R[i];
+      for (int i = 0; i < kRegBits; ++i) {
+        rm[i] = 1u << PH.R[i];
+        sm[i] = swz<T>(rm[i]);  // the swizzle is linear over GF(2): positions XOR
+      }
+      const uint32_t* l0tab = s_l0 + ph * 48;
       const uint32_t nsub = tile_n >> kRegBits;
       const uint32_t iters = (nsub + blockDim.x - 1) / blockDim.x;
       for (uint32_t it = 0; it < iters; ++it) {
         const uint32_t u = tid + it * blockDim.x;
         const bool active = u < nsub;
-        uint32_t l0 = 0;
-        for (int i = 0; i < PH.nq; ++i) l0 |= ((u >> i) & 1u) << PH.Q[i];
+        const uint32_t l0 = active ? (l0tab[u & 15u] | l0tab[16 + ((u >> 4) & 31u)]) : 0u;
+        const uint32_t p0 = swz<T>(l0);
+        // position and local index of register element j (constants per j)
+#define TPOS(j) \
+  (p0 ^ (((j) & 1) ? sm[0] : 0u) ^ (((j) & 2) ? sm[1] : 0u) ^ (((j) & 4) ? sm[2] : 0u) ^ (((j) & 8) ? sm[3] : 0u))
+#define TLOC(j) \
+  (l0 | (((j) & 1) ? rm[0] : 0u) | (((j) & 2) ? rm[1] : 0u) | (((j) & 4) ? rm[2] : 0u) | (((j) & 8) ? rm[3] : 0u))
         V a[RN], b[RN];
-        uint32_t lj[RN];
-#pragma unroll
-        for (int j = 0; j < RN; ++j) {
-          lj[j] = 0;
-          if (j & 1) lj[j] |= rm[0];
-          if (j & 2) lj[j] |= rm[1];
-          if (j & 4) lj[j] |= rm[2];
-          if (j & 8) lj[j] |= rm[3];
-          lj[j] |= l0;
-        }
         if (active) {
 #pragma unroll
           for (int j = 0; j < RN; ++j) {
-            const uint32_t p = swz<T>(lj[j]);
+            const uint32_t p = TPOS(j);
             a[j] = s_psi[p];
             if (NS == 2) b[j] = s_lam[p];
           }
@@ -359,11 +387,11 @@ __global__ void __launch_bounds__(kTileThreads) tile_pass_kernel(TileKArgs args)
 #pragma unroll
           for (int j = 0; j < RN; ++j) {
             a[j].x = a[j].y = 0;
-            b[j].x = b[j].y = 0;
+            if (NS == 2) b[j].x = b[j].y = 0;
           }
         }
         for (int o = PH.op_begin; o < PH.op_end; ++o) {
-          const DevOp op = args.ops[o];
+          const DevOp op = ops_staged ? s_ops[o - op_lo] : args.ops[o];
           const bool ok = active && ((l0 & op.lc) == op.lc) && ((toff & op.gc) == op.gc);
           const uint32_t jc = op.jc;
           const V* M = coef + op.coef;
@@ -371,28 +399,34 @@ __global__ void __launch_bounds__(kTileThreads) tile_pass_kernel(TileKArgs args)
           bool has_contrib = false;
           switch (op.type) {
             case OP_DENSE1: {
-#define CALL(R)                              \
-  op_dense1<V, R>(a, M, jc, ok);             \
-  if (NS == 2 && (op.flags & OPF_LAM)) op_dense1<V, R>(b, M, jc, ok);
+#define CALLJ(R, J)                          \
+  op_dense1<V, R, J>(a, M, jc, ok);          \
+  if (NS == 2 && (op.flags & OPF_LAM)) op_dense1<V, R, J>(b, M, jc, ok);
+#define CALL(R) if (jc) { CALLJ(R, true) } else { CALLJ(R, false) }
               QS_RB_SWITCH(op.rb0, CALL)
 #undef CALL
+#undef CALLJ
               break;
             }
             case OP_RX: {
               const V cs = M[0];
-#define CALL(R)                            \
-  op_rx<V, R>(a, cs, jc, ok);              \
-  if (NS == 2 && (op.flags & OPF_LAM)) op_rx<V, R>(b, cs, jc, ok);
+#define CALLJ(R, J)                        \
+  op_rx<V, R, J>(a, cs, jc, ok);           \
+  if (NS == 2 && (op.flags & OPF_LAM)) op_rx<V, R, J>(b, cs, jc, ok);
+#define CALL(R) if (jc) { CALLJ(R, true) } else { CALLJ(R, false) }
               QS_RB_SWITCH(op.rb0, CALL)
 #undef CALL
+#undef CALLJ
               break;
             }
             case OP_DENSE2: {
-#define CALL(R0, R1)                             \
-  op_dense2<V, R0, R1>(a, M, jc, ok);            \
-  if (NS == 2 && (op.flags & OPF_LAM)) op_dense2<V, R0, R1>(b, M, jc, ok);
+#define CALLJ(R0, R1, J)                         \
+  op_dense2<V, R0, R1, J>(a, M, jc, ok);         \
+  if (NS == 2 && (op.flags & OPF_LAM)) op_dense2<V, R0, R1, J>(b, M, jc, ok);
+#define CALL(R0, R1) if (jc) { CALLJ(R0, R1, true) } else { CALLJ(R0, R1, false) }
               QS_RB2_SWITCH(op.rb0, op.rb1, CALL)
 #undef CALL
+#undef CALLJ
               break;
             }
             case OP_DIAG:
@@ -402,13 +436,13 @@ __global__ void __launch_bounds__(kTileThreads) tile_pass_kernel(TileKArgs args)
 #pragma unroll
               for (int j = 0; j < RN; ++j) {
                 if (!(ok && ((uint32_t)j & jc) == jc)) continue;
-                const uint32_t b0 = op.dloc[0] >= 0 ? (lj[j] >> op.dloc[0]) & 1u : (uint32_t)g0;
-                const uint32_t b1 = op.dloc[1] >= 0 ? (lj[j] >> op.dloc[1]) & 1u : (uint32_t)g1;
+                const uint32_t b0 = op.dloc[0] >= 0 ? (TLOC(j) >> op.dloc[0]) & 1u : (uint32_t)g0;
+                const uint32_t b1 = op.dloc[1] >= 0 ? (TLOC(j) >> op.dloc[1]) & 1u : (uint32_t)g1;
                 const V d = M[b0 + 2 * b1];
                 if (op.type == OP_DIAG) {
                   a[j] = cmul(d, a[j]);
                   if (NS == 2 && (op.flags & OPF_LAM)) b[j] = cmul(d, b[j]);
-                } else {
+                } else if (NS == 2) {
                   contrib += 2 * re_conj_mul(b[j], cmul(d, a[j]));
                 }
               }
@@ -416,23 +450,30 @@ __global__ void __launch_bounds__(kTileThreads) tile_pass_kernel(TileKArgs args)
               break;
             }
             case OP_GRAD1: {
-#define CALL(R) contrib = grad_dense1<V, R>(a, b, M, jc, ok);
-              QS_RB_SWITCH(op.rb0, CALL)
+              if (NS == 2) {
+#define CALL(R) contrib = jc ? grad_dense1<V, R, true>(a, b, M, jc, ok) : grad_dense1<V, R, false>(a, b, M, jc, ok);
+                QS_RB_SWITCH(op.rb0, CALL)
 #undef CALL
+              }
               has_contrib = true;
               break;
             }
             case OP_GRAD2: {
-#define CALL(R0, R1) contrib = grad_dense2<V, R0, R1>(a, b, M, jc, ok);
-              QS_RB2_SWITCH(op.rb0, op.rb1, CALL)
+              if (NS == 2) {
+#define CALL(R0, R1) \
+  contrib = jc ? grad_dense2<V, R0, R1, true>(a, b, M, jc, ok) : grad_dense2<V, R0, R1, false>(a, b, M, jc, ok);
+                QS_RB2_SWITCH(op.rb0, op.rb1, CALL)
 #undef CALL
+              }
               has_contrib = true;
               break;
             }
             case OP_GRADX: {
-#define CALL(R) contrib = grad_x<V, R>(a, b, jc, ok);
-              QS_RB_SWITCH(op.rb0, CALL)
+              if (NS == 2) {
+#define CALL(R) contrib = jc ? grad_x<V, R, true>(a, b, jc, ok) : grad_x<V, R, false>(a, b, jc, ok);
+                QS_RB_SWITCH(op.rb0, CALL)
 #undef CALL
+              }
               has_contrib = true;
               break;
             }
@@ -440,7 +481,7 @@ __global__ void __launch_bounds__(kTileThreads) tile_pass_kernel(TileKArgs args)
               if (active) {
 #pragma unroll
                 for (int j = 0; j < RN; ++j) {
-                  const V d = M[s_cut[lj[j]]];
+                  const V d = M[s_cut[TLOC(j)]];
                   a[j] = cmul(d, a[j]);
                   if (NS == 2 && (op.flags & OPF_LAM)) b[j] = cmul(d, b[j]);
                 }
@@ -448,10 +489,10 @@ __global__ void __launch_bounds__(kTileThreads) tile_pass_kernel(TileKArgs args)
               break;
             }
             case OP_GRADCOST: {
-              if (active) {
+              if (NS == 2 && active) {
 #pragma unroll
                 for (int j = 0; j < RN; ++j) {
-                  const T C = (T)(n_edges - 2 * (int)s_cut[lj[j]]);
+                  const T C = (T)(n_edges - 2 * (int)s_cut[TLOC(j)]);
                   contrib += C * im_conj_mul(b[j], a[j]);
                 }
               }
@@ -462,10 +503,12 @@ __global__ void __launch_bounds__(kTileThreads) tile_pass_kernel(TileKArgs args)
               if (active) {
 #pragma unroll
                 for (int j = 0; j < RN; ++j) {
-                  const T C = (T)(n_edges - 2 * (int)s_cut[lj[j]]);
+                  const T C = (T)(n_edges - 2 * (int)s_cut[TLOC(j)]);
                   contrib += C * fmaT(a[j].x, a[j].x, a[j].y * a[j].y);
-                  b[j].x = C * a[j].x;
-                  b[j].y = C * a[j].y;
+                  if (NS == 2) {
+                    b[j].x = C * a[j].x;
+                    b[j].y = C * a[j].y;
+                  }
                 }
               }
               has_contrib = true;
@@ -482,11 +525,13 @@ __global__ void __launch_bounds__(kTileThreads) tile_pass_kernel(TileKArgs args)
         if (active) {
 #pragma unroll
           for (int j = 0; j < RN; ++j) {
-            const uint32_t p = swz<T>(lj[j]);
+            const uint32_t p = TPOS(j);
             s_psi[p] = a[j];
             if (NS == 2) s_lam[p] = b[j];
           }
         }
+#undef TPOS
+#undef TLOC
       }
       __syncthreads();
     }
@@ -535,7 +580,8 @@ __global__ void __launch_bounds__(kTileThreads) tile_pass_kernel(TileKArgs args)
 size_t tile_smem_bytes(qs_dtype dt, int m, int ns) {
   const size_t amp = dt == QS_C64 ? 8 : 16;
   const size_t tile = (size_t)1 << m;
-  return ns * tile * amp + tile /* cut */ + (size_t)kMaxSlotsPerPass * kTileWarps * 8 + 128 * 8;
+  return ns * tile * amp + tile /* cut */ + (size_t)kMaxSlotsPerPass * kTileWarps * 8 + 128 * 8 +
+         (size_t)kTileOpStage * sizeof(DevOp) + (size_t)kMaxPhasesPerPass * 48 * 4;
 }
 
 template <class T, int NS>

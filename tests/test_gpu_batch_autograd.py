@@ -146,3 +146,30 @@ def test_adam_training_reaches_the_paper_cut(Q):
             opt.step()
         best = max(best, (len(edges) - mod().item()) / 2)
     assert abs(best - g["cut"]) < 1e-5
+
+
+def test_batch_graph_replay_matches_direct_launches(Q):
+    """Batches with instances beyond shared memory replay a captured CUDA graph;
+    with launch tracing on they launch directly.  Both give the same bits."""
+    import torch
+    inst = I.batched_vqe(40, seed=9, n_range=(10, 16), depth_range=(1, 3))
+    b = Q.Batch(inst, Q.C64)
+    params = torch.tensor(np.concatenate([it.params for it in inst]), dtype=torch.float64, device="cuda")
+    e1 = torch.empty(len(inst), dtype=torch.float64, device="cuda")
+    g1 = torch.empty_like(params)
+    b.expectation_with_grad_device(params, e1, g1)  # graph (captured on first use)
+    b.expectation_with_grad_device(params, e1, g1)  # graph replay
+    Q.trace_enable(True)
+    e2 = torch.empty_like(e1)
+    g2 = torch.empty_like(g1)
+    b.expectation_with_grad_device(params, e2, g2)  # direct launches
+    Q.trace_enable(False)
+    Q.trace_read()
+    torch.cuda.synchronize()
+    assert torch.equal(e1, e2) and torch.equal(g1, g2)
+    k = int(np.argmax([it.circuit.n_qubits for it in inst]))
+    E, G = O.adjoint_gradient(inst[k].circuit, inst[k].ham, inst[k].params, O.zero_state(inst[k].circuit.n_qubits))
+    po = b.param_offsets
+    sc = max(1.0, float(np.abs(inst[k].ham.coef).sum()))
+    assert abs(e1[k].item() - E) <= 5e-5 * sc
+    assert np.max(np.abs(g1[po[k]:po[k + 1]].cpu().numpy() - G)) <= 5e-5 * sc

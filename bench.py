@@ -647,9 +647,80 @@ def dense_cpu_baseline(k, U, targets, n, n_small=20):
             "sample": f"{reps} applications at {n_small} qubits (complex128 numpy), scaled by 2^({n_small}-{n})"}
 
 
+def run_hea_workload(args):
+    """12-qubit HEA, 4 layers (RY, RZ per qubit, open CNOT ladder), 96 parameters
+    U[-pi, pi] seed 1, H = sum Z_i Z_{i+1} + 0.5 sum X_i, complex128 from |0>:
+    energy + 96 gradients per evaluation.  Single: one parameter vector through
+    the fused tile engine; many: 1024 parameter vectors (seeds 1..1024) in one
+    batched launch (each instance's psi and lam in one CTA's shared memory)."""
+    import numpy as np
+    import torch
+    from paper_2406_17248_gb300 import build, inputs as I
+    build.build()
+    from paper_2406_17248_gb300 import qsim as Q
+    n, layers = 12, 4
+    circ = I.hea_circuit(n, layers)
+    ham = I.chain_zz_x(n, 0.5)
+    params = I.uniform_params(circ.n_params, 1)
+    c = Q.circuit_from(circ).finalize(Q.C128)
+    h = Q.Hamiltonian(ham)
+    psi, lam = Q.State(n, Q.C128), Q.State(n, Q.C128)
+    for _ in range(max(3, args.warmup)):
+        psi.set_basis(0)
+        Q.expectation_with_grad(psi, lam, c, h, params)
+    torch.cuda.synchronize()
+    reps = max(args.steps, 10) * 10
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        psi.set_basis(0)
+        E, G = Q.expectation_with_grad(psi, lam, c, h, params)
+    torch.cuda.synchronize()
+    single = reps / (time.perf_counter() - t0)
+    n_inst = 1024
+    inst = [I.Instance(circ, ham, I.uniform_params(circ.n_params, s)) for s in range(1, n_inst + 1)]
+    b = Q.Batch(inst, Q.C128)
+    pd = torch.tensor(np.concatenate([it.params for it in inst]), dtype=torch.float64, device="cuda")
+    ed = torch.empty(n_inst, dtype=torch.float64, device="cuda")
+    gd = torch.empty_like(pd)
+    for _ in range(max(3, args.warmup)):
+        b.expectation_with_grad_device(pd, ed, gd)
+    clocks = ClockSampler()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        b.expectation_with_grad_device(pd, ed, gd)
+    ev1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    many = n_inst / (ms / 1e3)
+    line = {"metric": "12q HEA c128 adjoint energy+grad evals/s (one vector; 1024 vectors batched)",
+            "value": many, "unit": "evals/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "12-qubit HEA, 4 layers, 96 params U[-pi,pi] (seed 1; batch seeds 1..1024), "
+                                   "H = sum ZZ + 0.5 sum X, complex128", "l2": "64 KiB states: shared-memory bound"},
+            "single_vector": {"value": single, "unit": "evals/s", "engine": "fused tile passes, one call per eval"},
+            "batched": {"value": many, "unit": "evals/s", "instances": n_inst},
+            "energy_single": E, "gpu_launches": args.steps, "clocks": ck}
+    if not args.no_cpu_baseline:
+        from oracle import qsim_oracle as O
+        E0, G0 = O.adjoint_gradient(circ, ham, params, O.zero_state(n))
+        line["error_vs_oracle"] = {"energy": abs(E - E0), "grad_max": float(np.max(np.abs(G - G0)))}
+        t0 = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t0 < 10.0:
+            O.adjoint_gradient(circ, ham, params, O.zero_state(n))
+            k += 1
+        line["cpu_baseline"] = {"value": k / (time.perf_counter() - t0), "unit": "evals/s", "cores": 1,
+                                "kind": "oracle", "sample": f"{k} oracle adjoint evaluations of the same instance"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="qaoa30", choices=["qaoa30", "batch", "random28", "gnn", "dense28"])
+    ap.add_argument("--workload", default="qaoa30", choices=["qaoa30", "batch", "random28", "gnn", "dense28", "hea12"])
     ap.add_argument("--instances", type=int, default=2048)
     ap.add_argument("--plain-instances", type=int, default=2048)
     ap.add_argument("--gpus", type=int, default=1)
@@ -667,6 +738,8 @@ def main():
     args = ap.parse_args()
     if args.workload == "batch":
         return run_batch_workload(args)
+    if args.workload == "hea12":
+        return run_hea_workload(args)
     if args.workload == "dense28":
         return run_dense_workload(args)
     if args.workload == "gnn":

@@ -218,11 +218,13 @@ QS_API qs_status qs_qaoa_expectation_with_grad(qs_qaoa* q, qs_state* psi, qs_sta
 /* Many independent instances (circuit, Hamiltonian, parameters) evaluated
  * together: the batch dimension of get_expectation_with_grad (§4.1, output
  * shapes [n_batch, ...]), here with one circuit and Hamiltonian per instance.
- * All instances run in ONE persistent launch: each CTA takes instances from a
- * work queue (largest first) and runs the full adjoint evaluation of one
- * instance at a time, with psi and lam in shared memory when they fit
- * (complex64 n <= 13, complex128 n <= 12) and in a per-CTA global slot
- * otherwise. */
+ * Instances whose psi and lam fit in shared memory (complex64 n <= 13,
+ * complex128 n <= 12) run in ONE persistent launch: each CTA takes instances
+ * from a work queue (largest first) and runs the full adjoint evaluation of one
+ * instance at a time.  Larger instances get their own fused tile-pass plan at
+ * creation and run concurrently on the batch's streams, their gate matrices
+ * formed on the device from the device parameters.  A call is captured once as
+ * a CUDA graph and replayed (launches are direct while qs_trace is enabled). */
 typedef struct qs_batch qs_batch;
 
 /* One gate of a batched circuit: kind (any qs_gate_kind but QS_GATE_MATRIX),

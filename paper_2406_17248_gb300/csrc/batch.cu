@@ -158,8 +158,6 @@ static qs_status issue_all(qs_batch* b, cudaStream_t st, const double* dev_param
     a.energy = dev_energies;
     a.grad = dev_grads;
     a.queue = b->d_queue;
-    a.slots = nullptr;
-    a.slot_amps = 0;
     a.smem_amps = b->smem_amps;
     TraceRec* rec = trace_begin(st);
     QS_TRY(launch_batch(b->dt, a, b->grid, st));

@@ -21,7 +21,7 @@ struct BInst {
   int gate_begin, gate_end;
   int group_begin, group_end;  // Hamiltonian groups (terms sharing an X mask)
   int param_off, n_params;     // slice of the concatenated parameter / gradient arrays
-  int in_smem;                 // psi and lam fit in the CTA's shared memory
+  int in_smem;                 // psi and lam fit in shared memory (else: fused tile passes)
   int pad;
   double cost;                 // work estimate used to order the queue
 };
@@ -37,8 +37,6 @@ struct BatchArgs {
   double* energy;          // [n_inst]
   double* grad;            // concatenated, like params
   int* queue;              // work counter (zeroed before the launch)
-  void* slots;             // per-CTA global scratch for states too large for shared memory
-  size_t slot_amps;        // amplitudes per state in a slot
   int smem_amps;           // amplitudes per state in shared memory
 };
 

@@ -3,10 +3,11 @@
 // Hamiltonian and parameters) evaluated in ONE launch.  CTAs pull instances
 // from an atomic work queue ordered by decreasing cost; an instance is owned by
 // one CTA from start to finish: psi = U|0>, E = <psi|H|psi>, lam = H psi, then
-// the adjoint sweep (the gradient rule of §4.1 / §7.2) gate by gate.  psi and
-// lam live in the CTA's shared memory when both fit, otherwise in a per-CTA
-// global slot.  Gate matrices are formed on the device from the angle (the
-// definitions of §2.3.2 / §2.3.3); every reduction has a fixed order.
+// the adjoint sweep (the gradient rule of §4.1 / §7.2) gate by gate, with psi
+// and lam in the CTA's shared memory.  (Instances too large for shared memory
+// run on fused tile passes, see batch.cu.)  Gate matrices are formed on the
+// device from the angle (the definitions of §2.3.2 / §2.3.3); every reduction
+// has a fixed order.
 #include <cmath>
 
 #include "batch.h"
@@ -305,19 +306,13 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a) {
   __shared__ int s_next;
   V* s_psi = reinterpret_cast<V*>(smem);
   V* s_lam = s_psi + a.smem_amps;
-  V* g_psi = reinterpret_cast<V*>(a.slots) + (size_t)blockIdx.x * 2 * a.slot_amps;
-  V* g_lam = g_psi + a.slot_amps;
   while (true) {
     if (threadIdx.x == 0) s_next = atomicAdd(a.queue, 1);
     __syncthreads();
     const int i = s_next;
     __syncthreads();
     if (i >= a.n_inst) break;
-    const BInst& I = a.inst[a.order[i]];
-    if (I.in_smem)
-      run_instance<T>(a, I, s_psi, s_lam, sh);
-    else
-      run_instance<T>(a, I, g_psi, g_lam, sh);
+    run_instance<T>(a, a.inst[a.order[i]], s_psi, s_lam, sh);
     __syncthreads();
   }
 }

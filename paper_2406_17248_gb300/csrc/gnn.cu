@@ -7,7 +7,8 @@
 // and motivates slowly varying schedules by adiabatic evolution (§5.4); the
 // network itself is this library's definition (include/qsim.h states it).
 //
-// One CTA runs one graph at a time (graphs g = blockIdx.x, + gridDim.x, ...):
+// One CTA runs one graph at a time (graphs g = blockIdx.x, + gridDim.x, ...;
+// two CTAs per SM when every graph of the batch has at most 32 nodes):
 // the weights (bf16, rows padded by two elements so that both row and column
 // walks are free of bank conflicts), the per-layer node embeddings and the
 // adjacency live in shared memory.  The backward kernel recomputes the forward
@@ -82,22 +83,23 @@ GnnDims make_dims(int H, int L, int O) {
   return d;
 }
 
-// Shared-memory carve-up of one CTA (floats after the bf16 weights).
+// Shared-memory carve-up of one CTA for graphs of at most mn nodes (floats
+// after the bf16 weights).  Batches of graphs with at most 32 nodes use mn = 32:
+// half the activation storage, two CTAs per SM.
 struct GnnSmem {
-  size_t w_bytes, h_off, a_off, t0_off, t1_off, t2_off, vec_off, adj_off, total;
+  size_t w_bytes, h_off, a_off, t0_off, t1_off, vec_off, adj_off, total;
 };
 
-GnnSmem smem_layout(const GnnDims& d) {
+GnnSmem smem_layout(const GnnDims& d, int mn) {
   GnnSmem s{};
   s.w_bytes = ((size_t)d.s_w * 2 + 15) & ~(size_t)15;
-  const size_t nodeH = (size_t)kGnnMaxNodes * d.H * 4;
-  s.h_off = s.w_bytes;                        // h_0 .. h_L, each [64][H] (h_0 uses 2 columns)
-  s.a_off = s.h_off + (d.L + 1) * nodeH;      // a: mean over neighbours
+  const size_t nodeH = (size_t)mn * d.H * 4;
+  s.h_off = s.w_bytes;                        // h_0 .. h_L, each [mn][H] (h_0 uses 2 columns)
+  s.a_off = s.h_off + (d.L + 1) * nodeH;      // a: mean over neighbours (backward: also q)
   s.t0_off = s.a_off + nodeH;                 // backward: dh
   s.t1_off = s.t0_off + nodeH;                // backward: dpre
-  s.t2_off = s.t1_off + nodeH;                // backward: q
-  s.vec_off = s.t2_off + nodeH;               // r, zpre, y / dy, dz, dr: 8 x 64 floats
-  s.adj_off = s.vec_off + 8 * 64 * 4;         // local CSR: off[65] int + adj bytes
+  s.vec_off = s.t1_off + nodeH;               // r, zpre, y / dy, dz, dr: 8 x 64 floats
+  s.adj_off = s.vec_off + 8 * 64 * 4;         // local CSR: off[mn + 1] int + adj bytes
   s.total = s.adj_off + (kGnnMaxNodes + 1) * 4 + kGnnMaxAdj;
   return s;
 }
@@ -176,10 +178,10 @@ __device__ void transform(int nv, int d, int H, const __nv_bfloat16* sw, const G
 }
 
 // Forward pass of one graph, leaving h_0..h_L, r, zpre and y in shared memory.
-__device__ void forward_graph(const GnnDims& D, int nv, const __nv_bfloat16* sw, float* sh, float* sa, float* r,
-                              float* zpre, float* y, const int* s_off, const uint8_t* s_adj) {
+__device__ void forward_graph(const GnnDims& D, int nv, int mn, const __nv_bfloat16* sw, float* sh, float* sa,
+                              float* r, float* zpre, float* y, const int* s_off, const uint8_t* s_adj) {
   const int H = D.H;
-  const size_t nodeH = (size_t)kGnnMaxNodes * H;
+  const size_t nodeH = (size_t)mn * H;
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
     sh[v * H + 0] = 1.f;
     sh[v * H + 1] = (float)(s_off[v + 1] - s_off[v]) / 3.f;
@@ -232,40 +234,39 @@ struct GnnPtrs {
   float* sa;
   float* t0;
   float* t1;
-  float* t2;
   float* vec;
   int* s_off;
   uint8_t* s_adj;
 };
 
-__device__ GnnPtrs carve(const GnnDims& D, unsigned char* smem) {
+__device__ GnnPtrs carve(const GnnDims& D, unsigned char* smem, int mn) {
   // same arithmetic as smem_layout(), on the device
   const size_t w_bytes = ((size_t)D.s_w * 2 + 15) & ~(size_t)15;
-  const size_t nodeH = (size_t)kGnnMaxNodes * D.H;
+  const size_t nodeH = (size_t)mn * D.H;
   GnnPtrs p;
   p.sh = reinterpret_cast<float*>(smem + w_bytes);
   p.sa = p.sh + (D.L + 1) * nodeH;
   p.t0 = p.sa + nodeH;
   p.t1 = p.t0 + nodeH;
-  p.t2 = p.t1 + nodeH;
-  p.vec = p.t2 + nodeH;
+  p.vec = p.t1 + nodeH;
   p.s_off = reinterpret_cast<int*>(p.vec + 8 * 64);
   p.s_adj = reinterpret_cast<uint8_t*>(p.s_off + kGnnMaxNodes + 1);
   return p;
 }
 
 __global__ void __launch_bounds__(kGnnThreads) gnn_forward_kernel(GnnDims D, const __nv_bfloat16* __restrict__ wb,
-                                                                  GraphView G, int n_graphs, float* __restrict__ out) {
+                                                                  GraphView G, int n_graphs, int mn,
+                                                                  float* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem[];
   __nv_bfloat16* sw = reinterpret_cast<__nv_bfloat16*>(smem);
-  const GnnPtrs p = carve(D, smem);
+  const GnnPtrs p = carve(D, smem, mn);
   load_weights(D, wb, sw);
   for (int g = blockIdx.x; g < n_graphs; g += gridDim.x) {
     __syncthreads();
     const int nv = load_graph(G, g, p.s_off, p.s_adj);
     __syncthreads();
     float* y = p.vec + 2 * 64;
-    forward_graph(D, nv, sw, p.sh, p.sa, p.vec, p.vec + 64, y, p.s_off, p.s_adj);
+    forward_graph(D, nv, mn, sw, p.sh, p.sa, p.vec, p.vec + 64, y, p.s_off, p.s_adj);
     for (int o = threadIdx.x; o < D.O; o += blockDim.x) out[(size_t)g * D.O + o] = y[o];
   }
 }
@@ -273,14 +274,14 @@ __global__ void __launch_bounds__(kGnnThreads) gnn_forward_kernel(GnnDims D, con
 // Backward of one graph per iteration; weight gradients added to this CTA's
 // slice part[blockIdx.x * P ...] (one owning thread per entry).
 __global__ void __launch_bounds__(kGnnThreads) gnn_backward_kernel(GnnDims D, const __nv_bfloat16* __restrict__ wb,
-                                                                   GraphView G, int n_graphs,
+                                                                   GraphView G, int n_graphs, int mn,
                                                                    const float* __restrict__ dy_all,
                                                                    float* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem[];
   __nv_bfloat16* sw = reinterpret_cast<__nv_bfloat16*>(smem);
-  const GnnPtrs p = carve(D, smem);
+  const GnnPtrs p = carve(D, smem, mn);
   const int H = D.H, O = D.O;
-  const size_t nodeH = (size_t)kGnnMaxNodes * H;
+  const size_t nodeH = (size_t)mn * H;
   float* gp = part + (size_t)blockIdx.x * D.P;
   float* r = p.vec;
   float* zpre = p.vec + 64;
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(kGnnThreads) gnn_backward_kernel(GnnDims D, co
     __syncthreads();
     const int nv = load_graph(G, g, p.s_off, p.s_adj);
     __syncthreads();
-    forward_graph(D, nv, sw, p.sh, p.sa, r, zpre, y, p.s_off, p.s_adj);
+    forward_graph(D, nv, mn, sw, p.sh, p.sa, r, zpre, y, p.s_off, p.s_adj);
     for (int o = threadIdx.x; o < O; o += blockDim.x) dy[o] = dy_all[(size_t)g * O + o];
     __syncthreads();
     // readout MLP
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(kGnnThreads) gnn_backward_kernel(GnnDims D, co
     __syncthreads();
     float* dh = p.t0;
     float* dpre = p.t1;
-    float* q = p.t2;
+    float* q = p.sa;  // the neighbour means of this layer are dead once its gradients are added
     const float inv_nv = nv ? 1.f / (float)nv : 0.f;
     for (int w = threadIdx.x; w < nv * H; w += blockDim.x) dh[w] = dr[w % H] * inv_nv;
     __syncthreads();
@@ -356,6 +357,7 @@ __global__ void __launch_bounds__(kGnnThreads) gnn_backward_kernel(GnnDims D, co
         gp[Bb.off + o] += s;
       }
       if (l == 0) break;
+      __syncthreads();  // p.sa (a_l) is read above and becomes q below
       // q[v][i] = sum_o Wn[o][i] dpre[v][o] / deg(v)
       for (int w = threadIdx.x; w < nv * H; w += blockDim.x) {
         const int v = w / H, i = w % H;
@@ -455,7 +457,8 @@ struct qs_graphs {
 
 struct qs_gnn {
   GnnDims D{};
-  GnnSmem S{};
+  GnnSmem S[2]{};        // layouts for graphs of <= 32 and <= 64 nodes
+  int grid_max[2] = {1, 1};
   cudaStream_t st = nullptr;
   float* d_w = nullptr;  // float32 master weights
   float* d_m = nullptr;
@@ -464,7 +467,6 @@ struct qs_gnn {
   float* d_part = nullptr;
   size_t part_slices = 0;
   int step = 0;
-  int grid_max = 1;
 };
 
 namespace {
@@ -511,7 +513,10 @@ qs_status check_graphs(int n_graphs, const int* node_off, const int* adj_off, co
 
 GraphView view(const qs_graphs* G) { return GraphView{G->d_node_off, G->d_adj_off, G->d_adj}; }
 
-int gnn_grid(const qs_gnn* g, int n_graphs) { return std::max(1, std::min(n_graphs, g->grid_max)); }
+// Layout index (0: graphs of <= 32 nodes, 1: <= 64), node capacity and grid of a batch.
+int gnn_layout(const qs_graphs* G) { return G->max_nodes <= 32 ? 0 : 1; }
+int gnn_mn(int li) { return li == 0 ? 32 : kGnnMaxNodes; }
+int gnn_grid(const qs_gnn* g, int li, int n_graphs) { return std::max(1, std::min(n_graphs, g->grid_max[li])); }
 
 }  // namespace
 
@@ -563,20 +568,27 @@ qs_status qs_gnn_create(int hidden, int layers, int out_dim, void* cuda_stream, 
   QS_TRY(qs_gnn_n_weights(hidden, layers, out_dim, &P));
   qs_gnn* g = new qs_gnn();
   g->D = make_dims(hidden, layers, out_dim);
-  g->S = smem_layout(g->D);
+  g->S[0] = smem_layout(g->D, 32);
+  g->S[1] = smem_layout(g->D, kGnnMaxNodes);
   g->st = static_cast<cudaStream_t>(cuda_stream);
   int dev = 0, sms = 1, smem_optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e == cudaSuccess && (size_t)smem_optin < g->S.total) {
+  if (e == cudaSuccess && (size_t)smem_optin < g->S[1].total) {
     free_gnn(g);
     set_error("GNN shared-memory layout exceeds the device limit");
     return QS_ERR_UNSUPPORTED;
   }
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(gnn_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->S.total);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(gnn_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->S.total);
-  g->grid_max = sms;
+  const int smax = (int)g->S[1].total;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(gnn_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(gnn_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  for (int li = 0; li < 2 && e == cudaSuccess; ++li) {
+    // resident CTAs per SM of the heavier (backward) kernel with this layout
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gnn_backward_kernel, kGnnThreads, g->S[li].total);
+    g->grid_max[li] = sms * std::max(occ, 1);
+  }
   const size_t P4 = (size_t)P * 4;
   if (e == cudaSuccess) e = cudaMalloc(&g->d_w, P4);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_m, P4);
@@ -627,9 +639,10 @@ qs_status qs_gnn_forward(qs_gnn* g, const qs_graphs* graphs, float* dev_out) {
   QS_CHECK(g != nullptr && graphs != nullptr, "null argument");
   QS_CHECK(graphs->n_graphs == 0 || dev_out != nullptr, "null output");
   if (graphs->n_graphs == 0) return QS_OK;
-  const int grid = gnn_grid(g, graphs->n_graphs);
-  gnn_forward_kernel<<<grid, kGnnThreads, g->S.total, g->st>>>(g->D, g->d_wb, view(graphs), graphs->n_graphs,
-                                                                dev_out);
+  const int li = gnn_layout(graphs);
+  const int grid = gnn_grid(g, li, graphs->n_graphs);
+  gnn_forward_kernel<<<grid, kGnnThreads, g->S[li].total, g->st>>>(g->D, g->d_wb, view(graphs), graphs->n_graphs,
+                                                                    gnn_mn(li), dev_out);
   QS_CUDA(cudaGetLastError());
   return QS_OK;
 }
@@ -638,7 +651,8 @@ qs_status qs_gnn_backward(qs_gnn* g, const qs_graphs* graphs, const float* dev_d
   QS_CHECK(g != nullptr && graphs != nullptr && dev_grad != nullptr, "null argument");
   QS_CHECK(graphs->n_graphs == 0 || dev_dout != nullptr, "null dout");
   const int P = g->D.P;
-  const int grid = gnn_grid(g, graphs->n_graphs);
+  const int li = gnn_layout(graphs);
+  const int grid = gnn_grid(g, li, graphs->n_graphs);
   if ((size_t)grid > g->part_slices) {
     if (g->d_part) QS_CUDA(cudaFree(g->d_part));
     g->d_part = nullptr;
@@ -648,8 +662,9 @@ qs_status qs_gnn_backward(qs_gnn* g, const qs_graphs* graphs, const float* dev_d
   }
   QS_CUDA(cudaMemsetAsync(g->d_part, 0, (size_t)grid * P * 4, g->st));
   if (graphs->n_graphs > 0) {
-    gnn_backward_kernel<<<grid, kGnnThreads, g->S.total, g->st>>>(g->D, g->d_wb, view(graphs), graphs->n_graphs,
-                                                                   dev_dout, g->d_part);
+    gnn_backward_kernel<<<grid, kGnnThreads, g->S[li].total, g->st>>>(g->D, g->d_wb, view(graphs),
+                                                                       graphs->n_graphs, gnn_mn(li), dev_dout,
+                                                                       g->d_part);
     QS_CUDA(cudaGetLastError());
   }
   gnn_reduce_kernel<<<blocks_for(P, 256), 256, 0, g->st>>>(g->d_part, grid, P, dev_grad);

@@ -184,6 +184,26 @@ QS_API qs_status qs_expectation_with_grad(qs_state* psi, qs_state* lam, qs_circu
  * out_bits: host uint64[shots], little-endian bitstrings. */
 QS_API qs_status qs_sample(const qs_state* s, uint64_t shots, uint64_t seed, uint64_t* out_bits);
 
+/* The same for a list of Hamiltonians, evaluated together (§4.1: the gradient
+ * operator takes a list of observables; outputs [n_ham] energies and
+ * [n_ham, n_params] gradients, here for one encoder input).  One forward sweep;
+ * each Hamiltonian then forms lam = H_h psi_N and runs its own reverse sweep
+ * from a copy of psi_N kept in a buffer the call allocates on psi (2^n
+ * amplitudes, kept until psi is destroyed).  hams: host array of n_ham handles.
+ * energies: host double[n_ham]; grads: host double[n_ham * n_params],
+ * row-major.  Synchronises psi's stream. */
+QS_API qs_status qs_expectation_with_grad_multi(qs_state* psi, qs_state* lam, qs_circuit* c, int n_ham,
+                                                const qs_ham* const* hams, const double* params, int n_params,
+                                                double* energies, double* grads);
+
+/* Projective measurement of one qubit in the computational basis, mid-circuit
+ * (the measurement gate, §2.3; outcomes as in sampling, §2.6.3): with
+ * P(1) = sum of |psi_x|^2 over x with bit `qubit` set and P(0) = total - P(1),
+ * u = top 53 bits of splitmix64(seed) / 2^53, the outcome is 0 iff P(0) > u *
+ * total; the state is projected onto the outcome and renormalised in place.
+ * Sums are FP64 in a fixed order.  *outcome: host int.  Synchronises. */
+QS_API qs_status qs_measure(qs_state* s, int qubit, uint64_t seed, int* outcome);
+
 /* -------------------------------------------------------------------- QAOA */
 
 /* MaxCut QAOA engine (§5.2 ansatz; QuPack QAOA simulator interface §6.2):

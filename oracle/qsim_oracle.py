@@ -480,3 +480,22 @@ def qaoa_p1_energy_closed_form(n: int, edges, gamma: float, beta: float, gamma_s
                - 0.25 * math.sin(2 * b) ** 2 * math.cos(g) ** (du + dv - 2 * f) * (1 - math.cos(2 * g) ** f))
         total += 1.0 - 2.0 * cuv
     return total
+
+
+def measure(psi: np.ndarray, n: int, qubit: int, seed: int):
+    """Projective measurement of one qubit (the measurement gate of §2.3, with the
+    outcome drawn as in sampling, §2.6.3): P1 = sum of |psi_x|^2 over x with the
+    bit set, u = shot_uniform(seed, 0); outcome 0 iff P0 > u * total; the state is
+    projected onto the outcome and renormalised.  Returns (outcome, new state, P1 / total)."""
+    x = np.arange(psi.size, dtype=np.int64)
+    prob = np.abs(psi) ** 2
+    on = ((x >> qubit) & 1) == 1
+    tot = float(prob.sum())
+    p1 = float(prob[on].sum())
+    p0 = tot - p1
+    u = shot_uniform(seed, 0)
+    outcome = 0 if p0 > u * tot else 1
+    keep = on if outcome == 1 else ~on
+    out = np.where(keep, psi, 0.0).astype(psi.dtype)
+    pk = p1 if outcome == 1 else p0
+    return outcome, out / math.sqrt(pk), p1 / tot

@@ -531,6 +531,7 @@ qs_status qs_state_destroy(qs_state* s) {
   if (s->st) cudaStreamSynchronize(s->st);
   if (s->owned && s->ptr) cudaFree(s->ptr);
   if (s->scratch) cudaFree(s->scratch);
+  if (s->save) cudaFree(s->save);
   delete s;
   return QS_OK;
 }
@@ -871,6 +872,85 @@ qs_status qs_expectation_with_grad(qs_state* psi, qs_state* lam, qs_circuit* c, 
     QS_CUDA(cudaMemcpyAsync(grad, d_grad, c->n_params * sizeof(double), cudaMemcpyDeviceToHost, st));
   QS_CUDA(cudaStreamSynchronize(st));
   for (int p = c->n_params; p < n_params; ++p) grad[p] = 0.0;
+  return QS_OK;
+}
+
+qs_status qs_expectation_with_grad_multi(qs_state* psi, qs_state* lam, qs_circuit* c, int n_ham,
+                                         const qs_ham* const* hams, const double* params, int n_params,
+                                         double* energies, double* grads) {
+  QS_CHECK(n_ham >= 1 && hams != nullptr && energies != nullptr, "need n_ham >= 1 Hamiltonians and outputs");
+  for (int h = 0; h < n_ham; ++h) QS_CHECK(hams[h] != nullptr, "null Hamiltonian");
+  if (n_ham == 1) return qs_expectation_with_grad(psi, lam, c, hams[0], params, n_params, energies, grads);
+  QS_TRY(check_state(psi));
+  QS_TRY(check_state(lam));
+  QS_CHECK(c != nullptr, "null circuit");
+  QS_CHECK(psi != lam && psi->ptr != lam->ptr, "psi and lam must be different states");
+  QS_CHECK(psi->n == lam->n && psi->dt == lam->dt, "psi/lam n or dtype mismatch");
+  QS_CHECK(c->n == psi->n, "circuit/state qubit counts differ");
+  for (int h = 0; h < n_ham; ++h) QS_CHECK(hams[h]->n == psi->n, "hamiltonian/state qubit counts differ");
+  QS_CHECK(n_params >= c->n_params, "too few parameters");
+  QS_CHECK(c->n_params == 0 || (params != nullptr && grads != nullptr), "params/grads is null");
+  if (lam->st != psi->st) QS_CUDA(cudaStreamSynchronize(lam->st));
+  QS_TRY(ensure_plan(c, psi->dt, psi->st));
+  if (c->plan.fuse < 0) {
+    set_error("the adjoint gradient runs on fused tile passes (fuse = -1 is forward only)");
+    return QS_ERR_UNSUPPORTED;
+  }
+  CircuitPlan& P = c->plan;
+  cudaStream_t st = psi->st;
+  QS_TRY(fill_circuit_coef(c, params));
+  QS_TRY(upload_table(c->host_coef, psi->dt, P.d_coef, st, psi->host_out));
+  const int n_slots = (int)P.rev_slots.out.size();
+  const int hgrid = ham_grid_size(psi->ne);
+  const int np = std::max(c->n_params, 1);
+  const size_t part = (size_t)std::max(n_slots, 1) * P.grid2;
+  const size_t need = part + n_slots + n_ham + (size_t)n_ham * np + hgrid + 16;
+  QS_TRY(ensure_scratch(psi, need));
+  double* d_part = psi->scratch;
+  double* d_slot = d_part + part;
+  double* d_E = d_slot + n_slots;
+  double* d_grad = d_E + n_ham;
+  double* d_hpart = d_grad + (size_t)n_ham * np;
+  const size_t bytes = amp_bytes(psi->dt) << psi->ne;
+  if (!psi->save) QS_CUDA(cudaMalloc(&psi->save, bytes));
+  // one forward sweep; each Hamiltonian restarts the reverse sweep from its copy
+  QS_TRY(run_passes(P.fwd, 0, (int)P.fwd.passes.size(), psi->dt, psi->ptr, nullptr, P.d_coef, nullptr, d_part,
+                    psi->ne, 0, P.grid1, P.grid2, st));
+  QS_CUDA(cudaMemcpyAsync(psi->save, psi->ptr, bytes, cudaMemcpyDeviceToDevice, st));
+  for (int h = 0; h < n_ham; ++h) {
+    if (h > 0) QS_CUDA(cudaMemcpyAsync(psi->ptr, psi->save, bytes, cudaMemcpyDeviceToDevice, st));
+    QS_TRY(launch_ham_apply(psi->dt, psi->ptr, lam->ptr, psi->ne, hams[h]->d_groups, hams[h]->n_groups,
+                            hams[h]->d_terms, d_hpart, hgrid, st));
+    QS_TRY(launch_reduce_slots(d_hpart, 1, hgrid, nullptr, d_E + h, st));
+    QS_TRY(run_passes(P.rev, 0, (int)P.rev.passes.size(), psi->dt, psi->ptr, lam->ptr, P.d_coef, nullptr, d_part,
+                      psi->ne, 0, P.grid1, P.grid2, st));
+    if (c->n_params > 0) {
+      QS_TRY(launch_reduce_slots(d_part, n_slots, P.grid2, nullptr, d_slot, st));
+      QS_TRY(launch_param_gather(d_slot, P.d_row, P.d_sidx, P.d_w, c->n_params, d_grad + (size_t)h * np, st));
+    }
+  }
+  QS_CUDA(cudaMemcpyAsync(energies, d_E, n_ham * sizeof(double), cudaMemcpyDeviceToHost, st));
+  std::vector<double> g((size_t)n_ham * np);
+  if (c->n_params > 0) QS_CUDA(cudaMemcpyAsync(g.data(), d_grad, g.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  QS_CUDA(cudaStreamSynchronize(st));
+  if (grads)
+    for (int h = 0; h < n_ham; ++h)
+      for (int p = 0; p < n_params; ++p) grads[(size_t)h * n_params + p] = p < c->n_params ? g[(size_t)h * np + p] : 0.0;
+  return QS_OK;
+}
+
+qs_status qs_measure(qs_state* s, int qubit, uint64_t seed, int* outcome) {
+  QS_TRY(check_state(s));
+  QS_CHECK(qubit >= 0 && qubit < s->n, "qubit out of range");
+  QS_CHECK(outcome != nullptr, "outcome is null");
+  const uint64_t N = 1ull << s->ne;
+  const int nb = (int)std::min<uint64_t>(std::max<uint64_t>((N + 255) / 256, 1), 1024);
+  QS_TRY(ensure_scratch(s, 2 * (size_t)nb + 2));
+  QS_TRY(launch_measure(s->dt, s->ptr, s->ne, qubit, seed, s->scratch, nb, s->st));
+  double o = 0.0;
+  QS_CUDA(cudaMemcpyAsync(&o, s->scratch + 2 * nb, sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  QS_CUDA(cudaStreamSynchronize(s->st));
+  *outcome = (int)o;
   return QS_OK;
 }
 

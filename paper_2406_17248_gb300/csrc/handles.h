@@ -20,6 +20,7 @@ struct qs_state {
   cudaStream_t st = nullptr;
   double* scratch = nullptr;
   size_t scratch_n = 0;
+  void* save = nullptr;  // copy of the evolved state (several Hamiltonians in one gradient call)
   std::vector<double> host_out;
 };
 

@@ -353,6 +353,72 @@ __device__ __forceinline__ uint64_t splitmix64_out(uint64_t state) {
   return z ^ (z >> 31);
 }
 
+// ------------------------------------------------------- projective measurement
+// One qubit measured in the computational basis (the measurement gate of
+// §2.3 / §2.6.3): P(1) = sum |psi_x|^2 over x with bit q set, the outcome drawn
+// with the sampling rule (u_0 from splitmix64 of the seed; outcome 0 iff
+// P(0) > u_0 * total), then the state projected and renormalised.
+template <class T>
+__global__ void measure_mass_kernel(const typename V2<T>::V* __restrict__ psi, int n, int q, double* partials) {
+  __shared__ double s1[kThreads / 32], st[kThreads / 32];
+  double a1 = 0.0, at = 0.0;
+  const uint64_t N = 1ull << n;
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
+    const double p = (double)psi[x].x * (double)psi[x].x + (double)psi[x].y * (double)psi[x].y;
+    at += p;
+    if ((x >> q) & 1ull) a1 += p;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    at += __shfl_xor_sync(0xffffffffu, at, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s1[threadIdx.x >> 5] = a1;
+    st[threadIdx.x >> 5] = at;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b1 = 0.0, bt = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      b1 += s1[w];
+      bt += st[w];
+    }
+    partials[2 * blockIdx.x] = b1;
+    partials[2 * blockIdx.x + 1] = bt;
+  }
+}
+
+// out[0] = outcome, out[1] = 1 / sqrt(P(outcome)) (doubles), fixed summation order.
+__global__ void measure_decide_kernel(const double* partials, int nb, uint64_t seed, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double p1 = 0.0, tot = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    p1 += partials[2 * b];
+    tot += partials[2 * b + 1];
+  }
+  const double p0 = tot - p1;
+  const uint64_t z = splitmix64_out(seed);
+  const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  const int outcome = p0 > u * tot ? 0 : 1;
+  const double pk = outcome ? p1 : p0;
+  out[0] = (double)outcome;
+  out[1] = pk > 0.0 ? 1.0 / sqrt(pk) : 0.0;
+}
+
+template <class T>
+__global__ void measure_collapse_kernel(typename V2<T>::V* __restrict__ psi, int n, int q, const double* out) {
+  const uint64_t keep = (uint64_t)out[0];
+  const T sc = (T)out[1];
+  const uint64_t N = 1ull << n;
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
+    typename V2<T>::V v = psi[x];
+    const bool on = ((x >> q) & 1ull) == keep;
+    v.x = on ? v.x * sc : (T)0;
+    v.y = on ? v.y * sc : (T)0;
+    psi[x] = v;
+  }
+}
+
 // one warp per shot
 template <class T>
 __global__ void sample_kernel(const typename V2<T>::V* __restrict__ psi, int n, const double* __restrict__ chunk,
@@ -563,6 +629,22 @@ qs_status launch_max_u8(const uint8_t* v, uint64_t n, int* d_out, cudaStream_t s
   const uint64_t want = (n / 16 + kThreads - 1) / kThreads;
   const int g = (int)(want < 1 ? 1 : (want > 4096 ? 4096 : want));
   max_u8_kernel<<<g, kThreads, 0, st>>>(v, n, d_out);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_measure(qs_dtype dt, void* psi, int n, int q, uint64_t seed, double* scratch, int nb,
+                         cudaStream_t st) {
+  double* out = scratch + 2 * nb;
+  if (dt == QS_C64) {
+    measure_mass_kernel<float><<<nb, kThreads, 0, st>>>((const float2*)psi, n, q, scratch);
+    measure_decide_kernel<<<1, 32, 0, st>>>(scratch, nb, seed, out);
+    measure_collapse_kernel<float><<<nb, kThreads, 0, st>>>((float2*)psi, n, q, out);
+  } else {
+    measure_mass_kernel<double><<<nb, kThreads, 0, st>>>((const double2*)psi, n, q, scratch);
+    measure_decide_kernel<<<1, 32, 0, st>>>(scratch, nb, seed, out);
+    measure_collapse_kernel<double><<<nb, kThreads, 0, st>>>((double2*)psi, n, q, out);
+  }
   QS_CUDA(cudaGetLastError());
   return QS_OK;
 }

@@ -185,6 +185,10 @@ qs_status launch_max_u8(const uint8_t* v, uint64_t n, int* d_out, cudaStream_t s
 qs_status launch_sample(qs_dtype dt, const void* psi, int n, uint64_t shots, uint64_t seed,
                         double* scratch /* cdf of block sums */, uint64_t* d_out, cudaStream_t st);
 size_t sample_scratch_doubles(int n);
+// Projective measurement of qubit q: scratch holds 2 nb + 2 doubles; afterwards
+// scratch[2 nb] = outcome, scratch[2 nb + 1] = 1/sqrt(P(outcome)).
+qs_status launch_measure(qs_dtype dt, void* psi, int n, int q, uint64_t seed, double* scratch, int nb,
+                         cudaStream_t st);
 
 // ----------------------------------------------------------------------------- errors
 void set_error(const std::string& msg);

@@ -57,6 +57,8 @@ SIGNATURES = [
     ("qs_inner_product", [_VP, _VP, _PD]),
     ("qs_expectation_with_grad", [_VP, _VP, _VP, _VP, _PD, _I, _PD, _PD]),
     ("qs_sample", [_VP, _U64, _U64, _PU64]),
+    ("qs_expectation_with_grad_multi", [_VP, _VP, _VP, _I, _VP, _PD, _I, _PD, _PD]),
+    ("qs_measure", [_VP, _I, _U64, _PI]),
     ("qs_qaoa_create", [_I, _PI, _I, _I, _D, _I, _VP, _PVP]),
     ("qs_qaoa_destroy", [_VP]),
     ("qs_qaoa_info", [_VP, _PI, _PI, _PD]),
@@ -299,6 +301,26 @@ def expectation_with_grad(psi: State, lam: State, circ: Circuit, ham: Hamiltonia
     _check(lib().qs_expectation_with_grad(psi.h, lam.h, circ.h, ham.h, _dptr(pr) if pr.size else None,
                                           int(pr.size), C.byref(e), _dptr(grad)))
     return e.value, grad[: pr.size]
+
+
+def expectation_with_grad_multi(psi: State, lam: State, circ: Circuit, hams, params):
+    """Energies [n_ham] and gradients [n_ham, n_params] for a list of Hamiltonians
+    (one forward sweep, one reverse sweep per Hamiltonian)."""
+    pr = np.ascontiguousarray(params, dtype=np.float64)
+    n_ham = len(hams)
+    arr = (C.c_void_p * n_ham)(*[h.h for h in hams])
+    e = np.zeros(n_ham)
+    g = np.zeros(max(n_ham * pr.size, 1))
+    _check(lib().qs_expectation_with_grad_multi(psi.h, lam.h, circ.h, n_ham, C.cast(arr, C.c_void_p),
+                                                _dptr(pr) if pr.size else None, int(pr.size), _dptr(e), _dptr(g)))
+    return e, g[: n_ham * pr.size].reshape(n_ham, pr.size)
+
+
+def measure(state: State, qubit: int, seed: int) -> int:
+    """Measure one qubit (projective, in place); returns the outcome 0 or 1."""
+    o = C.c_int()
+    _check(lib().qs_measure(state.h, qubit, seed, C.byref(o)))
+    return o.value
 
 
 def sample(state: State, shots: int, seed: int) -> np.ndarray:

@@ -257,3 +257,45 @@ def test_error_paths(Q):
     q = Q.QAOA(5, [(0, 1)], 2)
     with pytest.raises(Q.QSimError, match="n/dtype"):
         q.expectation(s, [0, 0], [0, 0])
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_gradient_for_a_list_of_hamiltonians(Q, dt):
+    """§4.1: energies [n_ham] and gradients [n_ham, n_params] in one call against
+    the oracle's adjoint gradient per Hamiltonian."""
+    n = 9
+    circ = I.random_mixed_circuit(n, 40, 17, with_matrix=False)
+    params = I.uniform_params(circ.n_params, 5)
+    hams = [I.chain_zz_x(n, 0.5), I.random_pauli_sum(n, 12, 3), I.pauli_sum_from_strings(n, [(1.0, "Z0")])]
+    psi, lam = Q.State(n, dt).set_basis(0), Q.State(n, dt)
+    c = Q.circuit_from(circ).finalize(dt)
+    E, G = Q.expectation_with_grad_multi(psi, lam, c, [Q.Hamiltonian(h) for h in hams], params)
+    assert G.shape == (3, circ.n_params)
+    for k, h in enumerate(hams):
+        E0, G0 = O.adjoint_gradient(circ, h, params, O.zero_state(n))
+        assert abs(E[k] - E0) <= TOL[dt] * scale(h)
+        assert np.max(np.abs(G[k] - G0)) <= TOL[dt] * scale(h)
+    # psi is back at |0...0> afterwards (up to rounding)
+    assert abs(abs(complex(psi.amplitudes[0].item())) - 1.0) <= 1e-4
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_measurement_collapse_matches_oracle(Q, dt):
+    """Mid-circuit measurement: the outcome (decided in FP64 on both sides; cases
+    within 1e-9 of the decision boundary are skipped) and the collapsed state."""
+    n = 10
+    checked = 0
+    for seed in range(12):
+        psi0 = I.random_state(n, 100 + seed)
+        q = seed % n
+        base = psi0.astype(np.complex64 if dt == 0 else np.complex128).astype(np.complex128)
+        o_or, st_or, p1 = O.measure(base, n, q, seed)
+        u = O.shot_uniform(seed, 0)
+        if abs((1 - p1) - u) < 1e-9:
+            continue
+        s = Q.State(n, dt).set_qs(psi0)
+        o = Q.measure(s, q, seed)
+        assert o == o_or
+        assert np.max(np.abs(s.get_qs() - st_or)) <= TOL[dt] * max(1.0, np.max(np.abs(st_or)))
+        checked += 1
+    assert checked >= 10

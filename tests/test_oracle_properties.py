@@ -225,3 +225,24 @@ def test_dense_block_appliers_agree_and_factorise(k):
     for t, s in zip(targets, singles):
         want = O.apply_gate(want, n, s, [t])
     assert np.max(np.abs(O.apply_gate(psi, n, K, targets) - want)) < 1e-12
+
+
+def test_measure_bell_state_and_statistics():
+    """A Bell pair collapses onto |00> or |11> whichever qubit is measured; over
+    many seeds the outcome frequency follows P(1) (binomial, 5 sigma)."""
+    bell = np.zeros(4, dtype=complex)
+    bell[0] = bell[3] = 1 / math.sqrt(2)
+    for q in (0, 1):
+        for seed in range(8):
+            o, st, p1 = O.measure(bell, 2, q, seed)
+            want = np.zeros(4, dtype=complex)
+            want[3 if o else 0] = 1.0
+            assert abs(p1 - 0.5) < 1e-15 and np.allclose(st, want, atol=1e-15)
+    psi = I.random_state(5, 3)
+    _, _, p1 = O.measure(psi, 5, 2, 0)
+    trials = 4000
+    ones = sum(O.measure(psi, 5, 2, s)[0] for s in range(trials))
+    assert abs(ones - trials * p1) < 5 * math.sqrt(trials * p1 * (1 - p1))
+    o, st, _ = O.measure(psi, 5, 2, 11)
+    assert abs(np.linalg.norm(st) - 1.0) < 1e-13
+    assert np.all(st[((np.arange(32) >> 2) & 1) != o] == 0)

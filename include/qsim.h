@@ -153,6 +153,16 @@ QS_API qs_status qs_apply_circuit(qs_state* s, qs_circuit* c, const double* para
  * gave up; CUDA-core calls are asynchronous. */
 QS_API qs_status qs_apply_matrix(qs_state* s, int k, const int* targets, const double* matrix, int engine);
 
+/* Autotuner of the fused passes: applies the circuit to `s` (whose contents
+ * it overwrites) under each candidate tile shape -- tile bits m = largest, -1,
+ * -2 for the dtype and state size, times contiguous low bits 2..5 -- timing
+ * `reps` applications per candidate with CUDA events on s's stream, and keeps
+ * the fastest plan in the circuit (fuse = 1).  chosen (may be NULL) receives the
+ * options kept; best_ms (may be NULL) the time of one application.  Not part of
+ * the paper: it picks the engine's tile shape by measurement.  Synchronises. */
+QS_API qs_status qs_circuit_autotune(qs_circuit* c, qs_state* s, const double* params, int n_params, int reps,
+                                     qs_options* chosen, double* best_ms);
+
 /* ------------------------------------------------------------ Hamiltonians */
 
 /* H = sum_k coef[k] P_k with real coefficients (§2.5.1), P_k given by masks:

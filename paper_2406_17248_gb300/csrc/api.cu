@@ -954,6 +954,60 @@ qs_status qs_measure(qs_state* s, int qubit, uint64_t seed, int* outcome) {
   return QS_OK;
 }
 
+qs_status qs_circuit_autotune(qs_circuit* c, qs_state* s, const double* params, int n_params, int reps,
+                              qs_options* chosen, double* best_ms) {
+  QS_TRY(check_state(s));
+  QS_CHECK(c != nullptr, "null circuit");
+  QS_CHECK(c->n == s->n, "circuit and state differ in qubit count");
+  QS_CHECK(n_params >= c->n_params && (c->n_params == 0 || params != nullptr), "too few parameters");
+  QS_CHECK(reps >= 1 && reps <= 100, "reps must be 1..100");
+  const int ne = std::max(c->n, kRegBits);
+  const int mmax = std::min(max_tile_bits(s->dt), ne);
+  std::vector<std::pair<int, int>> cand;  // (tile bits, low bits)
+  for (int m = mmax; m >= std::max(kMinTileBits, mmax - 2); --m)
+    for (int lb = 2; lb <= 5; ++lb)
+      if (lb < m) cand.push_back({m, lb});
+  if (cand.empty()) cand.push_back({mmax, std::max(1, std::min(4, mmax))});
+  cudaEvent_t e0, e1;
+  QS_CUDA(cudaEventCreate(&e0));
+  QS_CUDA(cudaEventCreate(&e1));
+  const qs_options saved = c->opts;
+  double best = 1e300;
+  qs_options bo = saved;
+  qs_status st = QS_OK;
+  for (const auto& mc : cand) {
+    qs_options o = saved;
+    o.fuse = 1;
+    o.tile_bits = mc.first;
+    o.low_bits = mc.second;
+    c->opts = o;
+    if ((st = finalize_plan(c, s->dt, s->st)) != QS_OK) break;
+    if ((st = qs_apply_circuit(s, c, params, n_params)) != QS_OK) break;  // warm-up (uploads the plan's tables)
+    if (cudaEventRecord(e0, s->st) != cudaSuccess) { st = QS_ERR_CUDA; break; }
+    for (int r = 0; r < reps && st == QS_OK; ++r) st = qs_apply_circuit(s, c, params, n_params);
+    if (st != QS_OK) break;
+    float ms = 0.f;
+    if (cudaEventRecord(e1, s->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      st = QS_ERR_CUDA;
+      break;
+    }
+    if (ms / reps < best) {
+      best = ms / reps;
+      bo = o;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->opts = st == QS_OK ? bo : saved;
+  qs_status s2 = finalize_plan(c, s->dt, s->st);
+  if (st != QS_OK) return st;
+  if (s2 != QS_OK) return s2;
+  if (chosen) *chosen = bo;
+  if (best_ms) *best_ms = best;
+  return QS_OK;
+}
+
 qs_status qs_trace_enable(int enable) { return trace_enable(enable); }
 
 qs_status qs_trace_read(int max, int* n, double* ms, double* bytes, int* kinds) {

@@ -49,6 +49,7 @@ SIGNATURES = [
     ("qs_circuit_finalize", [_VP, _I, _VP]),
     ("qs_circuit_info", [_VP, _PI, _PI, _PI]),
     ("qs_apply_circuit", [_VP, _VP, _PD, _I]),
+    ("qs_circuit_autotune", [_VP, _VP, _PD, _I, _I, _VP, _PD]),
     ("qs_apply_matrix", [_VP, _I, _PI, _PD, _I]),
     ("qs_ham_create", [_I, _I, _PU64, _PU64, _PD, _PVP]),
     ("qs_ham_destroy", [_VP]),
@@ -244,6 +245,16 @@ class Circuit:
         pr = np.ascontiguousarray(params if params is not None else np.zeros(0), dtype=np.float64)
         _check(lib().qs_apply_circuit(state.h, self.h, _dptr(pr) if pr.size else None, int(pr.size)))
         return state
+
+    def autotune(self, state: State, params=None, reps: int = 2):
+        """Pick the tile shape by timing (qs_circuit_autotune); overwrites `state`.
+        Returns {"tile_bits", "low_bits", "ms"}."""
+        pr = np.ascontiguousarray(params if params is not None else np.zeros(0), dtype=np.float64)
+        o = Options(0, 0, 0)
+        ms = C.c_double()
+        _check(lib().qs_circuit_autotune(self.h, state.h, _dptr(pr) if pr.size else None, int(pr.size), reps,
+                                         C.byref(o), C.byref(ms)))
+        return {"tile_bits": o.tile_bits, "low_bits": o.low_bits, "ms": ms.value}
 
 
 def circuit_from(circ: I.Circuit) -> Circuit:

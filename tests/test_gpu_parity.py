@@ -299,3 +299,26 @@ def test_measurement_collapse_matches_oracle(Q, dt):
         assert np.max(np.abs(s.get_qs() - st_or)) <= TOL[dt] * max(1.0, np.max(np.abs(st_or)))
         checked += 1
     assert checked >= 10
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_autotuned_plan_stays_exact(Q, dt):
+    """The autotuner (timing of candidate tile shapes) keeps a plan whose results
+    still match the oracle, amplitudes and adjoint gradients."""
+    n = 14
+    circ = I.random_mixed_circuit(n, 60, 23, with_matrix=False)
+    params = I.uniform_params(circ.n_params, 8)
+    c = Q.circuit_from(circ).finalize(dt)
+    scratch = Q.State(n, dt).set_basis(0)
+    best = c.autotune(scratch, params, reps=1)
+    assert best["ms"] > 0 and 6 <= best["tile_bits"] <= 13 and 2 <= best["low_bits"] <= 5
+    psi0 = I.random_state(n, 4)
+    s = Q.State(n, dt).set_qs(psi0)
+    c.apply(s, params)
+    want = O.evolve(circ, params, psi0)
+    assert np.max(np.abs(s.get_qs() - want)) <= TOL[dt]
+    ham = I.chain_zz_x(n, 0.5)
+    psi, lam = Q.State(n, dt).set_basis(0), Q.State(n, dt)
+    E, G = Q.expectation_with_grad(psi, lam, c, Q.Hamiltonian(ham), params)
+    E0, G0 = O.adjoint_gradient(circ, ham, params, O.zero_state(n))
+    assert abs(E - E0) <= TOL[dt] * scale(ham) and np.max(np.abs(G - G0)) <= TOL[dt] * scale(ham)

@@ -214,6 +214,37 @@ QS_API qs_status qs_expectation_with_grad_multi(qs_state* psi, qs_state* lam, qs
  * Sums are FP64 in a fixed order.  *outcome: host int.  Synchronises. */
 QS_API qs_status qs_measure(qs_state* s, int qubit, uint64_t seed, int* outcome);
 
+/* ------------------------------------------------------- density matrices */
+
+/* Density-matrix simulation (§3.2: rho' = U rho U^dag, <H> = tr(rho H)) with
+ * quantum channels (§3.3: Psi(rho) = sum_i K_i rho K_i^dag, sum K_i^dag K_i = I).
+ * rho of n qubits is a qs_state of 2n qubits holding vec[x + 2^n y] = rho_{x,y};
+ * set_basis(0) prepares |0..0><0..0|.  A density-matrix circuit is a 2n-qubit
+ * qs_circuit: each gate is added on the low register and its complex conjugate
+ * on the high register, each channel as its superoperator sum_i K_i (x)
+ * conj(K_i) on (qubit, qubit + n).  Apply it with qs_apply_circuit; the adjoint
+ * gradient is refused once a channel is present (channels are not unitary). */
+typedef enum {
+  QS_CH_PAULI = 0,              /* p = (px, py, pz): (1-px-py-pz) rho + px X rho X + py Y rho Y + pz Z rho Z */
+  QS_CH_DEPOLARIZING = 1,       /* p = (p): (1 - p) rho + p/4 (I rho I + X rho X + Y rho Y + Z rho Z) */
+  QS_CH_AMPLITUDE_DAMPING = 2,  /* p = (gamma): E0 = diag(1, sqrt(1-gamma)), E1 = sqrt(gamma) |0><1| */
+  QS_CH_PHASE_DAMPING = 3,      /* p = (gamma): E0 = diag(1, sqrt(1-gamma)), E1 = sqrt(gamma) |1><1| */
+  QS_CH_KRAUS = 4               /* n_kraus 2x2 operators, (re, im) row-major, 8 doubles each */
+} qs_channel_kind;
+
+/* A density-matrix circuit of n_qubits (1..17) qubits. */
+QS_API qs_status qs_dm_circuit_create(int n_qubits, qs_circuit** out);
+/* Gate U on the system qubits (arguments as qs_circuit_add): adds U and conj(U). */
+QS_API qs_status qs_dm_add_gate(qs_circuit* c, int kind, const int* targets, int n_t, const int* ctrls, int n_c,
+                                int param_idx, double coef, double constant, const double* matrix);
+/* Channel on one system qubit; p: the kind's parameters (host), kraus: for
+ * QS_CH_KRAUS only.  Invalid probabilities or incomplete Kraus sets return
+ * QS_ERR_INVALID_ARG. */
+QS_API qs_status qs_dm_add_channel(qs_circuit* c, int kind, int qubit, const double* p, int n_kraus,
+                                   const double* kraus);
+/* *energy = tr(rho H) for a Pauli sum H on the n system qubits (rho: 2n qubits). */
+QS_API qs_status qs_dm_expectation(const qs_state* rho, const qs_ham* h, double* energy);
+
 /* -------------------------------------------------------------------- QAOA */
 
 /* MaxCut QAOA engine (§5.2 ansatz; QuPack QAOA simulator interface §6.2):

@@ -838,6 +838,7 @@ qs_status qs_expectation_with_grad(qs_state* psi, qs_state* lam, qs_circuit* c, 
   QS_CHECK(c->n == psi->n && h->n == psi->n, "circuit/hamiltonian/state qubit counts differ");
   QS_CHECK(n_params >= c->n_params, "too few parameters");
   QS_CHECK(c->n_params == 0 || (params != nullptr && grad != nullptr), "params/grad is null");
+  QS_CHECK(c->dm_n == 0, "density-matrix circuits: expectation with qs_dm_expectation (no adjoint gradient)");
   if (lam->st != psi->st) QS_CUDA(cudaStreamSynchronize(lam->st));
   QS_TRY(ensure_plan(c, psi->dt, psi->st));
   if (c->plan.fuse < 0) {
@@ -884,6 +885,7 @@ qs_status qs_expectation_with_grad_multi(qs_state* psi, qs_state* lam, qs_circui
   QS_TRY(check_state(psi));
   QS_TRY(check_state(lam));
   QS_CHECK(c != nullptr, "null circuit");
+  QS_CHECK(c->dm_n == 0, "density-matrix circuits: expectation with qs_dm_expectation (no adjoint gradient)");
   QS_CHECK(psi != lam && psi->ptr != lam->ptr, "psi and lam must be different states");
   QS_CHECK(psi->n == lam->n && psi->dt == lam->dt, "psi/lam n or dtype mismatch");
   QS_CHECK(c->n == psi->n, "circuit/state qubit counts differ");

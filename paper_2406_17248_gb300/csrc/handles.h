@@ -57,6 +57,8 @@ struct CircuitPlan {
 
 struct qs_circuit {
   int n = 0;
+  int dm_n = 0;               // > 0: a density-matrix circuit of dm_n qubits (2 dm_n stored)
+  bool has_channel = false;   // holds a channel (non-unitary): no adjoint gradient
   std::vector<HostGate> gates;
   int n_params = 0;
   qs_options opts{};

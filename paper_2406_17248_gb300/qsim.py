@@ -50,6 +50,10 @@ SIGNATURES = [
     ("qs_circuit_info", [_VP, _PI, _PI, _PI]),
     ("qs_apply_circuit", [_VP, _VP, _PD, _I]),
     ("qs_circuit_autotune", [_VP, _VP, _PD, _I, _I, _VP, _PD]),
+    ("qs_dm_circuit_create", [_I, _PVP]),
+    ("qs_dm_add_gate", [_VP, _I, _PI, _I, _PI, _I, _I, _D, _D, _PD]),
+    ("qs_dm_add_channel", [_VP, _I, _I, _PD, _I, _PD]),
+    ("qs_dm_expectation", [_VP, _VP, _PD]),
     ("qs_apply_matrix", [_VP, _I, _PI, _PD, _I]),
     ("qs_ham_create", [_I, _I, _PU64, _PU64, _PD, _PVP]),
     ("qs_ham_destroy", [_VP]),
@@ -424,6 +428,66 @@ class Batch:
         _check(lib().qs_batch_expectation_with_grad_device(self.h, C.c_void_p(params.data_ptr()),
                                                            C.c_void_p(energies.data_ptr()),
                                                            C.c_void_p(grads.data_ptr())))
+
+
+CHANNELS = {"pauli": 0, "depolarizing": 1, "amplitude_damping": 2, "phase_damping": 3, "kraus": 4}
+
+
+class DensityCircuit(Circuit):
+    """A density-matrix circuit of n qubits (qs_dm_*): a 2n-qubit circuit holding
+    each gate and its conjugate, and channels as superoperators."""
+
+    def __init__(self, n: int):
+        self.n_sys = n
+        h = C.c_void_p()
+        _check(lib().qs_dm_circuit_create(n, C.byref(h)))
+        self.h = h
+
+    def add(self, kind: str, targets: Sequence[int], ctrls: Sequence[int] = (), param: int = -1,
+            coef: float = 1.0, const: float = 0.0, matrix=None):
+        t = (C.c_int * len(targets))(*targets)
+        cc = (C.c_int * max(len(ctrls), 1))(*ctrls) if ctrls else None
+        m = None
+        if matrix is not None:
+            mm = np.ascontiguousarray(np.asarray(matrix, dtype=np.complex128)).view(np.float64).reshape(-1)
+            m = mm.ctypes.data_as(_PD)
+            self._keep = mm
+        _check(lib().qs_dm_add_gate(self.h, KIND[kind], t, len(targets), cc, len(ctrls), param, coef, const, m))
+        return self
+
+    def add_channel(self, kind: str, qubit: int, p=(), kraus=None):
+        pr = np.ascontiguousarray(p if len(p) else [0.0], dtype=np.float64)
+        kr = None
+        nk = 0
+        if kraus is not None:
+            ka = np.ascontiguousarray(np.asarray(kraus, dtype=np.complex128)).view(np.float64).reshape(-1)
+            nk = len(kraus)
+            kr = ka.ctypes.data_as(_PD)
+            self._keep_k = ka
+        _check(lib().qs_dm_add_channel(self.h, CHANNELS[kind], qubit, _dptr(pr), nk, kr))
+        return self
+
+
+def dm_circuit_from(circ: I.Circuit, channels_after=None) -> DensityCircuit:
+    """Density-matrix circuit of an inputs.Circuit; channels_after[i] = [(kind, p,
+    qubit)] added after gate i (key -1: before the first gate)."""
+    ch = channels_after or {}
+    c = DensityCircuit(circ.n_qubits)
+    for kind, p, q in ch.get(-1, []):
+        c.add_channel(kind, q, p)
+    for i, g in enumerate(circ.gates):
+        c.add(g.kind, g.targets, g.ctrls, g.param, g.coef, g.const,
+              None if g.matrix is None else np.asarray(g.matrix).reshape(1 << len(g.targets), -1))
+        for kind, p, q in ch.get(i, []):
+            c.add_channel(kind, q, p)
+    return c
+
+
+def dm_expectation(rho: State, ham: Hamiltonian) -> float:
+    """tr(rho H) of a density-matrix state (2n qubits) for an n-qubit Pauli sum."""
+    e = C.c_double()
+    _check(lib().qs_dm_expectation(rho.h, ham.h, C.byref(e)))
+    return e.value
 
 
 def apply_matrix(state: State, targets, matrix, engine: int = 0) -> State:

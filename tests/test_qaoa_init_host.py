@@ -64,3 +64,17 @@ def test_graph_validation(bad):
     with pytest.raises(Q.QSimError) as ex:
         Q.Graphs(node_off, adj_off, adj)
     assert ex.value.status == 1
+
+
+def test_density_matrix_channel_validation():
+    """Channel arguments are checked on the host before any device work."""
+    c = Q.DensityCircuit(3)
+    c.add("H", (0,)).add_channel("depolarizing", 0, (0.2,))
+    for kind, p, kraus in [("depolarizing", (1.5,), None), ("pauli", (0.5, 0.4, 0.3), None),
+                           ("amplitude_damping", (-0.1,), None),
+                           ("kraus", (), [np.eye(2), np.eye(2)])]:
+        with pytest.raises(Q.QSimError) as ex:
+            c.add_channel(kind, 1, p, kraus=kraus)
+        assert ex.value.status == 1
+    with pytest.raises(Q.QSimError):
+        c.add_channel("depolarizing", 3, (0.1,))  # qubit beyond the system

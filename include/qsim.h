@@ -376,6 +376,15 @@ QS_API qs_status qs_gnn_backward(qs_gnn* g, const qs_graphs* graphs, const float
 /* One Adam step (Kingma & Ba 2015, with bias correction; the step count is kept
  * by the network) on the float32 weights, then refresh the bfloat16 copy. */
 QS_API qs_status qs_gnn_adam_step(qs_gnn* g, const float* dev_grad, float lr, float beta1, float beta2, float eps);
+/* One training step on a batch in two launches: per graph the forward pass,
+ * dL/dy of L = mean over the batch's n_graphs * out_dim entries of (y - t)^2,
+ * and the backward pass; then the gradient sums and the Adam update (as
+ * qs_gnn_adam_step).  dev_targets: device float32 [n_graphs * out_dim];
+ * dev_loss: device float32 (may be NULL) receives L.  Equivalent to
+ * forward + qs_mse + backward + adam_step (same weights bit for bit; the loss
+ * is summed in another order).  Asynchronous. */
+QS_API qs_status qs_gnn_train_step(qs_gnn* g, const qs_graphs* graphs, const float* dev_targets, float lr,
+                                   float beta1, float beta2, float eps, float* dev_loss);
 /* *dev_loss = mean of (y - t)^2 over n entries and dev_dy = 2 (y - t) / n (either
  * output may be NULL).  Device float32 arrays, one CTA, fixed summation order. */
 QS_API qs_status qs_mse(int n, const float* dev_y, const float* dev_target, float* dev_loss, float* dev_dy,

@@ -36,6 +36,7 @@ constexpr int kGnnMaxHidden = 64;
 constexpr int kGnnMaxLayers = 4;
 constexpr int kGnnMaxOut = 64;
 constexpr int kGnnInDim = 2;       // node features (1, deg / 3)
+constexpr int kGnnMaxGrid = 4096;  // CTAs of one launch (per-CTA loss partials)
 
 struct GnnBlock {
   int off;   // offset in the flat parameter vector
@@ -271,12 +272,18 @@ __global__ void __launch_bounds__(kGnnThreads) gnn_forward_kernel(GnnDims D, con
   }
 }
 
-// Backward of one graph per iteration; weight gradients added to this CTA's
-// slice part[blockIdx.x * P ...] (one owning thread per entry).
+// Backward of one graph per iteration; weight gradients go to this CTA's slice
+// part[blockIdx.x * P ...] (one owning thread per entry; the CTA's first graph
+// writes every entry, later graphs add).  TRAIN: dL/dy = 2 (y - t) / n_out of
+// the mean squared error is formed in place from the targets, and the CTA's sum
+// of squared errors goes to loss_part[blockIdx.x] (a whole training step's
+// network work in one launch).
+template <bool TRAIN>
 __global__ void __launch_bounds__(kGnnThreads) gnn_backward_kernel(GnnDims D, const __nv_bfloat16* __restrict__ wb,
                                                                    GraphView G, int n_graphs, int mn,
                                                                    const float* __restrict__ dy_all,
-                                                                   float* __restrict__ part) {
+                                                                   float* __restrict__ part, float dy_scale,
+                                                                   float* __restrict__ loss_part) {
   extern __shared__ __align__(16) unsigned char smem[];
   __nv_bfloat16* sw = reinterpret_cast<__nv_bfloat16*>(smem);
   const GnnPtrs p = carve(D, smem, mn);
@@ -294,19 +301,37 @@ __global__ void __launch_bounds__(kGnnThreads) gnn_backward_kernel(GnnDims D, co
   const GnnBlock& b1 = D.blk[3 * D.L + 1];
   const GnnBlock& W2 = D.blk[3 * D.L + 2];
   const GnnBlock& b2 = D.blk[3 * D.L + 3];
+  float sse = 0.f;  // TRAIN: this CTA's sum of squared errors (thread 0)
   for (int g = blockIdx.x; g < n_graphs; g += gridDim.x) {
+    const bool first = g == (int)blockIdx.x;
+    // first graph of the CTA: assign, later graphs: accumulate
+    auto put = [&](int idx, float v) {
+      if (first)
+        gp[idx] = v;
+      else
+        gp[idx] += v;
+    };
     __syncthreads();
     const int nv = load_graph(G, g, p.s_off, p.s_adj);
     __syncthreads();
     forward_graph(D, nv, mn, sw, p.sh, p.sa, r, zpre, y, p.s_off, p.s_adj);
-    for (int o = threadIdx.x; o < O; o += blockDim.x) dy[o] = dy_all[(size_t)g * O + o];
+    if (TRAIN) {
+      for (int o = threadIdx.x; o < O; o += blockDim.x) dy[o] = dy_scale * (y[o] - dy_all[(size_t)g * O + o]);
+      if (threadIdx.x == 0)
+        for (int o = 0; o < O; ++o) {
+          const float e = y[o] - dy_all[(size_t)g * O + o];
+          sse = fmaf(e, e, sse);
+        }
+    } else {
+      for (int o = threadIdx.x; o < O; o += blockDim.x) dy[o] = dy_all[(size_t)g * O + o];
+    }
     __syncthreads();
     // readout MLP
     for (int w = threadIdx.x; w < O * H; w += blockDim.x) {
       const int o = w / H, j = w % H;
-      gp[W2.off + w] += dy[o] * fmaxf(zpre[j], 0.f);
+      put(W2.off + w, dy[o] * fmaxf(zpre[j], 0.f));
     }
-    for (int o = threadIdx.x; o < O; o += blockDim.x) gp[b2.off + o] += dy[o];
+    for (int o = threadIdx.x; o < O; o += blockDim.x) put(b2.off + o, dy[o]);
     for (int j = threadIdx.x; j < H; j += blockDim.x) {
       float s = 0.f;
       for (int o = 0; o < O; ++o) s = fmaf(bf(sw, W2.soff + o * (H + 2) + j), dy[o], s);
@@ -315,9 +340,9 @@ __global__ void __launch_bounds__(kGnnThreads) gnn_backward_kernel(GnnDims D, co
     __syncthreads();
     for (int w = threadIdx.x; w < H * H; w += blockDim.x) {
       const int j = w / H, k = w % H;
-      gp[W1.off + w] += dz[j] * r[k];
+      put(W1.off + w, dz[j] * r[k]);
     }
-    for (int j = threadIdx.x; j < H; j += blockDim.x) gp[b1.off + j] += dz[j];
+    for (int j = threadIdx.x; j < H; j += blockDim.x) put(b1.off + j, dz[j]);
     for (int k = threadIdx.x; k < H; k += blockDim.x) {
       float s = 0.f;
       for (int j = 0; j < H; ++j) s = fmaf(bf(sw, W1.soff + j * (H + 2) + k), dz[j], s);
@@ -348,13 +373,13 @@ __global__ void __launch_bounds__(kGnnThreads) gnn_backward_kernel(GnnDims D, co
           ss = fmaf(g_, h[v * H + i], ss);
           sn = fmaf(g_, p.sa[v * H + i], sn);
         }
-        gp[Bs.off + w] += ss;
-        gp[Bn.off + w] += sn;
+        put(Bs.off + w, ss);
+        put(Bn.off + w, sn);
       }
       for (int o = threadIdx.x; o < H; o += blockDim.x) {
         float s = 0.f;
         for (int v = 0; v < nv; ++v) s += dpre[v * H + o];
-        gp[Bb.off + o] += s;
+        put(Bb.off + o, s);
       }
       if (l == 0) break;
       __syncthreads();  // p.sa (a_l) is read above and becomes q below
@@ -378,6 +403,7 @@ __global__ void __launch_bounds__(kGnnThreads) gnn_backward_kernel(GnnDims D, co
       __syncthreads();
     }
   }
+  if (TRAIN && threadIdx.x == 0) loss_part[blockIdx.x] = sse;
 }
 
 // grad[i] = sum over CTA slices in CTA order.
@@ -386,6 +412,32 @@ __global__ void gnn_reduce_kernel(const float* __restrict__ part, int n_slices, 
     float s = 0.f;
     for (int c = 0; c < n_slices; ++c) s += part[(size_t)c * P + i];
     grad[i] = s;
+  }
+}
+
+// Training step tail: grad[i] = sum of the CTA slices (CTA order), then Adam
+// on weight i (as adam_f32_kernel) and its bf16 copy; block 0 also forms the
+// loss = (sum of the CTAs' squared errors) / n_out.
+__global__ void gnn_reduce_adam_kernel(const float* __restrict__ part, int n_slices, int P, float* __restrict__ w,
+                                       float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2,
+                                       float eps, float c1, float c2, __nv_bfloat16* __restrict__ wb,
+                                       const float* __restrict__ loss_part, float inv_n_out,
+                                       float* __restrict__ loss) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+    float gi = 0.f;
+    for (int c = 0; c < n_slices; ++c) gi += part[(size_t)c * P + i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    w[i] = wi;
+    wb[i] = __float2bfloat16_rn(wi);
+  }
+  if (loss && blockIdx.x == 0 && threadIdx.x == 0) {
+    float s = 0.f;
+    for (int c = 0; c < n_slices; ++c) s += loss_part[c];
+    *loss = s * inv_n_out;
   }
 }
 
@@ -466,6 +518,7 @@ struct qs_gnn {
   __nv_bfloat16* d_wb = nullptr;  // the bfloat16 copy the kernels compute with
   float* d_part = nullptr;
   size_t part_slices = 0;
+  float* d_loss_part = nullptr;  // per-CTA squared errors of a training step
   int step = 0;
 };
 
@@ -473,7 +526,8 @@ namespace {
 
 void free_gnn(qs_gnn* g) {
   if (!g) return;
-  for (void* p : {(void*)g->d_w, (void*)g->d_m, (void*)g->d_v, (void*)g->d_wb, (void*)g->d_part})
+  for (void* p : {(void*)g->d_w, (void*)g->d_m, (void*)g->d_v, (void*)g->d_wb, (void*)g->d_part,
+                  (void*)g->d_loss_part})
     if (p) cudaFree(p);
   delete g;
 }
@@ -582,11 +636,12 @@ qs_status qs_gnn_create(int hidden, int layers, int out_dim, void* cuda_stream, 
   }
   const int smax = (int)g->S[1].total;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(gnn_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(gnn_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(gnn_backward_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(gnn_backward_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
   for (int li = 0; li < 2 && e == cudaSuccess; ++li) {
     // resident CTAs per SM of the heavier (backward) kernel with this layout
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gnn_backward_kernel, kGnnThreads, g->S[li].total);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gnn_backward_kernel<true>, kGnnThreads, g->S[li].total);
     g->grid_max[li] = sms * std::max(occ, 1);
   }
   const size_t P4 = (size_t)P * 4;
@@ -660,12 +715,12 @@ qs_status qs_gnn_backward(qs_gnn* g, const qs_graphs* graphs, const float* dev_d
     QS_CUDA(cudaMalloc(&g->d_part, (size_t)grid * P * 4));
     g->part_slices = grid;
   }
-  QS_CUDA(cudaMemsetAsync(g->d_part, 0, (size_t)grid * P * 4, g->st));
-  if (graphs->n_graphs > 0) {
-    gnn_backward_kernel<<<grid, kGnnThreads, g->S[li].total, g->st>>>(g->D, g->d_wb, view(graphs),
-                                                                       graphs->n_graphs, gnn_mn(li), dev_dout,
-                                                                       g->d_part);
+  if (graphs->n_graphs > 0) {  // every CTA has a graph and writes its whole slice
+    gnn_backward_kernel<false><<<grid, kGnnThreads, g->S[li].total, g->st>>>(
+        g->D, g->d_wb, view(graphs), graphs->n_graphs, gnn_mn(li), dev_dout, g->d_part, 0.f, nullptr);
     QS_CUDA(cudaGetLastError());
+  } else {
+    QS_CUDA(cudaMemsetAsync(g->d_part, 0, (size_t)grid * P * 4, g->st));
   }
   gnn_reduce_kernel<<<blocks_for(P, 256), 256, 0, g->st>>>(g->d_part, grid, P, dev_grad);
   QS_CUDA(cudaGetLastError());
@@ -681,6 +736,38 @@ qs_status qs_gnn_adam_step(qs_gnn* g, const float* dev_grad, float lr, float bet
   const int P = g->D.P;
   adam_f32_kernel<<<blocks_for(P, 256), 256, 0, g->st>>>(P, g->d_w, g->d_m, g->d_v, dev_grad, lr, beta1, beta2, eps,
                                                          (float)c1, (float)c2, g->d_wb);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status qs_gnn_train_step(qs_gnn* g, const qs_graphs* graphs, const float* dev_targets, float lr, float beta1,
+                            float beta2, float eps, float* dev_loss) {
+  QS_CHECK(g != nullptr && graphs != nullptr, "null argument");
+  QS_CHECK(graphs->n_graphs >= 1 && dev_targets != nullptr, "need at least one graph and its targets");
+  QS_CHECK(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps > 0.f, "bad Adam hyper-parameters");
+  const int P = g->D.P;
+  const int li = gnn_layout(graphs);
+  const int grid = gnn_grid(g, li, graphs->n_graphs);
+  if ((size_t)grid > g->part_slices) {
+    if (g->d_part) QS_CUDA(cudaFree(g->d_part));
+    g->d_part = nullptr;
+    g->part_slices = 0;
+    QS_CUDA(cudaMalloc(&g->d_part, (size_t)grid * P * 4));
+    g->part_slices = grid;
+  }
+  if (!g->d_loss_part) QS_CUDA(cudaMalloc(&g->d_loss_part, (size_t)4 * 2 * kGnnMaxGrid));
+  QS_CHECK(grid <= 2 * kGnnMaxGrid, "too many CTAs for the loss buffer");
+  const int n_out = graphs->n_graphs * g->D.O;
+  gnn_backward_kernel<true><<<grid, kGnnThreads, g->S[li].total, g->st>>>(
+      g->D, g->d_wb, view(graphs), graphs->n_graphs, gnn_mn(li), dev_targets, g->d_part, 2.f / (float)n_out,
+      g->d_loss_part);
+  QS_CUDA(cudaGetLastError());
+  g->step += 1;
+  const double c1 = 1.0 / (1.0 - std::pow((double)beta1, g->step));
+  const double c2 = 1.0 / (1.0 - std::pow((double)beta2, g->step));
+  gnn_reduce_adam_kernel<<<blocks_for(P, 256), 256, 0, g->st>>>(g->d_part, grid, P, g->d_w, g->d_m, g->d_v, lr, beta1,
+                                                                beta2, eps, (float)c1, (float)c2, g->d_wb,
+                                                                g->d_loss_part, 1.f / (float)n_out, dev_loss);
   QS_CUDA(cudaGetLastError());
   return QS_OK;
 }

@@ -9,8 +9,8 @@ supplies the pieces around the CUDA kernels (qs_gnn_*, qs_batch_*, qs_adam_f64):
 * canonicalise: one representative of each class of angles with equal energy.
 * AngleOptimiser: Adam on the angles of many QAOA instances at once -- one
   batched energy+gradient launch and one Adam launch per step, on the device.
-* Initialiser: the network, its training loop (forward, MSE, backward, Adam on
-  the device) and prediction.
+* Initialiser: the network, its training loop (one fused training-step launch
+  plus the gradient-sum/Adam launch per batch) and prediction.
 * steps_to_ratio: Adam steps until the approximation ratio reaches a target.
 
 Angle convention (the circuit of §5.2): layer l applies RZZ(g_l) on every edge,
@@ -153,18 +153,11 @@ class Initialiser:
             gb = Q.Graphs.from_graphs([graphs[i] for i in idx])
             tb = torch.as_tensor(np.asarray(targets, dtype=np.float32)[idx]).to(dev)
             batches.append((gb, tb))
-        y = torch.zeros(batch_size, 2 * self.p, dtype=torch.float32, device=dev)
-        dy = torch.zeros_like(y)
-        grad = torch.zeros(self.net.n_weights, dtype=torch.float32, device=dev)
         losses = torch.zeros(epochs, len(batches), dtype=torch.float32, device=dev)
         for ep in range(epochs):
             for bi in rng.permutation(len(batches)):
                 gb, tb = batches[bi]
-                yb, dyb = y[: gb.n_graphs], dy[: gb.n_graphs]
-                self.net.forward(gb, yb)
-                Q.mse(yb, tb, losses[ep, bi:bi + 1], dyb, stream=self.stream)
-                self.net.backward(gb, dyb, grad)
-                self.net.adam_step(grad, lr)
+                self.net.train_step(gb, tb, lr, losses[ep, bi:bi + 1])
             if log_every and (ep + 1) % log_every == 0:
                 print(f"epoch {ep + 1}: loss {losses[ep].mean().item():.5f}", flush=True)
         return losses.mean(dim=1).cpu().numpy()

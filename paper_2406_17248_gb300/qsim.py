@@ -86,6 +86,7 @@ SIGNATURES = [
     ("qs_gnn_forward", [_VP, _VP, _VP]),
     ("qs_gnn_backward", [_VP, _VP, _VP, _VP]),
     ("qs_gnn_adam_step", [_VP, _VP, C.c_float, C.c_float, C.c_float, C.c_float]),
+    ("qs_gnn_train_step", [_VP, _VP, _VP, C.c_float, C.c_float, C.c_float, C.c_float, _VP]),
     ("qs_mse", [_I, _VP, _VP, _VP, _VP, _VP]),
     ("qs_adam_f64", [_I, _VP, _VP, _VP, _VP, _I, _D, _D, _D, _D, _I, _VP]),
     ("qs_expectation_noalloc", [_VP, _I, _I, _I, _PU64, _PU64, _PD, _VP, _PD]),
@@ -695,6 +696,12 @@ class GNN:
 
     def adam_step(self, grad, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
         _check(lib().qs_gnn_adam_step(self.h, _dev(grad), lr, beta1, beta2, eps))
+
+    def train_step(self, graphs: Graphs, targets, lr: float, loss=None, beta1: float = 0.9, beta2: float = 0.999,
+                   eps: float = 1e-8):
+        """Forward, MSE gradient, backward and Adam in two launches (qs_gnn_train_step)."""
+        _check(lib().qs_gnn_train_step(self.h, graphs.h, _dev(targets), lr, beta1, beta2, eps,
+                                       _dev(loss) if loss is not None else None))
 
 
 def mse(y, target, loss=None, dy=None, stream=None):

@@ -212,3 +212,44 @@ def test_gnn_bench_batch_forward_and_sampled_backward(Q):
     init.net.backward(Q.Graphs(*batch), torch.as_tensor(dy).cuda(), grad)
     g_or = G.backward(w64, *batch, dy.astype(np.float64))
     assert np.max(np.abs(grad.cpu().numpy() - g_or)) <= 1e-4 * max(1.0, np.max(np.abs(g_or)))
+
+
+def test_fused_train_step_equals_separate_calls(Q):
+    """qs_gnn_train_step (two launches) gives the same weights bit for bit as
+    forward + MSE + backward + Adam, and the loss to float32 rounding; the
+    loss matches the oracle's MSE of the oracle forward pass."""
+    dims = dict(hidden=64, layers=3, out_dim=8)
+    w0 = _random_weights(4, **dims)
+    graphs = I.graph_set(40, 12, (6, 26))
+    targets = np.random.default_rng(2).normal(size=(len(graphs), 8)).astype(np.float32)
+    gb = Q.Graphs.from_graphs(graphs)
+    t = torch.as_tensor(targets).cuda()
+    a, b = Q.GNN(64, 3, 8), Q.GNN(64, 3, 8)
+    a.set_weights(w0)
+    b.set_weights(w0)
+    loss_a = torch.zeros(1, device="cuda")
+    for _ in range(3):
+        a.train_step(gb, t, 1e-3, loss_a)
+    y = torch.zeros(len(graphs), 8, device="cuda")
+    dy = torch.zeros_like(y)
+    grad = torch.zeros(b.n_weights, device="cuda")
+    loss_b = torch.zeros(1, device="cuda")
+    for _ in range(3):
+        b.forward(gb, y)
+        Q.mse(y, t, loss_b, dy)
+        b.backward(gb, dy, grad)
+        b.adam_step(grad, 1e-3)
+    wa, wba = a.get_weights()
+    wb_, wbb = b.get_weights()
+    assert np.array_equal(wa, wb_) and np.array_equal(wba, wbb)
+    assert abs(loss_a.item() - loss_b.item()) <= 1e-5 * loss_b.item()
+    # the loss of the last step was taken before its update: compare with the
+    # oracle on the weights in force at that step (two steps applied)
+    c = Q.GNN(64, 3, 8)
+    c.set_weights(w0)
+    for _ in range(2):
+        c.train_step(gb, t, 1e-3)
+    _, wbc = c.get_weights()
+    y_or = G.forward(_bf16_bits_to_f64(wbc), *I.pack_graphs(graphs))
+    l_or, _ = G.mse(y_or, targets.astype(np.float64))
+    assert abs(loss_a.item() - l_or) <= 1e-4 * l_or

@@ -273,6 +273,46 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
       off += cnt;
     }
   }
+  // runs of single-qubit gates for the forward passes
+  P.run_head.assign(G, -1);
+  P.runs.clear();
+  P.run_off.clear();
+  P.run_diag.clear();
+  if (c->fuse_1q) {
+    auto single = [&](const HostGate& g) { return g.nt == 1 && g.ctrls.empty() && g.kind != QS_GATE_I; };
+    std::vector<int> last(64, -1);        // latest gate touching each qubit
+    std::vector<int> run_of(G, -1);       // gate -> index in P.runs of the run it heads or joins
+    for (size_t i = 0; i < G; ++i) {
+      const HostGate& g = c->gates[i];
+      if (g.kind == QS_GATE_I) continue;
+      if (single(g)) {
+        const int q = g.t[0], j = last[q];
+        if (j >= 0 && single(c->gates[j])) {
+          int r = run_of[j];
+          if (r < 0) {
+            r = (int)P.runs.size();
+            P.runs.push_back({j});
+            run_of[j] = r;
+          }
+          P.runs[r].push_back((int)i);
+          run_of[i] = r;
+          P.run_head[i] = P.runs[r][0];
+          last[q] = (int)i;
+          continue;
+        }
+      }
+      last[g.t[0]] = (int)i;
+      if (g.nt == 2) last[g.t[1]] = (int)i;
+      for (int q : g.ctrls) last[q] = (int)i;
+    }
+    for (const auto& r : P.runs) {
+      bool diag = true;
+      for (int i : r) diag = diag && gate_diagonal(c->gates[i].kind);
+      P.run_diag.push_back(diag);
+      P.run_off.push_back(off);
+      off += 4;
+    }
+  }
   P.n_coef = std::max(off, 1);
   QS_CUDA(cudaMalloc(&P.d_coef, (size_t)P.n_coef * 16));
   if (P.fuse < 0) {
@@ -304,8 +344,19 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
     return it;
   };
   std::vector<PlanItem> fwd, rev;
-  for (size_t i = 0; i < G; ++i)
-    if (c->gates[i].kind != QS_GATE_I) fwd.push_back(make_item(i, false));
+  std::vector<int> run_index(G, -1);  // head gate -> its run
+  for (size_t r = 0; r < P.runs.size(); ++r) run_index[P.runs[r][0]] = (int)r;
+  for (size_t i = 0; i < G; ++i) {
+    if (c->gates[i].kind == QS_GATE_I || P.run_head[i] >= 0) continue;  // absorbed into its run's head
+    PlanItem it = make_item(i, false);
+    const int r = run_index[i];
+    if (r >= 0) {  // the run's product replaces the head gate's op
+      it.kind = P.run_diag[r] ? IK_DIAG : IK_DENSE1;
+      it.ops.clear();
+      it.ops.push_back(ItemOp{(uint8_t)(P.run_diag[r] ? OP_DIAG : OP_DENSE1), 0, P.run_off[r], -1, 0.0});
+    }
+    fwd.push_back(it);
+  }
   for (size_t i = G; i-- > 0;)
     if (c->gates[i].kind != QS_GATE_I || c->gates[i].param >= 0) rev.push_back(make_item(i, true));
   SlotMap none;
@@ -358,6 +409,30 @@ qs_status fill_circuit_coef(qs_circuit* c, const double* params) {
         for (int k = 0; k < d; ++k) put(P.off_a[i], k, A[k * d + k]);
       } else {
         for (int k = 0; k < d * d; ++k) put(P.off_a[i], k, A[k]);
+      }
+    }
+  }
+  // products of the single-qubit runs (later gates multiply on the left)
+  for (size_t r = 0; r < P.runs.size(); ++r) {
+    cd M[4] = {1, 0, 0, 1};
+    for (int i : P.runs[r]) {
+      cd U[16];
+      int d = 0;
+      gate_unitary(c->gates[i], gate_angle(c->gates[i], params), U, &d);
+      const cd N[4] = {U[0] * M[0] + U[1] * M[2], U[0] * M[1] + U[1] * M[3], U[2] * M[0] + U[3] * M[2],
+                       U[2] * M[1] + U[3] * M[3]};
+      for (int k = 0; k < 4; ++k) M[k] = N[k];
+    }
+    const int o = P.run_off[r];
+    if (P.run_diag[r]) {
+      tab[2 * o] = M[0].real();
+      tab[2 * o + 1] = M[0].imag();
+      tab[2 * (o + 1)] = M[3].real();
+      tab[2 * (o + 1) + 1] = M[3].imag();
+    } else {
+      for (int k = 0; k < 4; ++k) {
+        tab[2 * (o + k)] = M[k].real();
+        tab[2 * (o + k) + 1] = M[k].imag();
       }
     }
   }

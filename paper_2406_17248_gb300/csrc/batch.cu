@@ -303,6 +303,7 @@ qs_status qs_batch_create(int n_inst, const int* n_qubits, const int* gate_offse
         s = qs_circuit_add(B.c, g.kind, g.targets, g.n_targets, ctrls, nc, g.param, g.coef, g.constant, nullptr);
       }
       if (s == QS_OK) B.c->n_params = std::max(B.c->n_params, param_offsets[i + 1] - param_offsets[i]);
+      B.c->fuse_1q = false;  // coefficients are formed per gate on the device
       if (s == QS_OK) s = qs_circuit_finalize(B.c, dtype, nullptr);
       if (s == QS_OK) {
         const int t0 = term_offsets[i], nt = term_offsets[i + 1] - t0;

@@ -31,6 +31,12 @@ struct CircuitPlan {
   TilePlan fwd, rev;
   SlotMap rev_slots;
   std::vector<int> off_u, off_ud, off_a, gclass;
+  // forward passes: runs of single-qubit, uncontrolled gates on one qubit with
+  // nothing else on that qubit in between become one 2x2 op (product of the run)
+  std::vector<int> run_head;                 // gate -> first gate of its run, -1 if not absorbed
+  std::vector<std::vector<int>> runs;        // runs of >= 2 gates, in circuit order
+  std::vector<int> run_off;                  // coefficient offset of each run's product
+  std::vector<char> run_diag;                // every gate of the run is diagonal
   int n_coef = 0;
   void* d_coef = nullptr;
   int* d_row = nullptr;
@@ -59,6 +65,7 @@ struct qs_circuit {
   int n = 0;
   int dm_n = 0;               // > 0: a density-matrix circuit of dm_n qubits (2 dm_n stored)
   bool has_channel = false;   // holds a channel (non-unitary): no adjoint gradient
+  bool fuse_1q = true;        // forward passes merge runs of single-qubit gates (needs host coefficients)
   std::vector<HostGate> gates;
   int n_params = 0;
   qs_options opts{};

@@ -41,6 +41,9 @@ struct qs_batch {
   std::vector<BLane> lanes;
   BCoefGate* d_cg = nullptr;       // coefficient-table entries of the large instances' gates
   int n_cg = 0;
+  BCoefRun* d_runs = nullptr;      // fused single-qubit runs of their forward passes
+  BCoefGate* d_run_members = nullptr;
+  int n_runs = 0;
   cudaEvent_t ev_fill = nullptr;
   // the whole call (coefficients, lanes, persistent kernel) captured once as a
   // CUDA graph on the batch's own parameter/output buffers and replayed
@@ -83,6 +86,8 @@ void free_batch(qs_batch* b) {
       if (p) cudaFree(p);
   }
   if (b->d_cg) cudaFree(b->d_cg);
+  if (b->d_runs) cudaFree(b->d_runs);
+  if (b->d_run_members) cudaFree(b->d_run_members);
   if (b->ev_fill) cudaEventDestroy(b->ev_fill);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->cap_st) cudaStreamDestroy(b->cap_st);
@@ -139,6 +144,7 @@ static qs_status issue_all(qs_batch* b, cudaStream_t st, const double* dev_param
   // persistent kernel)
   if (!b->large.empty()) {
     QS_TRY(launch_batch_coef(b->dt, b->d_cg, b->n_cg, dev_params, st));
+    QS_TRY(launch_batch_runs(b->dt, b->d_runs, b->n_runs, b->d_run_members, dev_params, st));
     QS_CUDA(cudaEventRecord(b->ev_fill, st));
     for (BLane& L : b->lanes) QS_CUDA(cudaStreamWaitEvent(L.st, b->ev_fill, 0));
     for (size_t k = 0; k < b->large.size(); ++k)
@@ -282,7 +288,8 @@ qs_status qs_batch_create(int n_inst, const int* n_qubits, const int* gate_offse
   if (big_n) {
     // instances beyond shared memory: a circuit plan and a Hamiltonian each, run
     // on fused tile passes; their matrices are formed on the device per call
-    std::vector<BCoefGate> cg;
+    std::vector<BCoefGate> cg, run_members;
+    std::vector<BCoefRun> runs;
     size_t need = 16;
     int max_ne = kRegBits;
     for (int i = 0; i < n_inst; ++i) {
@@ -303,7 +310,6 @@ qs_status qs_batch_create(int n_inst, const int* n_qubits, const int* gate_offse
         s = qs_circuit_add(B.c, g.kind, g.targets, g.n_targets, ctrls, nc, g.param, g.coef, g.constant, nullptr);
       }
       if (s == QS_OK) B.c->n_params = std::max(B.c->n_params, param_offsets[i + 1] - param_offsets[i]);
-      B.c->fuse_1q = false;  // coefficients are formed per gate on the device
       if (s == QS_OK) s = qs_circuit_finalize(B.c, dtype, nullptr);
       if (s == QS_OK) {
         const int t0 = term_offsets[i], nt = term_offsets[i + 1] - t0;
@@ -327,6 +333,25 @@ qs_status qs_batch_create(int n_inst, const int* n_qubits, const int* gate_offse
         d.constant = hg.constant;
         cg.push_back(d);
       }
+      for (size_t r = 0; r < P.runs.size(); ++r) {
+        BCoefRun R;
+        R.table = P.d_coef;
+        R.off = P.run_off[r];
+        R.begin = (int)run_members.size();
+        R.count = (int)P.runs[r].size();
+        R.diag = P.run_diag[r] ? 1 : 0;
+        for (int gi : P.runs[r]) {
+          const HostGate& hg = B.c->gates[gi];
+          BCoefGate d{};
+          d.kind = (uint8_t)hg.kind;
+          d.nt = 1;
+          d.param = hg.param >= 0 ? param_offsets[i] + hg.param : -1;
+          d.coef = hg.coef;
+          d.constant = hg.constant;
+          run_members.push_back(d);
+        }
+        runs.push_back(R);
+      }
       const size_t n_slots = P.rev_slots.out.size();
       need = std::max(need, std::max<size_t>(n_slots, 1) * P.grid2 + n_slots + 1 +
                                 (size_t)ham_grid_size(P.ne) + 16);
@@ -334,6 +359,9 @@ qs_status qs_batch_create(int n_inst, const int* n_qubits, const int* gate_offse
     }
     if (s == QS_OK) s = upload(&b->d_cg, cg);
     b->n_cg = (int)cg.size();
+    if (s == QS_OK) s = upload(&b->d_runs, runs);
+    if (s == QS_OK) s = upload(&b->d_run_members, run_members);
+    b->n_runs = (int)runs.size();
     if (s == QS_OK) {
       // instances of 14-17 qubits have only 4-32 tiles per pass: many lanes in
       // flight keep the SMs busy; the largest instances are dealt out first

@@ -53,6 +53,17 @@ struct BCoefGate {
 };
 // Fill the tables of every such gate from the device parameters.
 qs_status launch_batch_coef(qs_dtype dt, const BCoefGate* g, int n, const double* params, cudaStream_t st);
+
+// A run of single-qubit gates fused into one 2x2 op of a forward pass: its
+// product (members[begin .. begin + count), in circuit order) goes to table[off].
+struct BCoefRun {
+  void* table;
+  int off;
+  int begin, count;
+  int diag;  // store the two diagonal entries only
+};
+qs_status launch_batch_runs(qs_dtype dt, const BCoefRun* runs, int n, const BCoefGate* members,
+                            const double* params, cudaStream_t st);
 int batch_grid_size(qs_dtype dt, int smem_amps);
 size_t batch_smem_bytes(qs_dtype dt, int smem_amps);
 constexpr int kBatchThreads = 512;

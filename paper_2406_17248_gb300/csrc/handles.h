@@ -65,7 +65,7 @@ struct qs_circuit {
   int n = 0;
   int dm_n = 0;               // > 0: a density-matrix circuit of dm_n qubits (2 dm_n stored)
   bool has_channel = false;   // holds a channel (non-unitary): no adjoint gradient
-  bool fuse_1q = true;        // forward passes merge runs of single-qubit gates (needs host coefficients)
+  bool fuse_1q = true;        // forward passes merge runs of single-qubit gates into one 2x2 op
   std::vector<HostGate> gates;
   int n_params = 0;
   qs_options opts{};

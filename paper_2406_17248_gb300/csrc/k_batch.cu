@@ -363,7 +363,56 @@ __global__ void batch_coef_kernel(const BCoefGate* __restrict__ gates, int n, co
   }
 }
 
+// Products of single-qubit runs (later gates multiply on the left), from the
+// device parameters, into the fused op's table entries.
+template <class V>
+__global__ void batch_run_kernel(const BCoefRun* __restrict__ runs, int n, const BCoefGate* __restrict__ members,
+                                 const double* __restrict__ params) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const BCoefRun R = runs[r];
+  double2 M[4] = {{1, 0}, {0, 0}, {0, 0}, {1, 0}};
+  for (int k = 0; k < R.count; ++k) {
+    const BCoefGate g = members[R.begin + k];
+    const double th = g.param < 0 ? g.constant : g.constant + g.coef * params[g.param];
+    double2 U[16];
+    bgate_matrix<double2, double>(g.kind, th, U);
+    double2 N[4];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        const double2 x = bmul(U[2 * a], M[b]), y = bmul(U[2 * a + 1], M[2 + b]);
+        N[2 * a + b] = make_double2(x.x + y.x, x.y + y.y);
+      }
+    for (int e = 0; e < 4; ++e) M[e] = N[e];
+  }
+  V* tab = reinterpret_cast<V*>(R.table);
+  auto put = [&](int k, double2 v) {
+    V o;
+    o.x = (decltype(o.x))v.x;
+    o.y = (decltype(o.x))v.y;
+    tab[R.off + k] = o;
+  };
+  if (R.diag) {
+    put(0, M[0]);
+    put(1, M[3]);
+  } else {
+    for (int e = 0; e < 4; ++e) put(e, M[e]);
+  }
+}
+
 }  // namespace
+
+qs_status launch_batch_runs(qs_dtype dt, const BCoefRun* runs, int n, const BCoefGate* members,
+                            const double* params, cudaStream_t st) {
+  if (n <= 0) return QS_OK;
+  const int threads = 128, blocks = (n + threads - 1) / threads;
+  if (dt == QS_C64)
+    batch_run_kernel<float2><<<blocks, threads, 0, st>>>(runs, n, members, params);
+  else
+    batch_run_kernel<double2><<<blocks, threads, 0, st>>>(runs, n, members, params);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
 
 qs_status launch_batch_coef(qs_dtype dt, const BCoefGate* g, int n, const double* params, cudaStream_t st) {
   if (n <= 0) return QS_OK;

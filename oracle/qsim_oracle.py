@@ -499,3 +499,54 @@ def measure(psi: np.ndarray, n: int, qubit: int, seed: int):
     out = np.where(keep, psi, 0.0).astype(psi.dtype)
     pk = p1 if outcome == 1 else p0
     return outcome, out / math.sqrt(pk), p1 / tot
+
+
+# --------------------------------------------------------------------------- DC-QAOA (§5.4)
+
+def dcqaoa_state_by_definition(n: int, ham_prob: PauliSum, params: Sequence[float], p: int,
+                               cd: bool = True) -> np.ndarray:
+    """DC-QAOA state written from its definition in §5.4: start from H^n|0> (the
+    ground state of -sum X, prepared by a Hadamard on every qubit), then per layer
+    apply U_p(gamma) = exp(-i gamma H_prob), U_m(beta) = exp(-i beta sum_q X_q) and,
+    with ``cd``, U_cd(alpha) = exp(-i alpha sum_q Y_q), each as the matrix
+    exponential of the dense operator (scipy.linalg.expm; n <= 10).  Parameters
+    per layer: (gamma, beta, alpha), or (gamma, beta) without ``cd``.  This is
+    independent of any gate decomposition of the three evolutions."""
+    from scipy.linalg import expm
+    from paper_2406_17248_gb300.inputs import pauli_sum_from_strings
+    if n > 10:
+        raise ValueError("dense matrix exponentials are limited to n <= 10")
+    Hp = hamiltonian_matrix(ham_prob)
+    Hm = hamiltonian_matrix(pauli_sum_from_strings(n, [(1.0, f"X{q}") for q in range(n)]))
+    Hcd = hamiltonian_matrix(pauli_sum_from_strings(n, [(1.0, f"Y{q}") for q in range(n)]))
+    per = 3 if cd else 2
+    psi = plus_state(n)
+    for l in range(p):
+        psi = expm(-1j * params[per * l] * Hp) @ psi
+        psi = expm(-1j * params[per * l + 1] * Hm) @ psi
+        if cd:
+            psi = expm(-1j * params[per * l + 2] * Hcd) @ psi
+    return psi
+
+
+def dcqaoa_p1_energy_at_gamma0(n: int, J: float, h: float, alpha: float) -> float:
+    """<H_prob> of one DC-QAOA layer with gamma = 0 and k = 0, in closed form.
+    With gamma = 0 the state is a product: each qubit is exp(-i alpha Y)
+    exp(-i beta X)|+>; the X evolution only multiplies |+> by a phase, and the Y
+    evolution turns the Bloch vector (1, 0, 0) about the y axis by 2 alpha to
+    (cos 2a, 0, -sin 2a).  So <Z_q> = -sin 2a, <Z_i Z_{i+1}> = sin^2 2a and
+    E = -J (n - 1) sin^2(2a) + h n sin(2a), for every beta; at alpha = -pi/4 this is
+    the ground energy -(J (n - 1) + h n) of the chain (J, h >= 0)."""
+    s = math.sin(2.0 * alpha)
+    return -J * (n - 1) * s * s + h * n * s
+
+
+def ising_chain_min_energy_brute_force(n: int, J: float, h: float) -> float:
+    """min over spin configurations z in {+1, -1}^n of -J sum z_i z_{i+1} - h sum z_i
+    by enumeration (the diagonal of H_prob for k = 0, §5.4)."""
+    best = math.inf
+    for x in range(1 << n):
+        z = [1 - 2 * ((x >> q) & 1) for q in range(n)]
+        e = -J * sum(z[i] * z[i + 1] for i in range(n - 1)) - h * sum(z)
+        best = min(best, e)
+    return best

@@ -23,6 +23,12 @@ Workload recipes (shapes follow the paper's benchmarks, §7.1 random circuits an
 * ``erdos_renyi``      G(n, p).
 * ``qaoa_circuit``     |+>^n, then per layer RZZ(gamma_l) on every edge followed by
                        RX(beta_l) on every qubit (cost first, mixer second, §5.2).
+* ``lfim``             H_prob = -J sum_i Z_i Z_{i+1} - h sum_i Z_i + k sum_i X_i on an
+                       open chain (§5.4; the longitudinal-field case is J = h = 1, k = 0).
+* ``dcqaoa_circuit``   DC-QAOA (§5.4): |+>^n, then per layer U_p(gamma_l) =
+                       exp(-i gamma_l H_prob), U_m(beta_l) = exp(-i beta_l sum X),
+                       U_cd(alpha_l) = exp(-i alpha_l sum Y) with the CD pool term
+                       A* = sum_i Y_i.  Parameters per layer (gamma_l, beta_l, alpha_l).
 """
 from __future__ import annotations
 
@@ -224,6 +230,42 @@ def qaoa_circuit(n: int, edges: Sequence[Tuple[int, int]], p: int, gamma_coef: f
         for q in range(n):
             gates.append(Gate("RX", (q,), param=p + l))
     return Circuit(n, gates, 2 * p)
+
+
+def lfim(n: int, J: float = 1.0, h: float = 1.0, k: float = 0.0) -> PauliSum:
+    """The Ising problem Hamiltonian of the DC-QAOA example (§5.4) on an open chain."""
+    terms = [(-J, f"Z{i} Z{i + 1}") for i in range(n - 1)]
+    terms += [(-h, f"Z{i}") for i in range(n)]
+    if k != 0.0:
+        terms += [(k, f"X{i}") for i in range(n)]
+    return pauli_sum_from_strings(n, terms)
+
+
+def dcqaoa_circuit(n: int, p: int, J: float = 1.0, h: float = 1.0, k: float = 0.0, cd: bool = True) -> Circuit:
+    """Gate-level DC-QAOA ansatz (§5.4): H on every qubit, then per layer l
+    exp(-i gamma_l H_prob) as RZZ(-2 J gamma_l) on each chain bond, RZ(-2 h gamma_l)
+    and (k != 0) RX(2 k gamma_l) on each qubit -- exact for k = 0, where the terms
+    commute, and the first-order product of the term exponentials otherwise --
+    then RX(2 beta_l) on every qubit (mixer sum X) and, with ``cd``, RY(2 alpha_l)
+    on every qubit (the counterdiabatic term sum Y).  Parameters, layer by layer:
+    (gamma_l, beta_l, alpha_l), or (gamma_l, beta_l) without ``cd``."""
+    per = 3 if cd else 2
+    gates: List[Gate] = [Gate("H", (q,)) for q in range(n)]
+    for l in range(p):
+        g, b, a = per * l, per * l + 1, per * l + 2
+        for i in range(n - 1):
+            gates.append(Gate("RZZ", (i, i + 1), param=g, coef=-2.0 * J))
+        for q in range(n):
+            gates.append(Gate("RZ", (q,), param=g, coef=-2.0 * h))
+        if k != 0.0:
+            for q in range(n):
+                gates.append(Gate("RX", (q,), param=g, coef=2.0 * k))
+        for q in range(n):
+            gates.append(Gate("RX", (q,), param=b, coef=2.0))
+        if cd:
+            for q in range(n):
+                gates.append(Gate("RY", (q,), param=a, coef=2.0))
+    return Circuit(n, gates, per * p)
 
 
 # --------------------------------------------------------------------------- batches

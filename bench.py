@@ -795,9 +795,172 @@ def run_dm_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_dcqaoa_workload(args):
+    """DC-QAOA on the 12-qubit longitudinal-field Ising chain (J = h = 1, k = 0),
+    one layer (gamma, beta, alpha), CD term sum Y: ``--instances`` random starts
+    U[0, 0.1) (seeds 1, 2, ...) trained together with Adam (lr 0.05).  A step =
+    one batched energy + adjoint gradient of every start (complex128, each
+    start's psi and lam in one CTA's shared memory) and one Adam kernel over all
+    parameters.  value = start-steps/s."""
+    import numpy as np
+    import torch
+    from paper_2406_17248_gb300 import build, inputs as I
+    build.build()
+    from paper_2406_17248_gb300 import qsim as Q, vqa
+    n, p = 12, 1
+    starts = args.instances
+    inst = vqa.dcqaoa_multistart(n, p, starts, seed=1)
+    res = {}
+    for dt, name in ((Q.C64, "c64"), (Q.C128, "c128")):
+        opt = vqa.BatchAdam(inst, dt, lr=0.05)
+        for _ in range(max(3, args.warmup)):
+            opt.step()
+        torch.cuda.synchronize()
+        clocks = ClockSampler()
+        clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            opt.step()
+        ev1.record()
+        torch.cuda.synchronize()
+        ck = clocks.stop()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        res[name] = {"ms": ms, "value": starts / (ms / 1e3), "clocks": ck}
+    # the optimisation itself (untimed): 100 more steps of the complex128 run
+    opt.run(max(1, 100 - opt.t))
+    e_final = opt.energies.cpu().numpy()
+    # end to end through the public call with host buffers: params H2D, energies
+    # and gradients D2H every step, Adam on the host
+    b = opt.batch
+    x = np.concatenate([it.params for it in inst])
+    m, v = np.zeros_like(x), np.zeros_like(x)
+    b.expectation_with_grad(x)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for t in range(1, args.steps + 1):
+        e, g = b.expectation_with_grad(x)
+        gc = np.concatenate(g)
+        m = 0.9 * m + 0.1 * gc
+        v = 0.999 * v + 0.001 * gc * gc
+        x = x - 0.05 * (m / (1 - 0.9 ** t)) / (np.sqrt(v / (1 - 0.999 ** t)) + 1e-8)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    line = {"metric": "DC-QAOA multistart Adam start-steps/s (12-qubit LFIM, p = 1, energy + 3 gradients + update)",
+            "value": res["c128"]["value"], "unit": "start-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": res["c128"]["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"DC-QAOA, 12-qubit Ising chain J = h = 1, k = 0, p = 1, CD term sum Y, "
+                                   f"{starts} starts U[0, 0.1) seeds 1..{starts}, Adam lr 0.05, complex128",
+                       "starts": starts, "l2": "states in shared memory; L2 not involved"},
+            "c64": {"value": res["c64"]["value"], "unit": "start-steps/s", "ms_per_step": res["c64"]["ms"]},
+            "after_training": {"adam_steps": opt.t, "min_energy": float(e_final.min()), "ground_energy": -23.0,
+                                "starts_within_1e-3": int((e_final < -23.0 + 1e-3).sum())},
+            "e2e": {"value": starts / e2e_s, "unit": "start-steps/s", "h2d_bytes_per_step": int(x.nbytes),
+                    "d2h_bytes_per_step": int(x.nbytes + 8 * starts)},
+            "gpu_launches": 2 * args.steps, "clocks": res["c128"]["clocks"]}
+    if not args.no_cpu_baseline:
+        from oracle import gnn_oracle as G
+        from oracle import qsim_oracle as O
+        it = inst[0]
+        xs = np.array(it.params)
+        ms_, vs_ = np.zeros_like(xs), np.zeros_like(xs)
+        t0 = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t0 < 10.0:
+            k += 1
+            e, g = O.adjoint_gradient(it.circuit, it.ham, xs, O.zero_state(n))
+            xs, ms_, vs_ = G.adam(xs, ms_, vs_, g, k, 0.05)
+        line["cpu_baseline"] = {"value": k / (time.perf_counter() - t0), "unit": "start-steps/s", "cores": 1,
+                                "kind": "oracle", "sample": f"{k} oracle Adam steps of start 1"}
+    print(json.dumps(line), flush=True)
+
+
+def run_traj_workload(args):
+    """Noisy 12-qubit HEA (4 layers, 96 parameters U[-pi, pi] seed 1) with a
+    depolarizing channel p = 0.01 on every qubit after every layer (48 sites),
+    H = sum ZZ + 0.5 sum X, complex64, by Monte-Carlo trajectories: a step =
+    ``--instances`` trajectories, each with its energy and adjoint gradient, and
+    the mean gradient.  value = trajectories/s.  The exact tr(rho H) of the same
+    noisy circuit through the density-matrix engine (a 24-qubit vector) is timed
+    beside it."""
+    import numpy as np
+    import torch
+    from paper_2406_17248_gb300 import build, inputs as I
+    build.build()
+    from paper_2406_17248_gb300 import qsim as Q
+    n, layers = 12, 4
+    circ = I.hea_circuit(n, layers)
+    params = I.uniform_params(circ.n_params, 1)
+    ham = I.chain_zz_x(n, 0.5)
+    layer_end = [i for i, g in enumerate(circ.gates) if g.kind == "X" and g.targets == (n - 1,)]
+    ch = {i: [("depolarizing", (0.01,), q) for q in range(n)] for i in layer_end}
+    n_t = args.instances
+    eng = Q.trajectories_from(circ, ch, Q.C64)
+    H = Q.Hamiltonian(ham)
+    pd = torch.tensor(params, dtype=torch.float64, device="cuda")
+    ed = torch.empty(n_t, dtype=torch.float64, device="cuda")
+    gd = torch.empty(circ.n_params, dtype=torch.float64, device="cuda")
+    for w in range(max(3, args.warmup)):
+        eng.run_device(H, pd, n_t, seed=7, energies=ed, grad_mean=gd, first=w * n_t)
+    torch.cuda.synchronize()
+    clocks = ClockSampler()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for s in range(args.steps):
+        eng.run_device(H, pd, n_t, seed=7, energies=ed, grad_mean=gd, first=(s + 8) * n_t)
+    ev1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    e = ed.cpu().numpy()
+    # end to end through the host-buffer call (params H2D, energies + gradient D2H)
+    eng.run(H, params, n_t, seed=7, first=99 * n_t, grad=True)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        eh, gh = eng.run(H, params, n_t, seed=7, first=(s + 100) * n_t, grad=True)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    # exact noisy energy through the density-matrix engine
+    dmc = Q.dm_circuit_from(circ, ch).finalize(Q.C64)
+    rho = Q.State(2 * n, Q.C64)
+    rho.set_basis(0)
+    dmc.apply(rho, params)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        rho.set_basis(0)
+        dmc.apply(rho, params)
+        exact = Q.dm_expectation(rho, H)
+    dm_s = (time.perf_counter() - t0) / 5
+    info = eng.info()
+    line = {"metric": "noisy VQE Monte-Carlo trajectories/s (12-qubit HEA, energy + 96-parameter adjoint gradient each)",
+            "value": n_t / (ms / 1e3), "unit": "trajectories/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"12-qubit HEA, 4 layers, params U[-pi,pi] seed 1, depolarizing 0.01 on every qubit "
+                                   f"after every layer (48 sites), H = sum ZZ + 0.5 sum X, complex64, {n_t} "
+                                   "trajectories per step", "trajectories": n_t,
+                       "l2": "states in shared memory; L2 not involved"},
+            "mean_energy": float(e.mean()), "std_error": float(e.std() / np.sqrt(e.size)),
+            "density_matrix": {"energy": exact, "seconds_per_eval": dm_s, "state": "24-qubit complex64 vector"},
+            "e2e": {"value": n_t / e2e_s, "unit": "trajectories/s", "h2d_bytes_per_step": int(params.nbytes),
+                    "d2h_bytes_per_step": int(8 * n_t + params.nbytes)},
+            "grid": info["grid_grad"], "gpu_launches": 2 * args.steps, "clocks": ck}
+    if not args.no_cpu_baseline:
+        from oracle import traj_oracle as T
+        t0 = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t0 < 10.0:
+            T.trajectory_energy_and_grad(circ, ham, params, ch, 7, k)
+            k += 1
+        line["cpu_baseline"] = {"value": k / (time.perf_counter() - t0), "unit": "trajectories/s", "cores": 1,
+                                "kind": "oracle", "sample": f"{k} oracle trajectories (energy + adjoint gradient)"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="qaoa30", choices=["qaoa30", "batch", "random28", "gnn", "dense28", "hea12", "dm14"])
+    ap.add_argument("--workload", default="qaoa30", choices=["qaoa30", "batch", "random28", "gnn", "dense28", "hea12", "dm14", "dcqaoa12", "traj12"])
     ap.add_argument("--instances", type=int, default=2048)
     ap.add_argument("--plain-instances", type=int, default=2048)
     ap.add_argument("--gpus", type=int, default=1)
@@ -817,6 +980,10 @@ def main():
         return run_batch_workload(args)
     if args.workload == "dm14":
         return run_dm_workload(args)
+    if args.workload == "dcqaoa12":
+        return run_dcqaoa_workload(args)
+    if args.workload == "traj12":
+        return run_traj_workload(args)
     if args.workload == "hea12":
         return run_hea_workload(args)
     if args.workload == "dense28":

@@ -245,6 +245,61 @@ QS_API qs_status qs_dm_add_channel(qs_circuit* c, int kind, int qubit, const dou
 /* *energy = tr(rho H) for a Pauli sum H on the n system qubits (rho: 2n qubits). */
 QS_API qs_status qs_dm_expectation(const qs_state* rho, const qs_ham* h, double* energy);
 
+/* ------------------------------------------------ Monte-Carlo trajectories */
+
+/* The state-vector treatment of channels (§3.3: each noise gate acts with some
+ * probability; averaging over sampled runs of the circuit gives the noisy
+ * result).  A trajectory starts from |0..0>; at channel site s (sites numbered
+ * 0, 1, ... in the order they are added) it takes branch i with probability w_i
+ * and replaces psi by the branch operator applied to psi:
+ *   Pauli (px, py, pz):  w = (1 - px - py - pz, px, py, pz), operators I, X, Y, Z;
+ *   depolarizing (p):    q = p / 4, w = (1 - q - q - q, q, q, q), operators I, X, Y, Z;
+ *   damping / Kraus:     w_i = ||K_i psi||^2 (FP64 sums), operator K_i / sqrt(w_i)
+ *                        (amplitude and phase damping as in qs_channel_kind).
+ * The branch is the smallest i whose running sum w_0 + ... + w_i exceeds
+ * u * (w_0 + ... + w_last), else the last i with w_i > 0, with
+ * u = (splitmix64(seed + c * 0x9E3779B97F4A7C15) >> 11) * 2^-53 for the counter
+ * c = t * n_sites + s of trajectory t (the published splitmix64 of Steele, Lea &
+ * Flood 2014; the same generator as qs_sample).  The mean of the trajectory
+ * energies estimates tr(rho H) of the density-matrix simulator.
+ *
+ * Each trajectory runs in one CTA's shared memory: n_qubits 1..14 (complex64)
+ * or 1..13 (complex128) for energies; with gradients psi and lam both fit:
+ * 1..13 and 1..12.  cuda_stream: the engine's stream (NULL: legacy default). */
+typedef struct qs_traj qs_traj;
+QS_API qs_status qs_traj_create(int n_qubits, qs_dtype dtype, void* cuda_stream, qs_traj** out);
+QS_API qs_status qs_traj_destroy(qs_traj* t);
+/* A gate (arguments as qs_circuit_add; any kind but QS_GATE_MATRIX). */
+QS_API qs_status qs_traj_add_gate(qs_traj* t, int kind, const int* targets, int n_t, const int* ctrls, int n_c,
+                                  int param_idx, double coef, double constant);
+/* A channel site on one qubit: kind a qs_channel_kind, p its parameters (host);
+ * QS_CH_KRAUS: n_kraus (1..4) 2x2 operators, (re, im) row-major, 8 doubles each,
+ * complete to 1e-9.  At most 4096 sites. */
+QS_API qs_status qs_traj_add_channel(qs_traj* t, int kind, int qubit, const double* p, int n_kraus,
+                                     const double* kraus);
+/* Sites, parameters, and the persistent grid of the energy and gradient kernels
+ * (0: the state does not fit in shared memory). */
+QS_API qs_status qs_traj_info(const qs_traj* t, int* n_sites, int* n_params, int* grid_energy, int* grid_grad);
+/* Trajectories first .. first + n_traj - 1 (1 <= n_traj <= 2^24):
+ * energies[i] = <psi_t|H|psi_t> (host double[n_traj]).  grad_mean (host
+ * double[n_params], or NULL for energies only) = the mean over the trajectories
+ * of each trajectory's adjoint gradient (§4.1 / §7.2), each trajectory being the
+ * fixed unitary circuit of its sampled Paulis; refused (QS_ERR_INVALID_ARG)
+ * when a damping or Kraus channel is present.  choices (host
+ * uint8[n_traj * n_sites] or NULL): the branch taken at every site.
+ * Synchronises the engine's stream. */
+QS_API qs_status qs_traj_run(qs_traj* t, const qs_ham* h, const double* params, int n_params, uint64_t seed,
+                             long long first, int n_traj, double* energies, double* grad_mean,
+                             unsigned char* choices);
+/* The same on device buffers (d_params double[n_params], d_energies
+ * double[n_traj], d_grad_mean double[n_params] or NULL), enqueued on the
+ * engine's stream without synchronising. */
+QS_API qs_status qs_traj_run_device(qs_traj* t, const qs_ham* h, const double* d_params, uint64_t seed,
+                                    long long first, int n_traj, double* d_energies, double* d_grad_mean);
+/* The final state of trajectory `traj` into `out` (n_qubits, same dtype). */
+QS_API qs_status qs_traj_state(qs_traj* t, const double* params, int n_params, uint64_t seed, long long traj,
+                               qs_state* out);
+
 /* -------------------------------------------------------------------- QAOA */
 
 /* MaxCut QAOA engine (§5.2 ansatz; QuPack QAOA simulator interface §6.2):

@@ -19,7 +19,7 @@ Conventions fixed here (the paper does not print them):
 * the uniform of trajectory t at site s is ``shot_uniform(seed, t * n_sites + s)``
   -- splitmix64 (Steele, Lea & Flood 2014) of the counter, top 53 bits;
 * branch weights: for the Pauli channel (px, py, pz) the fixed probabilities
-  w = (1 - px - py - pz, px, py, pz) and for the depolarizing channel (p), with
+  w = (max(0, 1 - px - py - pz), px, py, pz) and for the depolarizing channel (p), with
   q = p / 4, w = (1 - q - q - q, q, q, q), each evaluated left to right in FP64;
   the branch operator is then the Pauli itself (I, X, Y, Z), a unitary.  For the
   damping channels and custom Kraus sets, w_i = ||K_i psi||^2 and the branch
@@ -62,7 +62,7 @@ def fixed_weights(kind: str, p: Sequence[float]):
     """Branch probabilities of a mixture-of-Paulis channel, or None."""
     if kind == "pauli":
         px, py, pz = (float(v) for v in p)
-        return [1.0 - px - py - pz, px, py, pz]
+        return [max(0.0, 1.0 - px - py - pz), px, py, pz]
     if kind == "depolarizing":
         q = float(p[0]) / 4.0
         return [1.0 - q - q - q, q, q, q]

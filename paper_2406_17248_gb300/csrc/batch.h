@@ -65,6 +65,42 @@ struct BCoefRun {
 qs_status launch_batch_runs(qs_dtype dt, const BCoefRun* runs, int n, const BCoefGate* members,
                             const double* params, cudaStream_t st);
 int batch_grid_size(qs_dtype dt, int smem_amps);
+
+// Monte-Carlo trajectories of one noisy circuit (the state-vector treatment of
+// channels, §3.3): each trajectory samples one branch operator per channel site
+// and runs in one CTA's shared memory.  A site is a BGate of kind kGateChannel
+// whose param is the site index.
+constexpr int kGateChannel = 250;
+constexpr int kTrajMaxSites = 4096;
+constexpr int kTrajMaxKraus = 4;
+struct BChannel {
+  double K[kTrajMaxKraus][8];  // branch operators, 2x2 (re, im) row-major
+  double w[kTrajMaxKraus];     // fixed branch weights (fixed = 1)
+  int n_kraus;
+  int fixed;  // 1: weights w and unitary branch operators (Pauli, depolarizing);
+              // 0: w_i = ||K_i psi||^2, branch operator K_i / sqrt(w_i)
+  int qubit;
+  int pad;
+};
+struct TrajArgs {
+  const BGate* gates;
+  const BChannel* ch;
+  const DevHamGroup* groups;
+  const DevHamTerm* terms;
+  const double* params;
+  double* energy;     // [n_traj]
+  double* grad;       // [n_traj * n_params] (gradient kernel)
+  uint8_t* choice;    // [n_traj * n_sites] branches taken, or null
+  void* state_out;    // final state of the launch's first trajectory, or null
+  int* queue;         // work counter (zeroed before the launch)
+  uint64_t seed;
+  long long first;    // global index of the launch's first trajectory
+  int n_traj, n, n_gates, n_sites, n_params, n_groups;
+};
+qs_status launch_traj(qs_dtype dt, bool grad, const TrajArgs& a, int grid, cudaStream_t st);
+int traj_grid_size(qs_dtype dt, bool grad, int n);
+// out[c] = (sum over r of rows[r * n_cols + c]) / n_rows, rows summed in order.
+qs_status launch_row_mean(const double* rows, int n_rows, int n_cols, double* out, cudaStream_t st);
 size_t batch_smem_bytes(qs_dtype dt, int smem_amps);
 constexpr int kBatchThreads = 512;
 

@@ -317,6 +317,188 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a) {
   }
 }
 
+// ------------------------------------------------------------ trajectories
+
+// Uniform in [0, 1) of counter c: splitmix64 (Steele, Lea & Flood 2014) of the
+// state seed + c * golden gamma, top 53 bits.
+__device__ __forceinline__ double traj_uniform(uint64_t seed, uint64_t c) {
+  uint64_t z = seed + c * 0x9E3779B97F4A7C15ull + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 0x1.0p-53;
+}
+
+// One channel site of trajectory t: branch weights (fixed, or ||K_i psi||^2 as
+// fixed-order FP64 sums), the branch whose running weight sum first exceeds
+// u * total, then psi <- branch operator psi.  Every thread takes the same
+// decision (the sums are broadcast).  Returns the branch.
+template <class T>
+__device__ int traj_site(const TrajArgs& a, const BChannel& C, int site, long long t, typename BV<T>::V* psi,
+                         double* sh) {
+  using V = typename BV<T>::V;
+  const int n = a.n, q = C.qubit, nk = C.n_kraus;
+  double w[kTrajMaxKraus] = {0, 0, 0, 0};
+  if (C.fixed) {
+    for (int k = 0; k < nk; ++k) w[k] = C.w[k];
+  } else {
+    double acc[kTrajMaxKraus] = {0, 0, 0, 0};
+    const uint64_t P = 1ull << (n - 1);
+    for (uint64_t i = threadIdx.x; i < P; i += blockDim.x) {
+      const uint64_t x0 = bins0(i, q), x1 = x0 | (1ull << q);
+      const double ar = psi[x0].x, ai = psi[x0].y, br = psi[x1].x, bi = psi[x1].y;
+      for (int k = 0; k < nk; ++k) {
+        const double* K = C.K[k];
+        const double y0r = K[0] * ar - K[1] * ai + K[2] * br - K[3] * bi;
+        const double y0i = K[0] * ai + K[1] * ar + K[2] * bi + K[3] * br;
+        const double y1r = K[4] * ar - K[5] * ai + K[6] * br - K[7] * bi;
+        const double y1i = K[4] * ai + K[5] * ar + K[6] * bi + K[7] * br;
+        acc[k] += y0r * y0r + y0i * y0i + y1r * y1r + y1i * y1i;
+      }
+    }
+    for (int k = 0; k < nk; ++k) w[k] = bsum(acc[k], sh);
+  }
+  double total = 0.0;
+  for (int k = 0; k < nk; ++k) total += w[k];
+  const double thr = traj_uniform(a.seed, (uint64_t)t * (uint64_t)a.n_sites + (uint64_t)site) * total;
+  int c = -1;
+  double cum = 0.0;
+  for (int k = 0; k < nk; ++k) {
+    cum += w[k];
+    if (c < 0 && cum > thr) c = k;
+  }
+  if (c < 0)
+    for (int k = 0; k < nk; ++k)
+      if (w[k] > 0) c = k;
+  if (c < 0) c = 0;
+  const double sc = C.fixed ? 1.0 : (w[c] > 0 ? 1.0 / sqrt(w[c]) : 0.0);
+  V M[16], A[16];
+  for (int e = 0; e < 4; ++e) M[e] = bmk<V, T>((T)(C.K[c][2 * e] * sc), (T)(C.K[c][2 * e + 1] * sc));
+  BGate g{};
+  g.kind = kGateChannel;
+  g.nt = 1;
+  g.t0 = (uint8_t)q;
+  bapply<T, false, false>(psi, psi, n, g, M, A);
+  __syncthreads();
+  return c;
+}
+
+// Trajectories from a work queue: psi = (gates and sampled branches)|0>,
+// E = <psi|H|psi>; with GRAD also lam = H psi and the adjoint sweep, each
+// sampled (unitary) branch undone by its adjoint, gradients of trajectory i in
+// row i of a.grad.
+template <class T, bool GRAD>
+__global__ void __launch_bounds__(kBatchThreads, 1) traj_kernel(TrajArgs a) {
+  using V = typename BV<T>::V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sh[kMaxBatchWarps];
+  __shared__ int s_next;
+  __shared__ uint8_t s_choice[kTrajMaxSites];
+  V* psi = reinterpret_cast<V*>(smem);
+  V* lam = psi + (GRAD ? (1ull << a.n) : 0);
+  const int n = a.n;
+  const uint64_t N = 1ull << n;
+  while (true) {
+    if (threadIdx.x == 0) s_next = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int i = s_next;
+    __syncthreads();
+    if (i >= a.n_traj) break;
+    const long long t = a.first + i;
+    double* grad = GRAD ? a.grad + (size_t)i * a.n_params : nullptr;
+    if (GRAD)
+      for (int p = threadIdx.x; p < a.n_params; p += blockDim.x) grad[p] = 0.0;
+    for (uint64_t x = threadIdx.x; x < N; x += blockDim.x) psi[x] = bmk<V, T>(x == 0 ? 1 : 0, 0);
+    __syncthreads();
+    V M[16], A[16];
+    for (int gi = 0; gi < a.n_gates; ++gi) {
+      const BGate g = a.gates[gi];
+      if (g.kind == kGateChannel) {
+        const int c = traj_site<T>(a, a.ch[g.param], g.param, t, psi, sh);
+        if (threadIdx.x == 0) s_choice[g.param] = (uint8_t)c;
+        continue;
+      }
+      const double th = g.param < 0 ? g.constant : g.constant + g.coef * a.params[g.param];
+      bgate_matrix<V, T>(g.kind, (T)th, M);
+      bapply<T, false, false>(psi, lam, n, g, M, A);
+      __syncthreads();
+    }
+    T e = 0;
+    for (uint64_t y = threadIdx.x; y < N; y += blockDim.x) {
+      T lr = 0, li = 0;
+      for (int gg = 0; gg < a.n_groups; ++gg) {
+        const DevHamGroup G = a.groups[gg];
+        const uint64_t x = y ^ G.xmask;
+        const V v = psi[x];
+        T fr = 0, fi = 0;
+        for (int k = G.begin; k < G.end; ++k) {
+          const DevHamTerm tm = a.terms[k];
+          const T sg = (__popcll(x & tm.zmask) & 1) ? (T)-1 : (T)1;
+          fr += sg * (T)tm.re;
+          fi += sg * (T)tm.im;
+        }
+        lr += fr * v.x - fi * v.y;
+        li += fr * v.y + fi * v.x;
+      }
+      if (GRAD) lam[y] = bmk<V, T>(lr, li);
+      const V p = psi[y];
+      e += p.x * lr + p.y * li;
+    }
+    const double E = bsum(e, sh);
+    if (threadIdx.x == 0) a.energy[i] = E;
+    __syncthreads();
+    if (GRAD) {
+      for (int gi = a.n_gates - 1; gi >= 0; --gi) {
+        const BGate g = a.gates[gi];
+        V Md[16];
+        if (g.kind == kGateChannel) {
+          const BChannel& C = a.ch[g.param];
+          const int c = s_choice[g.param];
+          for (int r = 0; r < 2; ++r)
+            for (int k = 0; k < 2; ++k)
+              Md[r * 2 + k] = bmk<V, T>((T)C.K[c][2 * (k * 2 + r)], (T)-C.K[c][2 * (k * 2 + r) + 1]);
+          BGate h{};
+          h.kind = kGateChannel;
+          h.nt = 1;
+          h.t0 = (uint8_t)C.qubit;
+          bapply<T, true, false>(psi, lam, n, h, Md, A);
+          __syncthreads();
+          continue;
+        }
+        const double th = g.param < 0 ? g.constant : g.constant + g.coef * a.params[g.param];
+        bgate_matrix<V, T>(g.kind, (T)th, M);
+        const int d = g.nt == 2 ? 4 : 2;
+        for (int r = 0; r < d; ++r)
+          for (int c2 = 0; c2 < d; ++c2) Md[r * d + c2] = bmk<V, T>(M[c2 * d + r].x, -M[c2 * d + r].y);
+        if (g.param >= 0) {
+          bgate_generator<V, T>(g.kind, A);
+          const T part = bapply<T, true, true>(psi, lam, n, g, Md, A);
+          const double gsum = bsum(part, sh);
+          if (threadIdx.x == 0) grad[g.param] += g.coef * gsum;
+        } else {
+          bapply<T, true, false>(psi, lam, n, g, Md, A);
+        }
+        __syncthreads();
+      }
+    }
+    if (a.choice)
+      for (int s2 = threadIdx.x; s2 < a.n_sites; s2 += blockDim.x) a.choice[(size_t)i * a.n_sites + s2] = s_choice[s2];
+    if (a.state_out && i == 0) {
+      V* out = reinterpret_cast<V*>(a.state_out);
+      for (uint64_t x = threadIdx.x; x < N; x += blockDim.x) out[x] = psi[x];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void row_mean_kernel(const double* __restrict__ rows, int n_rows, int n_cols, double* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cols) return;
+  double s = 0.0;
+  for (int r = 0; r < n_rows; ++r) s += rows[(size_t)r * n_cols + c];
+  out[c] = s / (double)n_rows;
+}
+
 // Coefficient tables of the instances that run on fused tile passes, formed on
 // the device from the device parameters (the same layout the host fills for a
 // single circuit: diagonal gates store their diagonal, RX stores (cos, sin) of
@@ -421,6 +603,53 @@ qs_status launch_batch_coef(qs_dtype dt, const BCoefGate* g, int n, const double
     batch_coef_kernel<float2><<<blocks, threads, 0, st>>>(g, n, params);
   else
     batch_coef_kernel<double2><<<blocks, threads, 0, st>>>(g, n, params);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+namespace {
+const void* traj_fn(qs_dtype dt, bool grad) {
+  if (dt == QS_C64) return grad ? (const void*)traj_kernel<float, true> : (const void*)traj_kernel<float, false>;
+  return grad ? (const void*)traj_kernel<double, true> : (const void*)traj_kernel<double, false>;
+}
+size_t traj_smem(qs_dtype dt, bool grad, int n) { return (grad ? 2 : 1) * ((size_t)1 << n) * (dt == QS_C64 ? 8 : 16); }
+}  // namespace
+
+int traj_grid_size(qs_dtype dt, bool grad, int n) {
+  const size_t smem = traj_smem(dt, grad, n);
+  const void* fn = traj_fn(dt, grad);
+  int occ = 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBatchThreads, smem) != cudaSuccess || occ < 1) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return (sms > 0 ? sms : 1) * occ;
+}
+
+qs_status launch_traj(qs_dtype dt, bool grad, const TrajArgs& a, int grid, cudaStream_t st) {
+  const size_t smem = traj_smem(dt, grad, a.n);
+  if (dt == QS_C64) {
+    if (grad)
+      traj_kernel<float, true><<<grid, kBatchThreads, smem, st>>>(a);
+    else
+      traj_kernel<float, false><<<grid, kBatchThreads, smem, st>>>(a);
+  } else {
+    if (grad)
+      traj_kernel<double, true><<<grid, kBatchThreads, smem, st>>>(a);
+    else
+      traj_kernel<double, false><<<grid, kBatchThreads, smem, st>>>(a);
+  }
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_row_mean(const double* rows, int n_rows, int n_cols, double* out, cudaStream_t st) {
+  if (n_cols <= 0) return QS_OK;
+  row_mean_kernel<<<(n_cols + 127) / 128, 128, 0, st>>>(rows, n_rows, n_cols, out);
   QS_CUDA(cudaGetLastError());
   return QS_OK;
 }

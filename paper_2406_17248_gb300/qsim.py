@@ -54,6 +54,14 @@ SIGNATURES = [
     ("qs_dm_add_gate", [_VP, _I, _PI, _I, _PI, _I, _I, _D, _D, _PD]),
     ("qs_dm_add_channel", [_VP, _I, _I, _PD, _I, _PD]),
     ("qs_dm_expectation", [_VP, _VP, _PD]),
+    ("qs_traj_create", [_I, _I, _VP, _PVP]),
+    ("qs_traj_destroy", [_VP]),
+    ("qs_traj_add_gate", [_VP, _I, _PI, _I, _PI, _I, _I, _D, _D]),
+    ("qs_traj_add_channel", [_VP, _I, _I, _PD, _I, _PD]),
+    ("qs_traj_info", [_VP, _PI, _PI, _PI, _PI]),
+    ("qs_traj_run", [_VP, _VP, _PD, _I, _U64, C.c_longlong, _I, _PD, _PD, C.POINTER(C.c_ubyte)]),
+    ("qs_traj_run_device", [_VP, _VP, _VP, _U64, C.c_longlong, _I, _VP, _VP]),
+    ("qs_traj_state", [_VP, _PD, _I, _U64, C.c_longlong, _VP]),
     ("qs_apply_matrix", [_VP, _I, _PI, _PD, _I]),
     ("qs_ham_create", [_I, _I, _PU64, _PU64, _PD, _PVP]),
     ("qs_ham_destroy", [_VP]),
@@ -482,6 +490,101 @@ def dm_circuit_from(circ: I.Circuit, channels_after=None) -> DensityCircuit:
         for kind, p, q in ch.get(i, []):
             c.add_channel(kind, q, p)
     return c
+
+
+class Trajectories:
+    """Monte-Carlo trajectories of a noisy circuit (qs_traj_*; §3.3): each
+    trajectory samples one branch per channel site; the mean of the trajectory
+    energies estimates tr(rho H)."""
+
+    def __init__(self, n: int, dtype: int = C64, stream=None):
+        self.n, self.dtype = n, dtype
+        h = C.c_void_p()
+        _check(lib().qs_traj_create(n, dtype, C.c_void_p(_stream_ptr(stream)), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qs_traj_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, kind: str, targets: Sequence[int], ctrls: Sequence[int] = (), param: int = -1,
+            coef: float = 1.0, const: float = 0.0):
+        t = (C.c_int * len(targets))(*targets)
+        cc = (C.c_int * max(len(ctrls), 1))(*ctrls) if ctrls else None
+        _check(lib().qs_traj_add_gate(self.h, KIND[kind], t, len(targets), cc, len(ctrls), param, coef, const))
+        return self
+
+    def add_channel(self, kind: str, qubit: int, p=(), kraus=None):
+        pr = np.ascontiguousarray(p if len(p) else [0.0], dtype=np.float64)
+        kr, nk = None, 0
+        if kraus is not None:
+            ka = np.ascontiguousarray(np.asarray(kraus, dtype=np.complex128)).view(np.float64).reshape(-1)
+            nk = len(kraus)
+            kr = ka.ctypes.data_as(_PD)
+            self._keep_k = ka
+        _check(lib().qs_traj_add_channel(self.h, CHANNELS[kind], qubit, _dptr(pr), nk, kr))
+        return self
+
+    def info(self):
+        a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(lib().qs_traj_info(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+        return {"sites": a.value, "params": b.value, "grid_energy": c.value, "grid_grad": d.value}
+
+    def run(self, ham: Hamiltonian, params, n_traj: int, seed: int, first: int = 0, grad: bool = False,
+            choices: bool = False):
+        """Energies [n_traj] (+ mean gradient [n_params]) (+ branches [n_traj, n_sites])."""
+        pr = np.ascontiguousarray(params, dtype=np.float64)
+        e = np.zeros(n_traj)
+        g = np.zeros(max(pr.size, 1)) if grad else None
+        ns = self.info()["sites"]
+        ch = np.zeros((n_traj, max(ns, 1)), dtype=np.uint8) if choices else None
+        _check(lib().qs_traj_run(self.h, ham.h, _dptr(pr) if pr.size else None, int(pr.size), seed, first, n_traj,
+                                 _dptr(e), _dptr(g) if grad else None,
+                                 ch.ctypes.data_as(C.POINTER(C.c_ubyte)) if choices else None))
+        out = [e]
+        if grad:
+            out.append(g[: pr.size])
+        if choices:
+            out.append(ch[:, :ns])
+        return out[0] if len(out) == 1 else tuple(out)
+
+    def run_device(self, ham: Hamiltonian, params, n_traj: int, seed: int, energies, grad_mean=None, first: int = 0):
+        """Device (torch float64 CUDA tensors) variant: no copies, no synchronisation."""
+        _check(lib().qs_traj_run_device(self.h, ham.h, C.c_void_p(params.data_ptr()) if params.numel() else None,
+                                        seed, first, n_traj, C.c_void_p(energies.data_ptr()),
+                                        C.c_void_p(grad_mean.data_ptr()) if grad_mean is not None else None))
+
+    def state(self, params, seed: int, traj: int, out: "State") -> "State":
+        pr = np.ascontiguousarray(params, dtype=np.float64)
+        _check(lib().qs_traj_state(self.h, _dptr(pr) if pr.size else None, int(pr.size), seed, traj, out.h))
+        return out
+
+
+def trajectories_from(circ: I.Circuit, channels_after=None, dtype: int = C64, stream=None) -> Trajectories:
+    """Trajectory engine of an inputs.Circuit; channels_after[i] = [(kind, p, qubit)
+    or ("kraus", (), qubit, matrices)] added after gate i (key -1: first)."""
+    ch = channels_after or {}
+    t = Trajectories(circ.n_qubits, dtype, stream)
+
+    def site(c):
+        t.add_channel(c[0], c[2], c[1], c[3] if len(c) > 3 else None)
+
+    for c in ch.get(-1, []):
+        site(c)
+    for i, g in enumerate(circ.gates):
+        if g.kind == "MATRIX":
+            raise ValueError("MATRIX gates are not supported in trajectories")
+        t.add(g.kind, g.targets, g.ctrls, g.param, g.coef, g.const)
+        for c in ch.get(i, []):
+            site(c)
+    return t
 
 
 def dm_expectation(rho: State, ham: Hamiltonian) -> float:

@@ -1,0 +1,177 @@
+"""GPU parity of Monte-Carlo trajectory noise (§3.3) against the FP64 oracle:
+the branch taken at every channel site (bit-exact wherever the oracle's decision
+is further than the state's rounding from a branch boundary; always for Pauli
+and depolarizing channels, whose weights are constants), the final state of
+each trajectory, the trajectory energies, the mean adjoint gradient of
+Pauli-channel trajectories, convergence of the mean to tr(rho H), 64-bit
+trajectory counters, and the size limits.
+
+Tolerances: amplitudes and energies 5e-5 (complex64) / 1e-11 (complex128)
+times max(1, sum |c_k|) for energies, as in the other parity tests."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dm_oracle as D
+from oracle import qsim_oracle as O
+from oracle import traj_oracle as T
+from paper_2406_17248_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+TOL = {0: 5e-5, 1: 1e-11}
+MARGIN = {0: 1e-5, 1: 1e-12}
+
+
+@pytest.fixture(scope="module")
+def Q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_17248_gb300 import build
+    build.build()
+    from paper_2406_17248_gb300 import qsim
+    return qsim
+
+
+def _kraus3(seed):
+    rng = np.random.default_rng(seed)
+    a = rng.normal(size=(6, 2)) + 1j * rng.normal(size=(6, 2))
+    q, _ = np.linalg.qr(a)
+    return [q[2 * i:2 * i + 2, :] for i in range(3)]
+
+
+def _mixed_noise(n, layers, seed):
+    circ = I.hea_circuit(n, layers)
+    params = I.uniform_params(circ.n_params, seed)
+    kinds = [("depolarizing", (0.2,)), ("amplitude_damping", (0.3,)), ("pauli", (0.1, 0.15, 0.05)),
+             ("phase_damping", (0.4,))]
+    ch = {-1: [("amplitude_damping", (0.5,), 0)]}
+    for i in range(0, len(circ.gates), 2):
+        k, p = kinds[(i // 2) % 4]
+        ch[i] = [(k, p, (i // 2) % n)]
+    ch[len(circ.gates) - 1] = ch.get(len(circ.gates) - 1, []) + [("kraus", (), n - 1, _kraus3(seed))]
+    return circ, params, ch
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_states_and_branches_match_oracle(Q, dt):
+    n = 5
+    circ, params, ch = _mixed_noise(n, 2, 3)
+    eng = Q.trajectories_from(circ, ch, dt)
+    seed = 2024
+    ham = I.chain_zz_x(n, 0.5)
+    e, branches = eng.run(Q.Hamiltonian(ham), params, 48, seed, choices=True)
+    checked = 0
+    for t in range(48):
+        psi, choices, margins = T.trajectory(circ, params, ch, seed, t)
+        if min(margins) < MARGIN[dt]:
+            continue
+        checked += 1
+        assert list(branches[t]) == choices, t
+        s = Q.State(n, dt)
+        eng.state(params, seed, t, s)
+        assert np.abs(s.get_qs().astype(np.complex128) - psi).max() < TOL[dt], t
+        assert abs(e[t] - O.expectation(psi, ham)) < TOL[dt] * float(np.abs(ham.coef).sum()), t
+    assert checked >= 40
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_pauli_channel_gradients_match_oracle(Q, dt):
+    n = 6
+    circ = I.hea_circuit(n, 2)
+    params = I.uniform_params(circ.n_params, 11)
+    ham = I.chain_zz_x(n, 0.7)
+    ch = {i: [("depolarizing", (0.1,), i % n), ("pauli", (0.05, 0.02, 0.08), (i + 3) % n)]
+          for i in range(0, len(circ.gates), 3)}
+    eng = Q.trajectories_from(circ, ch, dt)
+    n_t, seed, first = 96, 77, 5
+    e, g, branches = eng.run(Q.Hamiltonian(ham), params, n_t, seed, first=first, grad=True, choices=True)
+    es, gs = [], []
+    for i in range(n_t):
+        eo, go, co, _ = T.trajectory_energy_and_grad(circ, ham, params, ch, seed, first + i)
+        assert list(branches[i]) == co, i  # constant weights: the same decision on both sides
+        es.append(eo)
+        gs.append(go)
+    tol = TOL[dt] * max(1.0, float(np.abs(ham.coef).sum()))
+    assert np.abs(e - np.array(es)).max() < tol
+    assert np.abs(g - np.mean(gs, axis=0)).max() < tol
+
+
+def test_gradients_refused_with_damping(Q):
+    circ = I.hea_circuit(3, 1)
+    eng = Q.trajectories_from(circ, {0: [("amplitude_damping", (0.1,), 0)]}, 0)
+    with pytest.raises(Q.QSimError, match="gradients need"):
+        eng.run(Q.Hamiltonian(I.chain_zz_x(3)), np.zeros(circ.n_params), 4, 1, grad=True)
+
+
+def test_mean_converges_to_density_matrix(Q):
+    n = 6
+    circ = I.hea_circuit(n, 2)
+    params = I.uniform_params(circ.n_params, 9)
+    ham = I.chain_zz_x(n, 0.5)
+    ch = {i: [("depolarizing", (0.05,), i % n), ("amplitude_damping", (0.1,), (i + 2) % n)]
+          for i in range(0, len(circ.gates), 3)}
+    exact = D.expectation(D.run(circ, params, ch, n), ham)
+    eng = Q.trajectories_from(circ, ch, 0)
+    e = eng.run(Q.Hamiltonian(ham), params, 20000, seed=31)
+    assert abs(e.mean() - exact) < 5 * e.std() / math.sqrt(e.size)
+    # and the GPU density-matrix simulator agrees with the exact value
+    dmc = Q.dm_circuit_from(circ, ch).finalize(1)
+    rho = Q.State(2 * n, 1)
+    rho.set_basis(0)
+    dmc.apply(rho, params)
+    assert Q.dm_expectation(rho, Q.Hamiltonian(ham)) == pytest.approx(exact, abs=1e-10)
+
+
+def test_zero_noise_is_the_noiseless_state(Q):
+    n = 7
+    circ = I.hea_circuit(n, 3)
+    params = I.uniform_params(circ.n_params, 4)
+    ch = {i: [("depolarizing", (0.0,), i % n), ("amplitude_damping", (0.0,), (i + 1) % n)]
+          for i in range(0, len(circ.gates), 5)}
+    eng = Q.trajectories_from(circ, ch, 1)
+    s = Q.State(n, 1)
+    eng.state(params, 5, 123, s)
+    np.testing.assert_allclose(s.get_qs(), O.evolve(circ, params, O.zero_state(n)), atol=1e-12)
+
+
+def test_64_bit_trajectory_counters(Q):
+    n = 4
+    circ = I.hea_circuit(n, 1)
+    params = I.uniform_params(circ.n_params, 2)
+    ch = {i: [("pauli", (0.2, 0.2, 0.2), i % n)] for i in range(len(circ.gates))}
+    eng = Q.trajectories_from(circ, ch, 1)
+    first = (1 << 40) + 17
+    _, branches = eng.run(Q.Hamiltonian(I.chain_zz_x(n)), params, 16, seed=(1 << 63) + 5, first=first, choices=True)
+    for i in range(16):
+        assert list(branches[i]) == T.trajectory(circ, params, ch, (1 << 63) + 5, first + i)[1]
+
+
+@pytest.mark.parametrize("dt,n,grad", [(0, 14, False), (0, 13, True), (1, 13, False), (1, 12, True)])
+def test_largest_shared_memory_trajectories(Q, dt, n, grad):
+    circ = I.hea_circuit(n, 1)
+    params = I.uniform_params(circ.n_params, 6)
+    ham = I.chain_zz_x(n, 0.5)
+    ch = {i: [("depolarizing", (0.1,), i % n)] for i in range(0, len(circ.gates), 4)}
+    eng = Q.trajectories_from(circ, ch, dt)
+    info = eng.info()
+    assert (info["grid_grad"] if grad else info["grid_energy"]) > 0
+    out = eng.run(Q.Hamiltonian(ham), params, 3, seed=8, grad=grad)
+    e = out[0] if grad else out
+    tol = TOL[dt] * max(1.0, float(np.abs(ham.coef).sum()))
+    gs = []
+    for t in range(3):
+        eo, go, _, _ = T.trajectory_energy_and_grad(circ, ham, params, ch, 8, t)
+        assert abs(e[t] - eo) < tol
+        gs.append(go)
+    if grad:
+        assert np.abs(out[1] - np.mean(gs, axis=0)).max() < tol
+
+
+def test_too_large_for_shared_memory_is_refused(Q):
+    circ = I.hea_circuit(14, 1)
+    eng = Q.trajectories_from(circ, {0: [("depolarizing", (0.1,), 0)]}, 1)
+    assert eng.info()["grid_energy"] == 0
+    with pytest.raises(Q.QSimError, match="too many qubits"):
+        eng.run(Q.Hamiltonian(I.chain_zz_x(14)), np.zeros(circ.n_params), 2, 1)

@@ -550,3 +550,50 @@ def ising_chain_min_energy_brute_force(n: int, J: float, h: float) -> float:
         e = -J * sum(z[i] * z[i + 1] for i in range(n - 1)) - h * sum(z)
         best = min(best, e)
     return best
+
+
+# --------------------------------------------------------------------------- generalised expectation (§2.6.2, §4.1)
+
+def general_expectation(circ_r: Circuit, circ_l: Circuit, ham: PauliSum, params, psi0, phi0) -> complex:
+    """E = <phi|U_l^dag H U_r|psi> (the generalised observable of §2.6.2 and §4.1):
+    U_r applied to psi0, U_l to phi0, both with the same parameter vector."""
+    r = evolve(circ_r, params, psi0)
+    l = evolve(circ_l, params, phi0)
+    return inner_product(l, apply_hamiltonian(r, ham))
+
+
+def _derivative_states(circ: Circuit, params, psi0):
+    """For every parametric gate k: (param, coef, U_N..U_{k+1} (P_ctrl (x) dU_k) U_{k-1}..U_1 psi0)."""
+    n = circ.n_qubits
+    out = []
+    for k, g in enumerate(circ.gates):
+        if g.param < 0:
+            continue
+        psi = psi0.astype(C128, copy=True)
+        for j, h in enumerate(circ.gates):
+            if j == k:
+                dU = gate_matrix_derivative(h.kind, h.angle(params))
+                psi = apply_on_control_subspace_only(psi, n, dU, h.targets, h.ctrls)
+            else:
+                psi = apply_gate(psi, n, gate_unitary(h, params), h.targets, h.ctrls)
+        out.append((g.param, g.coef, psi))
+    return out
+
+
+def general_expectation_grad(circ_r: Circuit, circ_l: Circuit, ham: PauliSum, params, psi0, phi0):
+    """E and dE/dparams (complex) by the product rule, one derivative circuit per
+    parametric gate occurrence (no adjoint sweep):
+      dE/dp = sum_{k in U_r, param p} coef_k <phi_l| H |d_k psi>
+            + sum_{k in U_l, param p} coef_k <d_k phi| H |psi_r>,
+    with d_k the circuit whose gate k is replaced by its derivative."""
+    n_params = max(circ_r.n_params, circ_l.n_params)
+    r = evolve(circ_r, params, psi0)
+    l = evolve(circ_l, params, phi0)
+    Hl = apply_hamiltonian(l, ham)
+    Hr = apply_hamiltonian(r, ham)
+    grad = np.zeros(n_params, dtype=C128)
+    for p, coef, d in _derivative_states(circ_r, params, psi0):
+        grad[p] += coef * np.vdot(Hl, d)
+    for p, coef, d in _derivative_states(circ_l, params, phi0):
+        grad[p] += coef * np.vdot(d, Hr)
+    return inner_product(l, Hr), grad

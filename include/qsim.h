@@ -206,6 +206,22 @@ QS_API qs_status qs_expectation_with_grad_multi(qs_state* psi, qs_state* lam, qs
                                                 const qs_ham* const* hams, const double* params, int n_params,
                                                 double* energies, double* grads);
 
+/* Generalised expectation (§2.6.2 and §4.1: E = <phi|U_l^dag H U_r|psi>, which
+ * gives the physical expectation for phi = psi, U_l = U_r, inner products for
+ * H = I, and projections for H a projector) and its gradient with respect to
+ * every parameter, complex in general:
+ *   dE/dp = sum_{k in U_r} coef_k <phi_l|H|..dU_k..psi> + sum_{k in U_l} coef_k <..dU_k..phi|H|psi_r>,
+ * both circuits reading the same parameter vector.  Each circuit runs forward
+ * once and backward twice (adjoint sweeps with lam and with i lam give the real
+ * and imaginary parts).  psi, phi: the right and left input states (restored on
+ * return up to rounding); lam: a third state used as the adjoint buffer (all
+ * three of one n and dtype, distinct).  c_left NULL: U_l = U_r.  energy2: host
+ * double[2] (re, im); grad2: host double[2 * n_params] (re, im interleaved).
+ * Synchronises psi's stream. */
+QS_API qs_status qs_expectation_general(qs_state* psi, qs_state* phi, qs_state* lam, qs_circuit* c_right,
+                                        qs_circuit* c_left, const qs_ham* h, const double* params, int n_params,
+                                        double* energy2, double* grad2);
+
 /* Projective measurement of one qubit in the computational basis, mid-circuit
  * (the measurement gate, §2.3; outcomes as in sampling, §2.6.3): with
  * P(1) = sum of |psi_x|^2 over x with bit `qubit` set and P(0) = total - P(1),

@@ -1016,6 +1016,109 @@ qs_status qs_expectation_with_grad_multi(qs_state* psi, qs_state* lam, qs_circui
   return QS_OK;
 }
 
+qs_status qs_expectation_general(qs_state* psi, qs_state* phi, qs_state* lam, qs_circuit* c_right,
+                                 qs_circuit* c_left, const qs_ham* h, const double* params, int n_params,
+                                 double* energy2, double* grad2) {
+  QS_TRY(check_state(psi));
+  QS_TRY(check_state(phi));
+  QS_TRY(check_state(lam));
+  QS_CHECK(c_right != nullptr && h != nullptr && energy2 != nullptr, "null argument");
+  qs_circuit* cr = c_right;
+  qs_circuit* cl = c_left ? c_left : c_right;
+  QS_CHECK(psi->ptr != phi->ptr && psi->ptr != lam->ptr && phi->ptr != lam->ptr, "psi, phi and lam must differ");
+  QS_CHECK(psi->n == phi->n && psi->n == lam->n && psi->dt == phi->dt && psi->dt == lam->dt,
+           "psi/phi/lam n or dtype mismatch");
+  QS_CHECK(cr->n == psi->n && cl->n == psi->n && h->n == psi->n, "circuit/hamiltonian/state qubit counts differ");
+  QS_CHECK(cr->dm_n == 0 && cl->dm_n == 0, "density-matrix circuits have no generalised expectation");
+  const int np = std::max(cr->n_params, cl->n_params);
+  QS_CHECK(n_params >= np, "too few parameters");
+  QS_CHECK(np == 0 || (params != nullptr && grad2 != nullptr), "params/grad is null");
+  cudaStream_t st = psi->st;
+  if (phi->st != st) QS_CUDA(cudaStreamSynchronize(phi->st));
+  if (lam->st != st) QS_CUDA(cudaStreamSynchronize(lam->st));
+  QS_TRY(ensure_plan(cr, psi->dt, st));
+  QS_TRY(ensure_plan(cl, psi->dt, st));
+  QS_CHECK(cr->plan.fuse >= 0 && cl->plan.fuse >= 0,
+           "the adjoint gradient runs on fused tile passes (fuse = -1 is forward only)");
+  const int ne = psi->ne;
+  const size_t bytes = amp_bytes(psi->dt) << ne;
+  if (!psi->save) QS_CUDA(cudaMalloc(&psi->save, bytes));
+  if (!phi->save) QS_CUDA(cudaMalloc(&phi->save, bytes));
+  const int hgrid = ham_grid_size(ne);
+  const int igrid = hgrid;
+  const int slots = std::max<int>({(int)cr->plan.rev_slots.out.size(), (int)cl->plan.rev_slots.out.size(), 1});
+  const size_t part = (size_t)slots * std::max(cr->plan.grid2, cl->plan.grid2);
+  const int npp = std::max(np, 1);
+  const size_t need = part + slots + 2 + 4 * (size_t)npp + hgrid + 2 * (size_t)igrid + 16;
+  QS_TRY(ensure_scratch(psi, need));
+  double* d_part = psi->scratch;
+  double* d_slot = d_part + part;
+  double* d_E = d_slot + slots;
+  double* d_g = d_E + 2;  // [4][npp]: right Re, right Im, left Re, left Im (each 2 Re <.|A|.> sums)
+  double* d_hpart = d_g + 4 * (size_t)npp;
+  double* d_ipart = d_hpart + hgrid;
+  QS_CUDA(cudaMemsetAsync(d_g, 0, 4 * (size_t)npp * sizeof(double), st));
+  const int t0 = 0;
+  const double times_i[4] = {0.0, 1.0, 0.0, 1.0};
+  // coefficient tables (one fill when both sides are the same circuit)
+  QS_TRY(fill_circuit_coef(cr, params));
+  QS_TRY(upload_table(cr->host_coef, psi->dt, cr->plan.d_coef, st, psi->host_out));
+  if (cl != cr) {
+    QS_TRY(fill_circuit_coef(cl, params));
+    QS_TRY(upload_table(cl->host_coef, psi->dt, cl->plan.d_coef, st, psi->host_out));
+  }
+  const CircuitPlan& R = cr->plan;
+  const CircuitPlan& L = cl->plan;
+  // forward: psi_r = U_r psi, phi_l = U_l phi
+  QS_TRY(run_passes(R.fwd, 0, (int)R.fwd.passes.size(), psi->dt, psi->ptr, nullptr, R.d_coef, nullptr, d_part, ne, 0,
+                    R.grid1, R.grid2, st));
+  QS_TRY(run_passes(L.fwd, 0, (int)L.fwd.passes.size(), psi->dt, phi->ptr, nullptr, L.d_coef, nullptr, d_part, ne, 0,
+                    L.grid1, L.grid2, st));
+  QS_CUDA(cudaMemcpyAsync(psi->save, psi->ptr, bytes, cudaMemcpyDeviceToDevice, st));
+  QS_CUDA(cudaMemcpyAsync(phi->save, phi->ptr, bytes, cudaMemcpyDeviceToDevice, st));
+  // E = <H phi_l | psi_r>
+  QS_TRY(launch_ham_apply(psi->dt, phi->ptr, lam->ptr, ne, h->d_groups, h->n_groups, h->d_terms, d_hpart, hgrid, st));
+  QS_TRY(launch_inner(psi->dt, lam->ptr, psi->ptr, ne, d_ipart, igrid, st));
+  QS_TRY(launch_reduce_slots(d_ipart, 2, igrid, nullptr, d_E, st));
+  // Each side sweeps twice: with lam and with i lam, giving 2 Re and 2 Im of
+  // sum_k coef_k <lam_k|A_k|x_k>.  Right: x = psi, lam = H phi_l.  Left:
+  // x = phi, lam = H psi_r (its terms enter conjugated).
+  for (int side = 0; side < 2; ++side) {
+    qs_circuit* c = side == 0 ? cr : cl;
+    const CircuitPlan& P = c->plan;
+    qs_state* x = side == 0 ? psi : phi;
+    const void* other = side == 0 ? phi->save : psi->save;
+    // without parameters one sweep still brings x back to its input state
+    const int sweeps = c->n_params > 0 ? 2 : 1;
+    for (int im = 0; im < sweeps; ++im) {
+      if (im == 1) QS_CUDA(cudaMemcpyAsync(x->ptr, x->save, bytes, cudaMemcpyDeviceToDevice, st));
+      QS_TRY(launch_ham_apply(psi->dt, other, lam->ptr, ne, h->d_groups, h->n_groups, h->d_terms, d_hpart, hgrid, st));
+      if (im == 1) QS_TRY(launch_gate_diag(psi->dt, lam->ptr, ne, 1, &t0, 0, times_i, st));
+      QS_TRY(run_passes(P.rev, 0, (int)P.rev.passes.size(), psi->dt, x->ptr, lam->ptr, P.d_coef, nullptr, d_part, ne,
+                        0, P.grid1, P.grid2, st));
+      const int ns = (int)P.rev_slots.out.size();
+      if (c->n_params == 0 || ns == 0) continue;
+      QS_TRY(launch_reduce_slots(d_part, ns, P.grid2, nullptr, d_slot, st));
+      QS_TRY(launch_param_gather(d_slot, P.d_row, P.d_sidx, P.d_w, c->n_params, d_g + (size_t)(2 * side + im) * npp,
+                                 st));
+    }
+  }
+  double E[2];
+  std::vector<double> g(4 * (size_t)npp);
+  QS_CUDA(cudaMemcpyAsync(E, d_E, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  QS_CUDA(cudaMemcpyAsync(g.data(), d_g, g.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  QS_CUDA(cudaStreamSynchronize(st));
+  energy2[0] = E[0];
+  energy2[1] = E[1];
+  if (grad2)
+    for (int p = 0; p < n_params; ++p) {
+      const bool in = p < np;
+      grad2[2 * p] = in ? 0.5 * (g[p] + g[2 * (size_t)npp + p]) : 0.0;
+      grad2[2 * p + 1] = in ? 0.5 * (g[(size_t)npp + p] - g[3 * (size_t)npp + p]) : 0.0;
+    }
+  return QS_OK;
+}
+
 qs_status qs_measure(qs_state* s, int qubit, uint64_t seed, int* outcome) {
   QS_TRY(check_state(s));
   QS_CHECK(qubit >= 0 && qubit < s->n, "qubit out of range");

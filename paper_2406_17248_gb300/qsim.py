@@ -71,6 +71,7 @@ SIGNATURES = [
     ("qs_expectation_with_grad", [_VP, _VP, _VP, _VP, _PD, _I, _PD, _PD]),
     ("qs_sample", [_VP, _U64, _U64, _PU64]),
     ("qs_expectation_with_grad_multi", [_VP, _VP, _VP, _I, _VP, _PD, _I, _PD, _PD]),
+    ("qs_expectation_general", [_VP, _VP, _VP, _VP, _VP, _VP, _PD, _I, _PD, _PD]),
     ("qs_measure", [_VP, _I, _U64, _PI]),
     ("qs_qaoa_create", [_I, _PI, _I, _I, _D, _I, _VP, _PVP]),
     ("qs_qaoa_destroy", [_VP]),
@@ -338,6 +339,18 @@ def expectation_with_grad_multi(psi: State, lam: State, circ: Circuit, hams, par
     _check(lib().qs_expectation_with_grad_multi(psi.h, lam.h, circ.h, n_ham, C.cast(arr, C.c_void_p),
                                                 _dptr(pr) if pr.size else None, int(pr.size), _dptr(e), _dptr(g)))
     return e, g[: n_ham * pr.size].reshape(n_ham, pr.size)
+
+
+def expectation_general(psi: State, phi: State, lam: State, c_right: Circuit, c_left: Optional[Circuit],
+                        ham: Hamiltonian, params):
+    """E = <phi|U_l^dag H U_r|psi> and dE/dparams, both complex (qs_expectation_general);
+    c_left None: U_l = U_r."""
+    pr = np.ascontiguousarray(params, dtype=np.float64)
+    e = np.zeros(2)
+    g = np.zeros(2 * max(pr.size, 1))
+    _check(lib().qs_expectation_general(psi.h, phi.h, lam.h, c_right.h, c_left.h if c_left is not None else None,
+                                        ham.h, _dptr(pr) if pr.size else None, int(pr.size), _dptr(e), _dptr(g)))
+    return complex(e[0], e[1]), g[: 2 * pr.size].view(np.complex128)
 
 
 def measure(state: State, qubit: int, seed: int) -> int:

@@ -67,3 +67,32 @@ def dcqaoa_multistart(n: int, p: int, starts: int, seed: int, J: float = 1.0, h:
     circ = I.dcqaoa_circuit(n, p, J, h, k, cd=cd)
     ham = I.lfim(n, J, h, k)
     return [I.Instance(circ, ham, I.uniform_params(circ.n_params, seed + s, lo, hi)) for s in range(starts)]
+
+
+class GradientOperator:
+    """The gradient operator of §4.1 with an encoder batch and a list of
+    Hamiltonians: the circuit's parameters [0, n_encoder) are encoder inputs (one
+    row per batch item) and the rest ansatz parameters shared by the batch.
+    ``op(enc, ans)`` returns f [n_batch, n_ham], grad_enc [n_batch, n_ham,
+    n_encoder] and grad_ans [n_batch, n_ham, n_ansatz] -- every (batch item,
+    Hamiltonian) pair is one instance of a single batched launch (energy and
+    adjoint gradient of each, in shared memory for small circuits)."""
+
+    def __init__(self, circ: I.Circuit, hams: Sequence[I.PauliSum], n_encoder: int, n_batch: int,
+                 dtype: int = Q.C128):
+        if not 0 <= n_encoder <= circ.n_params:
+            raise ValueError("n_encoder must be in [0, n_params]")
+        self.n_enc, self.n_ans = n_encoder, circ.n_params - n_encoder
+        self.n_batch, self.n_ham = n_batch, len(hams)
+        zeros = np.zeros(circ.n_params)
+        self.batch = Q.Batch([I.Instance(circ, h, zeros) for _ in range(n_batch) for h in hams], dtype)
+
+    def __call__(self, enc, ans):
+        enc = np.asarray(enc, dtype=np.float64).reshape(self.n_batch, self.n_enc)
+        ans = np.asarray(ans, dtype=np.float64).reshape(self.n_ans)
+        rows = np.concatenate([enc, np.broadcast_to(ans, (self.n_batch, self.n_ans))], axis=1)
+        params = np.repeat(rows, self.n_ham, axis=0).reshape(-1)
+        e, g = self.batch.expectation_with_grad(params)
+        f = e.reshape(self.n_batch, self.n_ham)
+        g = np.stack(g).reshape(self.n_batch, self.n_ham, self.n_enc + self.n_ans)
+        return f, g[:, :, :self.n_enc], g[:, :, self.n_enc:]

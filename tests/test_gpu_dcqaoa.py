@@ -96,3 +96,28 @@ def test_device_adam_trajectory_matches_oracle(Q):
     # the paper's observation: DC-QAOA reaches the ground energy -23, QAOA does not
     assert hist[-1, :4].max() < -22.9
     assert hist[:, 4:].min() > -12.0
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_encoder_batch_gradient_operator(Q, dt):
+    # §4.1: f [n_batch, n_ham], gradients [n_batch, n_ham, n_encoder] and [n_batch, n_ham, n_ansatz]
+    from paper_2406_17248_gb300 import vqa
+    n, n_enc = 8, 8
+    enc_gates = [I.Gate("RY", (q,), param=q) for q in range(n)]
+    ans = I.hea_circuit(n, 2)
+    ans_gates = [I.Gate(g.kind, g.targets, g.ctrls, g.param + n_enc if g.param >= 0 else -1, g.coef, g.const)
+                 for g in ans.gates]
+    circ = I.Circuit(n, enc_gates + ans_gates, n_enc + ans.n_params)
+    hams = [I.chain_zz_x(n, 0.5), I.pauli_sum_from_strings(n, [(1.0, "Z0"), (0.5, "X3 Y4")]), I.tfim(n, np.random.default_rng(1))]
+    n_batch = 5
+    op = vqa.GradientOperator(circ, hams, n_enc, n_batch, dt)
+    enc = np.random.default_rng(2).uniform(-np.pi, np.pi, (n_batch, n_enc))
+    a = I.uniform_params(ans.n_params, 3)
+    f, ge, ga = op(enc, a)
+    assert f.shape == (n_batch, 3) and ge.shape == (n_batch, 3, n_enc) and ga.shape == (n_batch, 3, ans.n_params)
+    for b in range(n_batch):
+        for h, ham in enumerate(hams):
+            E0, G0 = O.adjoint_gradient(circ, ham, np.concatenate([enc[b], a]), O.zero_state(n))
+            tol = TOL[dt] * scale(ham)
+            assert abs(f[b, h] - E0) < tol
+            assert np.abs(np.concatenate([ge[b, h], ga[b, h]]) - G0).max() < tol

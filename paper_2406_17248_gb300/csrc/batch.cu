@@ -61,7 +61,7 @@ struct qs_batch {
   double* d_energy = nullptr;
   double* d_grad = nullptr;
   int* d_queue = nullptr;
-  int smem_amps = 0;
+  int smem_amps = 0, smem_gates = 0, smem_params = 0;
   int grid = 0;
 };
 
@@ -165,6 +165,8 @@ static qs_status issue_all(qs_batch* b, cudaStream_t st, const double* dev_param
     a.grad = dev_grads;
     a.queue = b->d_queue;
     a.smem_amps = b->smem_amps;
+    a.smem_gates = b->smem_gates;
+    a.smem_params = b->smem_params;
     TraceRec* rec = trace_begin(st);
     QS_TRY(launch_batch(b->dt, a, b->grid, st));
     if (rec) {
@@ -261,7 +263,8 @@ qs_status qs_batch_create(int n_inst, const int* n_qubits, const int* gate_offse
     I.group_end = (int)groups.size();
     I.param_off = param_offsets[i];
     I.n_params = np;
-    I.in_smem = n <= smem_n ? 1 : 0;
+    const int max_p = dtype == QS_C64 ? kBatchMaxSmemParams : kBatchMaxSmemParams / 2;
+    I.in_smem = (n <= smem_n && I.gate_end - I.gate_begin <= kBatchMaxSmemGates && np <= max_p) ? 1 : 0;
     I.pad = 0;
     I.cost = (double)(3 * (I.gate_end - I.gate_begin) + 2 * (I.group_end - I.group_begin) + 1) * (double)(1ull << n);
     if (!I.in_smem) big_n = std::max(big_n, n);
@@ -271,7 +274,18 @@ qs_status qs_batch_create(int n_inst, const int* n_qubits, const int* gate_offse
   b->st = (cudaStream_t)cuda_stream;
   b->n_inst = n_inst;
   b->n_params_total = param_offsets[n_inst];
-  b->smem_amps = 1 << smem_n;
+  // shared memory sized for the largest shared-memory instance (more CTAs per SM
+  // when all are small)
+  int sm_n = 1, sm_g = 1, sm_p = 1;
+  for (int i = 0; i < n_inst; ++i)
+    if (inst[i].in_smem) {
+      sm_n = std::max(sm_n, inst[i].n);
+      sm_g = std::max(sm_g, inst[i].gate_end - inst[i].gate_begin);
+      sm_p = std::max(sm_p, inst[i].n_params);
+    }
+  b->smem_amps = 1 << sm_n;
+  b->smem_gates = sm_g;
+  b->smem_params = sm_p;
   // the persistent kernel's queue holds the shared-memory instances, largest first
   std::vector<int> order;
   for (int i = 0; i < n_inst; ++i)
@@ -279,7 +293,7 @@ qs_status qs_batch_create(int n_inst, const int* n_qubits, const int* gate_offse
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return inst[a].cost > inst[c].cost; });
   b->n_small = (int)order.size();
   qs_status s = QS_OK;
-  b->grid = batch_grid_size(dtype, b->smem_amps);
+  b->grid = batch_grid_size(dtype, b->smem_amps, b->smem_gates, b->smem_params);
   if (b->grid < 1) {
     free_batch(b);
     set_error("batch: the shared-memory states do not fit");

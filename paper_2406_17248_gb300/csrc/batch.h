@@ -6,6 +6,13 @@
 
 namespace qs {
 
+constexpr int kBatchThreads = 256;
+// dynamic shared memory one CTA of the batched or trajectory kernels may use
+constexpr size_t kBatchSmemBudget = 220 * 1024;
+// instances with more gates or parameters than these run on fused tile passes
+constexpr int kBatchMaxSmemGates = 1024;
+constexpr int kBatchMaxSmemParams = 512;
+
 // One gate of a batched circuit (device layout, 32 bytes).
 struct BGate {
   uint8_t kind;   // qs_gate_kind (MATRIX is not supported in batches)
@@ -38,6 +45,8 @@ struct BatchArgs {
   double* grad;            // concatenated, like params
   int* queue;              // work counter (zeroed before the launch)
   int smem_amps;           // amplitudes per state in shared memory
+  int smem_gates;          // gate-data entries in shared memory (the most gates of an instance)
+  int smem_params;         // gradient slots in shared memory (the most parameters of an instance)
 };
 
 qs_status launch_batch(qs_dtype dt, const BatchArgs& a, int grid, cudaStream_t st);
@@ -64,7 +73,7 @@ struct BCoefRun {
 };
 qs_status launch_batch_runs(qs_dtype dt, const BCoefRun* runs, int n, const BCoefGate* members,
                             const double* params, cudaStream_t st);
-int batch_grid_size(qs_dtype dt, int smem_amps);
+int batch_grid_size(qs_dtype dt, int smem_amps, int smem_gates, int smem_params);
 
 // Monte-Carlo trajectories of one noisy circuit (the state-vector treatment of
 // channels, §3.3): each trajectory samples one branch operator per channel site
@@ -98,10 +107,10 @@ struct TrajArgs {
   int n_traj, n, n_gates, n_sites, n_params, n_groups;
 };
 qs_status launch_traj(qs_dtype dt, bool grad, const TrajArgs& a, int grid, cudaStream_t st);
-int traj_grid_size(qs_dtype dt, bool grad, int n);
+int traj_grid_size(qs_dtype dt, bool grad, int n, int n_gates, int n_params);
+size_t traj_smem_bytes(qs_dtype dt, bool grad, int n, int n_gates, int n_params);
 // out[c] = (sum over r of rows[r * n_cols + c]) / n_rows, rows summed in order.
 qs_status launch_row_mean(const double* rows, int n_rows, int n_cols, double* out, cudaStream_t st);
-size_t batch_smem_bytes(qs_dtype dt, int smem_amps);
-constexpr int kBatchThreads = 512;
+size_t batch_smem_bytes(qs_dtype dt, int smem_amps, int smem_gates, int smem_params);
 
 }  // namespace qs

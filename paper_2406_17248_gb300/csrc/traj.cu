@@ -72,9 +72,9 @@ void set_op(BChannel& C, int k, double a_re, double a_im, double b_re, double b_
 qs_status run(qs_traj* t, const qs_ham* h, const double* d_params, uint64_t seed, long long first, int n_traj,
               double* d_energy, bool grad, double* d_gmean, uint8_t* d_choice, void* state_out) {
   QS_TRY(upload(t));
-  int grid = traj_grid_size(t->dt, grad, t->n);
-  QS_CHECK(grid > 0, grad ? "too many qubits for shared-memory trajectories with gradients"
-                          : "too many qubits for shared-memory trajectories");
+  int grid = traj_grid_size(t->dt, grad, t->n, (int)t->gates.size(), t->n_params);
+  QS_CHECK(grid > 0, grad ? "too many qubits, gates or parameters for shared-memory trajectories with gradients"
+                          : "too many qubits or gates for shared-memory trajectories");
   grid = std::min(grid, n_traj);
   if (grad) QS_TRY(ensure(&t->d_grad, &t->cap_grad, (size_t)n_traj * std::max(t->n_params, 1)));
   QS_CUDA(cudaMemsetAsync(t->d_queue, 0, sizeof(int), t->st));
@@ -258,8 +258,8 @@ qs_status qs_traj_info(const qs_traj* t, int* n_sites, int* n_params, int* grid_
   QS_CHECK(t != nullptr, "null trajectory engine");
   if (n_sites) *n_sites = (int)t->ch.size();
   if (n_params) *n_params = t->n_params;
-  if (grid_energy) *grid_energy = traj_grid_size(t->dt, false, t->n);
-  if (grid_grad) *grid_grad = traj_grid_size(t->dt, true, t->n);
+  if (grid_energy) *grid_energy = traj_grid_size(t->dt, false, t->n, (int)t->gates.size(), t->n_params);
+  if (grid_grad) *grid_grad = traj_grid_size(t->dt, true, t->n, (int)t->gates.size(), t->n_params);
   return QS_OK;
 }
 

@@ -330,8 +330,14 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
     it.touched = it.ctrl | (1ull << g.t[0]) | (g.nt == 2 ? (1ull << g.t[1]) : 0);
     const int cls = P.gclass[i];
     it.kind = cls == GC_DENSE1 ? IK_DENSE1 : cls == GC_DENSE2 ? IK_DENSE2 : IK_DIAG;
-    const bool rx = g.kind == QS_GATE_RX;
-    const uint8_t apply_type = cls == GC_DENSE1 ? (rx ? OP_RX : OP_DENSE1) : cls == GC_DENSE2 ? OP_DENSE2 : OP_DIAG;
+    // X gates (CNOT, Toffoli) swap amplitudes in complex128 forward passes (FP64
+    // bound there: 397 -> 467 gates/s on the random 28-qubit circuit); complex64
+    // keeps them as 2x2 matrices (the extra op cost the issue-bound complex64
+    // interpreter more than it saved: 5541 -> 4625), and so does the two-state
+    // reverse kernel (its registers are at the limit)
+    const bool rx = g.kind == QS_GATE_RX, x = g.kind == QS_GATE_X && !reverse && dt == QS_C128;
+    const uint8_t apply_type =
+        cls == GC_DENSE1 ? (rx ? OP_RX : x ? OP_X : OP_DENSE1) : cls == GC_DENSE2 ? OP_DENSE2 : OP_DIAG;
     if (!reverse) {
       it.ops.push_back(ItemOp{apply_type, 0, P.off_u[i], -1, 0.0});
     } else {

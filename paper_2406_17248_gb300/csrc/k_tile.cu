@@ -143,6 +143,20 @@ __device__ __forceinline__ void op_rx(V (&a)[RN], V cs, uint32_t jc, bool ok) {
   }
 }
 
+template <class V, int RB, bool JC>
+__device__ __forceinline__ void op_x(V (&a)[RN], uint32_t jc, bool ok) {
+#pragma unroll
+  for (int j = 0; j < RN; ++j) {
+    if (j & (1 << RB)) continue;
+    const int j1 = j | (1 << RB);
+    if (ok && (!JC || ((uint32_t)j & jc) == jc)) {
+      const V x0 = a[j];
+      a[j] = a[j1];
+      a[j1] = x0;
+    }
+  }
+}
+
 template <class V, int RB0, int RB1, bool JC>
 __device__ __forceinline__ void op_dense2(V (&a)[RN], const V* M, uint32_t jc, bool ok) {
 #pragma unroll
@@ -406,6 +420,14 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? QS_TILE_C64_MIN
               QS_RB_SWITCH(op.rb0, CALL)
 #undef CALL
 #undef CALLJ
+              break;
+            }
+            case OP_X: {  // complex128 forward passes only (where the planner emits it)
+              if constexpr (NS == 1 && sizeof(T) == 8) {
+#define CALL(R) if (jc) { op_x<V, R, true>(a, jc, ok); } else { op_x<V, R, false>(a, jc, ok); }
+                QS_RB_SWITCH(op.rb0, CALL)
+#undef CALL
+              }
               break;
             }
             case OP_RX: {

@@ -958,9 +958,72 @@ def run_traj_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_gates_workload(args):
+    """Single-gate sweep on an n-qubit state (default 30, complex64, from |+>^n):
+    H, RZ(0.3), CNOT (control q + 1) and CZ (control q + 1) on every target q,
+    each gate one launch of the per-gate kernels (`fuse = -1`).  Algorithmic bytes
+    count the amplitudes a gate changes, read and written: H and RZ 2 S, CNOT S,
+    CZ S / 2 (S = the state's bytes).  value = the sweep's bytes / its time."""
+    import numpy as np
+    import torch
+    from paper_2406_17248_gb300 import build, inputs as I
+    build.build()
+    from paper_2406_17248_gb300 import qsim as Q
+    n = args.n
+    dt = Q.C128 if args.gate_dtype == "c128" else Q.C64
+    S = (8 if dt == Q.C64 else 16) * float(1 << n)
+    s = Q.State(n, dt)
+    s.set_plus()
+    kinds = {"H": (lambda q: I.Gate("H", (q,)), 2 * S), "RZ": (lambda q: I.Gate("RZ", (q,), const=0.3), 2 * S),
+             "CNOT": (lambda q: I.Gate("X", (q,), ((q + 1) % n,)), S),
+             "CZ": (lambda q: I.Gate("Z", (q,), ((q + 1) % n,)), S / 2)}
+    circs = {k: [Q.circuit_from(I.Circuit(n, [mk(q)])).finalize(dt, fuse=-1) for q in range(n)]
+             for k, (mk, _) in kinds.items()}
+    st = torch.cuda.current_stream()
+    for k in kinds:
+        for q in range(n):
+            circs[k][q].apply(s, [])
+    torch.cuda.synchronize()
+    peak, peak_kind = measured_peak_hbm()
+    clocks = ClockSampler()
+    clocks.start()
+    per = {}
+    tot_bytes = tot_ms = 0.0
+    reps = max(1, args.steps)
+    for k, (_, by) in kinds.items():
+        ms_q = []
+        for q in range(n):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                circs[k][q].apply(s, [])
+            e1.record(st)
+            e1.synchronize()
+            ms_q.append(e0.elapsed_time(e1) / reps)
+        gbs = [by / (m / 1e3) / 1e9 for m in ms_q]
+        per[k] = {"GBps_median": float(np.median(gbs)), "GBps_min": float(np.min(gbs)),
+                  "frac_median": float(np.median(gbs)) / peak, "frac_min": float(np.min(gbs)) / peak,
+                  "ms_median": float(np.median(ms_q)), "GBps_by_target": [round(g, 1) for g in gbs]}
+        tot_bytes += by * n
+        tot_ms += sum(ms_q)
+    ck = clocks.stop()
+    ach = tot_bytes / (tot_ms / 1e3) / 1e9
+    line = {"metric": f"{n}-qubit {'complex64' if dt == Q.C64 else 'complex128'} single-gate sweep (H, RZ, CNOT, CZ on "
+                      "every qubit), HBM GB/s",
+            "value": ach, "unit": "GB/s", "n_gpus": 1, "steps": reps, "warmup": 1,
+            "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if dt == Q.C64 else "f64", "data": "synthetic",
+            "config": {"workload": f"{n} qubits from |+>^n, 4 x {n} single-gate launches", "l2": "state > L2"},
+            "gates_per_s": 4 * n / (tot_ms / 1e3),
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs"},
+            "per_kind": per, "gpu_launches": 4 * n * reps, "clocks": ck}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="qaoa30", choices=["qaoa30", "batch", "random28", "gnn", "dense28", "hea12", "dm14", "dcqaoa12", "traj12"])
+    ap.add_argument("--workload", default="qaoa30", choices=["qaoa30", "batch", "random28", "gnn", "dense28", "hea12", "dm14", "dcqaoa12", "traj12", "gates"])
     ap.add_argument("--instances", type=int, default=2048)
     ap.add_argument("--plain-instances", type=int, default=2048)
     ap.add_argument("--gpus", type=int, default=1)
@@ -975,6 +1038,7 @@ def main():
     ap.add_argument("--ref-qubits", type=int, default=18)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--block-k", type=int, default=5)
+    ap.add_argument("--gate-dtype", default="c64", choices=["c64", "c128"])
     args = ap.parse_args()
     if args.workload == "batch":
         return run_batch_workload(args)
@@ -984,6 +1048,8 @@ def main():
         return run_dcqaoa_workload(args)
     if args.workload == "traj12":
         return run_traj_workload(args)
+    if args.workload == "gates":
+        return run_gates_workload(args)
     if args.workload == "hea12":
         return run_hea_workload(args)
     if args.workload == "dense28":

@@ -1,5 +1,7 @@
 // Per-gate kernels, state initialisation, Pauli-sum application and
 // expectation, deterministic reductions, MaxCut cut values and sampling.
+#include <algorithm>
+
 #include "qsim_internal.h"
 
 namespace qs {
@@ -104,6 +106,193 @@ __global__ void gate_diag_kernel(typename V2<T>::V* psi, int n, int nt, int t0, 
     if (nt == 2) b |= (int)((x >> t1) & 1) << 1;
     psi[x] = mulc(d[b], psi[x]);
   }
+}
+
+// --------------------------------------------------------------- per-gate at HBM speed
+// A single-qubit dense gate or a diagonal gate on one or two qubits, applied to
+// exactly the amplitudes it changes: work item i enumerates the free bits (every
+// bit but the fixed ones, in increasing order), the fixed bits are deposited
+// (controls and, for diagonal gates whose first entry is 1, the target as 1; the
+// target of a dense gate as 0).  With bit 0 free a complex64 item covers two
+// adjacent amplitudes per 16-byte access; each thread keeps kGateUnroll items in
+// flight, streaming loads and stores (the state is touched once).
+constexpr int kGateUnroll = 4;
+constexpr int kMaxFixed = 8;
+struct FixedBits {
+  int k;
+  int pos[kMaxFixed];  // increasing
+  uint64_t ones;       // fixed bits deposited as 1
+};
+
+__device__ __forceinline__ uint64_t deposit(uint64_t i, const FixedBits& F) {
+#pragma unroll
+  for (int j = 0; j < kMaxFixed; ++j) {  // static indices: F stays in the parameter bank
+    if (j < F.k) {
+      const int q = F.pos[j];
+      i = ((i >> q) << (q + 1)) | (i & ((1ull << q) - 1)) | (F.ones & (1ull << q));
+    }
+  }
+  return i;
+}
+
+__device__ __forceinline__ float4 ldcs4(const float2* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void stcs4(float2* p, float4 v) { __stcs(reinterpret_cast<float4*>(p), v); }
+
+template <class V>
+__device__ __forceinline__ V lin2(V m0, V a, V m1, V b) {
+  V r;
+  r.x = m0.x * a.x - m0.y * a.y + m1.x * b.x - m1.y * b.y;
+  r.y = m0.x * a.y + m0.y * a.x + m1.x * b.y + m1.y * b.x;
+  return r;
+}
+
+// complex64, bit 0 free: item = two pairs (x, x + 1) and (x | T, x + 1 | T).
+__global__ void gate1_c64_vec_kernel(float2* __restrict__ psi, uint64_t items, int t, FixedBits F, float2 m00,
+                                     float2 m01, float2 m10, float2 m11) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t T = 1ull << t;
+  for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < items; i0 += stride * kGateUnroll) {
+    float4 a[kGateUnroll], b[kGateUnroll];
+    uint64_t x[kGateUnroll];
+#pragma unroll
+    for (int u = 0; u < kGateUnroll; ++u) {
+      const uint64_t i = i0 + u * stride;
+      x[u] = i < items ? deposit(i, F) : 0;  // F fixes bit 0 (as 0)
+      if (i < items) {
+        a[u] = ldcs4(psi + x[u]);
+        b[u] = ldcs4(psi + (x[u] | T));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kGateUnroll; ++u) {
+      if (i0 + u * stride >= items) continue;
+      const float2 a0 = make_float2(a[u].x, a[u].y), a1 = make_float2(a[u].z, a[u].w);
+      const float2 b0 = make_float2(b[u].x, b[u].y), b1 = make_float2(b[u].z, b[u].w);
+      const float2 y0 = lin2(m00, a0, m01, b0), z0 = lin2(m10, a0, m11, b0);
+      const float2 y1 = lin2(m00, a1, m01, b1), z1 = lin2(m10, a1, m11, b1);
+      stcs4(psi + x[u], make_float4(y0.x, y0.y, y1.x, y1.y));
+      stcs4(psi + (x[u] | T), make_float4(z0.x, z0.y, z1.x, z1.y));
+    }
+  }
+}
+
+// complex64 with the target on qubit 0: item = one pair in one 16-byte access.
+__global__ void gate1_c64_q0_kernel(float2* __restrict__ psi, uint64_t items, FixedBits F, float2 m00, float2 m01,
+                                    float2 m10, float2 m11) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < items; i0 += stride * kGateUnroll) {
+    float4 a[kGateUnroll];
+    uint64_t x[kGateUnroll];
+#pragma unroll
+    for (int u = 0; u < kGateUnroll; ++u) {
+      const uint64_t i = i0 + u * stride;
+      x[u] = i < items ? deposit(i, F) : 0;
+      if (i < items) a[u] = ldcs4(psi + x[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kGateUnroll; ++u) {
+      if (i0 + u * stride >= items) continue;
+      const float2 a0 = make_float2(a[u].x, a[u].y), a1 = make_float2(a[u].z, a[u].w);
+      const float2 y = lin2(m00, a0, m01, a1), z = lin2(m10, a0, m11, a1);
+      stcs4(psi + x[u], make_float4(y.x, y.y, z.x, z.y));
+    }
+  }
+}
+
+// One pair per item (complex128, or complex64 with bit 0 fixed by a control).
+template <class T>
+__global__ void gate1_pair_kernel(typename V2<T>::V* __restrict__ psi, uint64_t items, int t, FixedBits F,
+                                  typename V2<T>::V m00, typename V2<T>::V m01, typename V2<T>::V m10,
+                                  typename V2<T>::V m11) {
+  using V = typename V2<T>::V;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t Tb = 1ull << t;
+  for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < items; i0 += stride * kGateUnroll) {
+    V a[kGateUnroll], b[kGateUnroll];
+    uint64_t x[kGateUnroll];
+#pragma unroll
+    for (int u = 0; u < kGateUnroll; ++u) {
+      const uint64_t i = i0 + u * stride;
+      x[u] = i < items ? deposit(i, F) : 0;
+      if (i < items) {
+        a[u] = __ldcs(psi + x[u]);
+        b[u] = __ldcs(psi + (x[u] | Tb));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kGateUnroll; ++u) {
+      if (i0 + u * stride >= items) continue;
+      __stcs(psi + x[u], lin2(m00, a[u], m01, b[u]));
+      __stcs(psi + (x[u] | Tb), lin2(m10, a[u], m11, b[u]));
+    }
+  }
+}
+
+// Diagonal: amplitude x gets d[bit t0 + 2 bit t1] (targets that are fixed bits
+// contribute their deposited value).  VEC (complex64, bit 0 free): two adjacent
+// amplitudes per item, which share the factor unless a target is qubit 0.
+template <class T, bool VEC>
+__global__ void diag_fast_kernel(typename V2<T>::V* __restrict__ psi, uint64_t items, int nt, int t0, int t1,
+                                 FixedBits F, typename V2<T>::V d0, typename V2<T>::V d1, typename V2<T>::V d2,
+                                 typename V2<T>::V d3) {
+  using V = typename V2<T>::V;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < items; i0 += stride * kGateUnroll) {
+    uint64_t x[kGateUnroll];
+    float4 a4[kGateUnroll];
+    V a[kGateUnroll];
+#pragma unroll
+    for (int u = 0; u < kGateUnroll; ++u) {
+      const uint64_t i = i0 + u * stride;
+      x[u] = i < items ? deposit(i, F) : 0;  // VEC: F fixes bit 0 (as 0)
+      if (i < items) {
+        if constexpr (VEC)
+          a4[u] = ldcs4(reinterpret_cast<const float2*>(psi) + x[u]);
+        else
+          a[u] = __ldcs(psi + x[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kGateUnroll; ++u) {
+      if (i0 + u * stride >= items) continue;
+      auto factor = [&](uint64_t y) {
+        int b = (int)((y >> t0) & 1);
+        if (nt == 2) b |= (int)((y >> t1) & 1) << 1;
+        return b == 0 ? d0 : (b == 1 ? d1 : (b == 2 ? d2 : d3));
+      };
+      if constexpr (VEC) {
+        const V f0 = factor(x[u]), f1 = factor(x[u] + 1);
+        const V y0 = mulc(f0, make_float2(a4[u].x, a4[u].y)), y1 = mulc(f1, make_float2(a4[u].z, a4[u].w));
+        stcs4(reinterpret_cast<float2*>(psi) + x[u], make_float4(y0.x, y0.y, y1.x, y1.y));
+      } else {
+        __stcs(psi + x[u], mulc(factor(x[u]), a[u]));
+      }
+    }
+  }
+}
+
+int gate_grid(uint64_t work) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const uint64_t want = (work + (uint64_t)kThreads * kGateUnroll - 1) / ((uint64_t)kThreads * kGateUnroll);
+  return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * 8));
+}
+
+// Sorted fixed bits from a position mask; false if there are too many.
+bool fixed_from(uint64_t fixed_mask, uint64_t ones, FixedBits* F) {
+  F->k = 0;
+  F->ones = ones;
+  for (int q = 0; q < 64; ++q)
+    if ((fixed_mask >> q) & 1) {
+      if (F->k == kMaxFixed) return false;
+      F->pos[F->k++] = q;
+    }
+  return true;
 }
 
 // --------------------------------------------------------------- init
@@ -492,6 +681,43 @@ __global__ void sample_kernel(const typename V2<T>::V* __restrict__ psi, int n, 
 
 qs_status launch_gate_dense(qs_dtype dt, void* psi, int n, int nt, const int* t, uint64_t cmask, const double* mat,
                             cudaStream_t st) {
+  if (nt == 1) {
+    const int q = t[0];
+    FixedBits F;
+    if (fixed_from(cmask | (1ull << q), cmask, &F)) {
+      const int nfix = F.k;
+      const uint64_t pairs = 1ull << (n - nfix);  // items of one pair each
+      if (dt == QS_C64) {
+        const float2 m00 = make_float2((float)mat[0], (float)mat[1]), m01 = make_float2((float)mat[2], (float)mat[3]);
+        const float2 m10 = make_float2((float)mat[4], (float)mat[5]), m11 = make_float2((float)mat[6], (float)mat[7]);
+        if (q == 0 && cmask == 0) {
+          FixedBits F0;
+          fixed_from(1ull, 0, &F0);
+          gate1_c64_q0_kernel<<<gate_grid(pairs), kThreads, 0, st>>>((float2*)psi, pairs, F0, m00, m01, m10, m11);
+        } else if (!(cmask & 1ull) && q != 0 && n - nfix >= 1) {
+          // bit 0 free: fix it too, two amplitudes per access
+          FixedBits F2;
+          if (fixed_from(cmask | (1ull << q) | 1ull, cmask, &F2)) {
+            gate1_c64_vec_kernel<<<gate_grid(pairs / 2), kThreads, 0, st>>>((float2*)psi, pairs / 2, q, F2, m00, m01,
+                                                                            m10, m11);
+          } else {
+            gate1_pair_kernel<float><<<gate_grid(pairs), kThreads, 0, st>>>((float2*)psi, pairs, q, F, m00, m01, m10,
+                                                                           m11);
+          }
+        } else {
+          gate1_pair_kernel<float><<<gate_grid(pairs), kThreads, 0, st>>>((float2*)psi, pairs, q, F, m00, m01, m10,
+                                                                         m11);
+        }
+      } else {
+        const double2 m00 = make_double2(mat[0], mat[1]), m01 = make_double2(mat[2], mat[3]);
+        const double2 m10 = make_double2(mat[4], mat[5]), m11 = make_double2(mat[6], mat[7]);
+        gate1_pair_kernel<double><<<gate_grid(pairs), kThreads, 0, st>>>((double2*)psi, pairs, q, F, m00, m01, m10,
+                                                                        m11);
+      }
+      QS_CUDA(cudaGetLastError());
+      return QS_OK;
+    }
+  }
   Mat4 M;
   const int D = 1 << nt;
   for (int i = 0; i < D * D; ++i) {
@@ -518,6 +744,41 @@ qs_status launch_gate_dense(qs_dtype dt, void* psi, int n, int nt, const int* t,
 
 qs_status launch_gate_diag(qs_dtype dt, void* psi, int n, int nt, const int* t, uint64_t cmask, const double* diag,
                            cudaStream_t st) {
+  {
+    // amplitudes left unchanged are skipped: a single-qubit diagonal with first
+    // entry 1 (Z, S, T, phase shift) changes only the target's |1> half
+    const bool first_one = nt == 1 && diag[0] == 1.0 && diag[1] == 0.0;
+    uint64_t fixed = cmask, ones = cmask;
+    if (first_one) {
+      fixed |= 1ull << t[0];
+      ones |= 1ull << t[0];
+    }
+    FixedBits F;
+    if (fixed_from(fixed, ones, &F)) {
+      const uint64_t amps = 1ull << (n - F.k);
+      const int t0 = t[0], t1 = nt == 2 ? t[1] : t[0];
+      if (dt == QS_C64) {
+        float2 d[4];
+        for (int i = 0; i < 4; ++i) d[i] = i < (1 << nt) ? make_float2((float)diag[2 * i], (float)diag[2 * i + 1])
+                                                          : make_float2(1.f, 0.f);
+        FixedBits F2;
+        if (!(fixed & 1ull) && n - F.k >= 1 && fixed_from(fixed | 1ull, ones, &F2))
+          diag_fast_kernel<float, true><<<gate_grid(amps / 2), kThreads, 0, st>>>((float2*)psi, amps / 2, nt, t0, t1, F2,
+                                                                                  d[0], d[1], d[2], d[3]);
+        else
+          diag_fast_kernel<float, false><<<gate_grid(amps), kThreads, 0, st>>>((float2*)psi, amps, nt, t0, t1, F, d[0],
+                                                                              d[1], d[2], d[3]);
+      } else {
+        double2 d[4];
+        for (int i = 0; i < 4; ++i)
+          d[i] = i < (1 << nt) ? make_double2(diag[2 * i], diag[2 * i + 1]) : make_double2(1.0, 0.0);
+        diag_fast_kernel<double, false><<<gate_grid(amps), kThreads, 0, st>>>((double2*)psi, amps, nt, t0, t1, F, d[0],
+                                                                             d[1], d[2], d[3]);
+      }
+      QS_CUDA(cudaGetLastError());
+      return QS_OK;
+    }
+  }
   Mat4 D;
   for (int i = 0; i < (1 << nt); ++i) {
     D.re[i] = diag[2 * i];

@@ -127,3 +127,48 @@ def test_batched_vqe_workload_sampled_instances(Q):
         sc = max(1.0, float(np.abs(it.ham.coef).sum()))
         assert abs(e[i] - E) <= TOL[0] * sc
         assert np.max(np.abs(g[i] - G)) <= TOL[0] * sc
+
+
+def _sweep_amplitude(n, x, rz, cnots, czs):
+    """Amplitude at index x after H on every qubit of |0..0>, RZ(rz[q]) on every
+    qubit, the CNOTs (c, t) in order, then CZ on each pair: CNOTs and CZs map a
+    product state to a phased permutation of it, so the amplitude is written out
+    from the definitions (RZ(a) = diag(e^{-ia/2}, e^{ia/2}))."""
+    phase = 0.0
+    for c, t in czs:
+        if (x >> c) & 1 and (x >> t) & 1:
+            phase += math.pi
+    for c, t in reversed(cnots):  # undo the permutation back to the product state
+        if (x >> c) & 1:
+            x ^= 1 << t
+    for q in range(n):
+        phase += rz[q] / 2 if (x >> q) & 1 else -rz[q] / 2
+    return 2.0 ** (-n / 2) * complex(math.cos(phase), math.sin(phase))
+
+
+@pytest.mark.parametrize("dt,n", [(0, 30), (1, 29)])
+def test_per_gate_sweep_at_full_size(Q, dt, n):
+    """The single-gate kernels bench.py's gate sweep times, at its size: H, RZ,
+    controlled X and controlled Z on every qubit (the paired, qubit-0, controlled
+    and diagonal paths), checked on 4096 sampled amplitudes against the closed
+    form and on the norm."""
+    import torch
+    rng = np.random.default_rng(7)
+    rz = rng.uniform(-np.pi, np.pi, n)
+    cnots = [(q, (q + 1) % n) for q in range(n)]
+    czs = [((q + 2) % n, q) for q in range(n)]
+    gates = [I.Gate("H", (q,)) for q in range(n)]
+    gates += [I.Gate("RZ", (q,), const=float(rz[q])) for q in range(n)]
+    gates += [I.Gate("X", (t,), (c,)) for c, t in cnots]
+    gates += [I.Gate("Z", (t,), (c,)) for c, t in czs]
+    c = Q.circuit_from(I.Circuit(n, gates)).finalize(dt, fuse=-1)
+    s = Q.State(n, dt)
+    s.set_basis(0)
+    c.apply(s, [])
+    idx = np.concatenate([np.arange(64), (1 << n) - 1 - np.arange(64), rng.integers(0, 1 << n, 3968)])
+    got = s.amplitudes[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    want = np.array([_sweep_amplitude(n, int(x), rz, cnots, czs) for x in idx])
+    assert np.abs(got - want).max() < TOL[dt] * 2.0 ** (-n / 2) * 10
+    assert abs(s.norm2() - 1.0) < (1e-5 if dt == 0 else 1e-12)
+    del s
+    torch.cuda.empty_cache()

@@ -317,35 +317,42 @@ def run_ours(args, ws, rank, local):
     }
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_block(n, args.cpu_qubits, p, 1)
+    if ws == 1 and not args.no_extras:
+        # the rest of the headline: the single-gate sweep against the HBM roofline
+        # and batched vs one-launch-per-circuit (untimed by the step clock above)
+        del psi, lam, q
+        torch.cuda.empty_cache()
+        sw = measure_gate_sweep(Q, n, Q.C64, 3)
+        line["gate_sweep"] = {k: sw[k] for k in ("n_qubits", "dtype", "GBps", "frac", "gates_per_s", "launches")}
+        line["gate_sweep"]["per_kind_frac_median"] = {k: v["frac_median"] for k, v in sw["per_kind"].items()}
+        line["batched_vs_plain"] = measure_batched_vs_plain(Q, args.instances, 3, args.plain_instances)
     print(json.dumps(line), flush=True)
 
 
-def run_batch_workload(args):
-    """2048 batched-VQE instances (n ~ U{10..20}, HEA depth ~ U{2..10}, TFIM, seed 4):
-    one persistent launch per step vs one launch sequence per circuit."""
+def measure_batched_vs_plain(Q, instances, steps, plain_instances, warmup=3):
+    """The batched-VQE recipe (n ~ U{10..20}, HEA depth ~ U{2..10}, TFIM, seed 4):
+    one persistent launch per step (CUDA events) vs one launch sequence per
+    circuit through the single-instance engine (host clock, synchronised)."""
     import numpy as np
     import torch
-    from paper_2406_17248_gb300 import build, inputs as I
-    build.build()
-    from paper_2406_17248_gb300 import qsim as Q
-    inst = I.batched_vqe(args.instances, seed=4)
+    from paper_2406_17248_gb300 import inputs as I
+    inst = I.batched_vqe(instances, seed=4)
     b = Q.Batch(inst, Q.C64)
     params = torch.tensor(np.concatenate([it.params for it in inst]), dtype=torch.float64, device="cuda")
     energies = torch.empty(len(inst), dtype=torch.float64, device="cuda")
     grads = torch.empty_like(params)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.expectation_with_grad_device(params, energies, grads)
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         b.expectation_with_grad_device(params, energies, grads)
     t1.record()
     torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1) / args.steps
+    ms = t0.elapsed_time(t1) / steps
     batched = len(inst) / (ms / 1e3)
-    # plain: one launch sequence per circuit through the single-instance engine
-    plain_n = min(len(inst), args.plain_instances)
+    plain_n = min(len(inst), plain_instances)
     circs = [Q.circuit_from(it.circuit).finalize(Q.C64) for it in inst[:plain_n]]
     hams = [Q.Hamiltonian(it.ham) for it in inst[:plain_n]]
     states = {}
@@ -353,11 +360,13 @@ def run_batch_workload(args):
         n = it.circuit.n_qubits
         if n not in states:
             states[n] = (Q.State(n, Q.C64), Q.State(n, Q.C64))
+
     def plain_pass():
         for it, c, h in zip(inst[:plain_n], circs, hams):
             psi, lam = states[it.circuit.n_qubits]
             psi.set_basis(0)
             Q.expectation_with_grad(psi, lam, c, h, it.params)
+
     plain_pass()
     torch.cuda.synchronize()
     h0 = time.perf_counter()
@@ -365,19 +374,30 @@ def run_batch_workload(args):
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - h0
     plain = plain_n / plain_s
-    # energies of the two forms agree
     e_b = energies.cpu().numpy()[:plain_n]
     psi, lam = states[inst[0].circuit.n_qubits]
     psi.set_basis(0)
     e0, _ = Q.expectation_with_grad(psi, lam, circs[0], hams[0], inst[0].params)
+    return {"instances": len(inst), "batched": batched, "ms_per_step": ms, "steps": steps,
+            "plain": plain, "plain_instances_timed": plain_n, "plain_seconds": plain_s,
+            "speedup_vs_plain": batched / plain, "energy_check": abs(float(e_b[0]) - e0), "batch_info": b.info()}
+
+
+def run_batch_workload(args):
+    """2048 batched-VQE instances (n ~ U{10..20}, HEA depth ~ U{2..10}, TFIM, seed 4):
+    one persistent launch per step vs one launch sequence per circuit."""
+    from paper_2406_17248_gb300 import build
+    build.build()
+    from paper_2406_17248_gb300 import qsim as Q
+    r = measure_batched_vs_plain(Q, args.instances, args.steps, args.plain_instances, args.warmup)
     line = {"metric": "batched VQE energy+adjoint-grad instances/s (persistent launch vs one launch sequence per circuit)",
-            "value": batched, "unit": "instances/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{len(inst)} instances, n ~ U{{10..20}}, HEA depth ~ U{{2..10}}, TFIM J~N(1,0.2) "
-                                   "h~U[0.5,1.5], complex64, seed 4", "instances": len(inst)},
-            "plain": {"value": plain, "unit": "instances/s", "instances_timed": plain_n, "seconds": plain_s},
-            "speedup_vs_plain": batched / plain, "energy_check": abs(float(e_b[0]) - e0),
-            "batch_info": b.info()}
+            "value": r["batched"], "unit": "instances/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": r["ms_per_step"], "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{r['instances']} instances, n ~ U{{10..20}}, HEA depth ~ U{{2..10}}, TFIM "
+                                   "J~N(1,0.2) h~U[0.5,1.5], complex64, seed 4", "instances": r["instances"]},
+            "plain": {"value": r["plain"], "unit": "instances/s", "instances_timed": r["plain_instances_timed"],
+                      "seconds": r["plain_seconds"]},
+            "speedup_vs_plain": r["speedup_vs_plain"], "energy_check": r["energy_check"], "batch_info": r["batch_info"]}
     print(json.dumps(line), flush=True)
 
 
@@ -958,19 +978,15 @@ def run_traj_workload(args):
     print(json.dumps(line), flush=True)
 
 
-def run_gates_workload(args):
-    """Single-gate sweep on an n-qubit state (default 30, complex64, from |+>^n):
-    H, RZ(0.3), CNOT (control q + 1) and CZ (control q + 1) on every target q,
-    each gate one launch of the per-gate kernels (`fuse = -1`).  Algorithmic bytes
-    count the amplitudes a gate changes, read and written: H and RZ 2 S, CNOT S,
-    CZ S / 2 (S = the state's bytes).  value = the sweep's bytes / its time."""
+def measure_gate_sweep(Q, n, dt, reps):
+    """Single-gate sweep on an n-qubit state from |+>^n: H, RZ(0.3), CNOT (control
+    q + 1) and CZ (control q + 1) on every target q, each gate one launch of the
+    per-gate kernels (`fuse = -1`), CUDA events on the launching stream.
+    Algorithmic bytes count the amplitudes a gate changes, read and written: H and
+    RZ 2 S, CNOT S, CZ S / 2 (S = the state's bytes)."""
     import numpy as np
     import torch
-    from paper_2406_17248_gb300 import build, inputs as I
-    build.build()
-    from paper_2406_17248_gb300 import qsim as Q
-    n = args.n
-    dt = Q.C128 if args.gate_dtype == "c128" else Q.C64
+    from paper_2406_17248_gb300 import inputs as I
     S = (8 if dt == Q.C64 else 16) * float(1 << n)
     s = Q.State(n, dt)
     s.set_plus()
@@ -985,11 +1001,8 @@ def run_gates_workload(args):
             circs[k][q].apply(s, [])
     torch.cuda.synchronize()
     peak, peak_kind = measured_peak_hbm()
-    clocks = ClockSampler()
-    clocks.start()
     per = {}
     tot_bytes = tot_ms = 0.0
-    reps = max(1, args.steps)
     for k, (_, by) in kinds.items():
         ms_q = []
         for q in range(n):
@@ -1006,18 +1019,34 @@ def run_gates_workload(args):
                   "ms_median": float(np.median(ms_q)), "GBps_by_target": [round(g, 1) for g in gbs]}
         tot_bytes += by * n
         tot_ms += sum(ms_q)
-    ck = clocks.stop()
+    del s
+    torch.cuda.empty_cache()
     ach = tot_bytes / (tot_ms / 1e3) / 1e9
-    line = {"metric": f"{n}-qubit {'complex64' if dt == Q.C64 else 'complex128'} single-gate sweep (H, RZ, CNOT, CZ on "
-                      "every qubit), HBM GB/s",
-            "value": ach, "unit": "GB/s", "n_gpus": 1, "steps": reps, "warmup": 1,
-            "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+    return {"n_qubits": n, "dtype": "complex64" if dt == Q.C64 else "complex128", "GBps": ach, "peak": peak,
+            "frac": ach / peak, "peak_kind": f"{peak_kind} hbm_gbs", "ms": tot_ms, "gates_per_s": 4 * n / (tot_ms / 1e3),
+            "launches": 4 * n * reps, "per_kind": per}
+
+
+def run_gates_workload(args):
+    """`measure_gate_sweep` at --n qubits (default 30), complex64 or complex128."""
+    from paper_2406_17248_gb300 import build
+    build.build()
+    from paper_2406_17248_gb300 import qsim as Q
+    dt = Q.C128 if args.gate_dtype == "c128" else Q.C64
+    reps = max(1, args.steps)
+    clocks = ClockSampler()
+    clocks.start()
+    r = measure_gate_sweep(Q, args.n, dt, reps)
+    ck = clocks.stop()
+    line = {"metric": f"{args.n}-qubit {r['dtype']} single-gate sweep (H, RZ, CNOT, CZ on every qubit), HBM GB/s",
+            "value": r["GBps"], "unit": "GB/s", "n_gpus": 1, "steps": reps, "warmup": 1,
+            "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if dt == Q.C64 else "f64", "data": "synthetic",
-            "config": {"workload": f"{n} qubits from |+>^n, 4 x {n} single-gate launches", "l2": "state > L2"},
-            "gates_per_s": 4 * n / (tot_ms / 1e3),
-            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs"},
-            "per_kind": per, "gpu_launches": 4 * n * reps, "clocks": ck}
+            "config": {"workload": f"{args.n} qubits from |+>^n, 4 x {args.n} single-gate launches", "l2": "state > L2"},
+            "gates_per_s": r["gates_per_s"],
+            "roofline": {"bound": "hbm", "achieved": r["GBps"], "peak": r["peak"], "unit": "GB/s", "frac": r["frac"],
+                         "traffic": None, "peak_kind": r["peak_kind"]},
+            "per_kind": r["per_kind"], "gpu_launches": r["launches"], "clocks": ck}
     print(json.dumps(line), flush=True)
 
 
@@ -1037,6 +1066,7 @@ def main():
     ap.add_argument("--cpu-qubits", type=int, default=20)
     ap.add_argument("--ref-qubits", type=int, default=18)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="default workload: skip the gate sweep and batch lines")
     ap.add_argument("--block-k", type=int, default=5)
     ap.add_argument("--gate-dtype", default="c64", choices=["c64", "c128"])
     args = ap.parse_args()

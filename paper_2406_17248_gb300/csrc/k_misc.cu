@@ -199,8 +199,25 @@ __global__ void gate1_c64_q0_kernel(float2* __restrict__ psi, uint64_t items, Fi
   }
 }
 
+// y = m0 a + m1 b for the matrix forms: 0 general complex, 1 real entries (H, RY,
+// X: half the multiplications), 2 real diagonal and imaginary off-diagonal (RX).
+template <int FORM, class V>
+__device__ __forceinline__ V lin2f(V m0, V a, V m1, V b) {
+  V r;
+  if constexpr (FORM == 1) {
+    r.x = m0.x * a.x + m1.x * b.x;
+    r.y = m0.x * a.y + m1.x * b.y;
+  } else if constexpr (FORM == 2) {  // m0 real on the diagonal, m1 = i m1.y off it
+    r.x = m0.x * a.x - m1.y * b.y;
+    r.y = m0.x * a.y + m1.y * b.x;
+  } else {
+    r = lin2(m0, a, m1, b);
+  }
+  return r;
+}
+
 // One pair per item (complex128, or complex64 with bit 0 fixed by a control).
-template <class T>
+template <class T, int FORM>
 __global__ void gate1_pair_kernel(typename V2<T>::V* __restrict__ psi, uint64_t items, int t, FixedBits F,
                                   typename V2<T>::V m00, typename V2<T>::V m01, typename V2<T>::V m10,
                                   typename V2<T>::V m11) {
@@ -222,8 +239,8 @@ __global__ void gate1_pair_kernel(typename V2<T>::V* __restrict__ psi, uint64_t 
 #pragma unroll
     for (int u = 0; u < kGateUnroll; ++u) {
       if (i0 + u * stride >= items) continue;
-      __stcs(psi + x[u], lin2(m00, a[u], m01, b[u]));
-      __stcs(psi + (x[u] | Tb), lin2(m10, a[u], m11, b[u]));
+      __stcs(psi + x[u], lin2f<FORM>(m00, a[u], m01, b[u]));
+      __stcs(psi + (x[u] | Tb), lin2f<FORM>(m11, b[u], m10, a[u]));
     }
   }
 }
@@ -701,18 +718,28 @@ qs_status launch_gate_dense(qs_dtype dt, void* psi, int n, int nt, const int* t,
             gate1_c64_vec_kernel<<<gate_grid(pairs / 2), kThreads, 0, st>>>((float2*)psi, pairs / 2, q, F2, m00, m01,
                                                                             m10, m11);
           } else {
-            gate1_pair_kernel<float><<<gate_grid(pairs), kThreads, 0, st>>>((float2*)psi, pairs, q, F, m00, m01, m10,
-                                                                           m11);
+            gate1_pair_kernel<float, 0><<<gate_grid(pairs), kThreads, 0, st>>>((float2*)psi, pairs, q, F, m00, m01,
+                                                                              m10, m11);
           }
         } else {
-          gate1_pair_kernel<float><<<gate_grid(pairs), kThreads, 0, st>>>((float2*)psi, pairs, q, F, m00, m01, m10,
-                                                                         m11);
+          gate1_pair_kernel<float, 0><<<gate_grid(pairs), kThreads, 0, st>>>((float2*)psi, pairs, q, F, m00, m01, m10,
+                                                                            m11);
         }
       } else {
         const double2 m00 = make_double2(mat[0], mat[1]), m01 = make_double2(mat[2], mat[3]);
         const double2 m10 = make_double2(mat[4], mat[5]), m11 = make_double2(mat[6], mat[7]);
-        gate1_pair_kernel<double><<<gate_grid(pairs), kThreads, 0, st>>>((double2*)psi, pairs, q, F, m00, m01, m10,
-                                                                        m11);
+        // complex128 is bound by the FP64 rate: use the cheapest form the matrix allows
+        const bool real = mat[1] == 0 && mat[3] == 0 && mat[5] == 0 && mat[7] == 0;
+        const bool rxf = mat[1] == 0 && mat[7] == 0 && mat[2] == 0 && mat[4] == 0;
+        if (real)
+          gate1_pair_kernel<double, 1><<<gate_grid(pairs), kThreads, 0, st>>>((double2*)psi, pairs, q, F, m00, m01,
+                                                                             m10, m11);
+        else if (rxf)
+          gate1_pair_kernel<double, 2><<<gate_grid(pairs), kThreads, 0, st>>>((double2*)psi, pairs, q, F, m00, m01,
+                                                                             m10, m11);
+        else
+          gate1_pair_kernel<double, 0><<<gate_grid(pairs), kThreads, 0, st>>>((double2*)psi, pairs, q, F, m00, m01,
+                                                                             m10, m11);
       }
       QS_CUDA(cudaGetLastError());
       return QS_OK;

@@ -707,10 +707,9 @@ qs_status launch_gate_dense(qs_dtype dt, void* psi, int n, int nt, const int* t,
       if (dt == QS_C64) {
         const float2 m00 = make_float2((float)mat[0], (float)mat[1]), m01 = make_float2((float)mat[2], (float)mat[3]);
         const float2 m10 = make_float2((float)mat[4], (float)mat[5]), m11 = make_float2((float)mat[6], (float)mat[7]);
-        if (q == 0 && cmask == 0) {
-          FixedBits F0;
-          fixed_from(1ull, 0, &F0);
-          gate1_c64_q0_kernel<<<gate_grid(pairs), kThreads, 0, st>>>((float2*)psi, pairs, F0, m00, m01, m10, m11);
+        if (q == 0) {
+          // the pair (x, x + 1) is one aligned 16-byte word; controls are fixed bits
+          gate1_c64_q0_kernel<<<gate_grid(pairs), kThreads, 0, st>>>((float2*)psi, pairs, F, m00, m01, m10, m11);
         } else if (!(cmask & 1ull) && q != 0 && n - nfix >= 1) {
           // bit 0 free: fix it too, two amplitudes per access
           FixedBits F2;

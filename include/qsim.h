@@ -85,9 +85,14 @@ typedef struct qs_qaoa qs_qaoa;
 
 /* Execution options for a circuit plan.  Zero means "library default". */
 typedef struct {
-  int fuse;      /* 1 (default): fused shared-memory tile passes; -1: one kernel per gate */
-  int tile_bits; /* log2 amplitudes per fused tile, 6..13 (default 12 for c64, 11 for c128) */
-  int low_bits;  /* low (contiguous) qubits present in every tile, 1..tile_bits (default 4) */
+  int fuse;       /* 1 (default): fused shared-memory tile passes; -1: one kernel per gate */
+  int tile_bits;  /* log2 amplitudes per fused tile, 6..13 (default 12 for c64, 11 for c128) */
+  int low_bits;   /* low (contiguous) qubits present in every tile, 1..tile_bits (default 4) */
+  int checkpoint; /* adjoint state checkpoints, 0 (default): none.  Circuits: every `checkpoint`
+                     gates the forward sweep saves psi (passes never span that boundary) and the
+                     reverse sweep reloads it there instead of the uncomputed state, which bounds
+                     the rounding drift of long uncompute chains; one extra state of memory per
+                     checkpoint.  QAOA engine: every `checkpoint` layers (about two passes each). */
 } qs_options;
 
 /* Library version string and the last error message of this thread. */

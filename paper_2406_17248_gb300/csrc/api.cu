@@ -278,6 +278,10 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
   P.runs.clear();
   P.run_off.clear();
   P.run_diag.clear();
+  // checkpoint segments: gates [s K, (s + 1) K); no run and no pass crosses them
+  const int ckK = c->opts.checkpoint > 0 ? c->opts.checkpoint : 0;
+  auto seg_of = [&](size_t i) { return ckK > 0 ? (int)(i / (size_t)ckK) : 0; };
+  const int n_seg = ckK > 0 ? std::max(1, (int)((G + ckK - 1) / ckK)) : 1;
   if (c->fuse_1q) {
     auto single = [&](const HostGate& g) { return g.nt == 1 && g.ctrls.empty() && g.kind != QS_GATE_I; };
     std::vector<int> last(64, -1);        // latest gate touching each qubit
@@ -287,7 +291,7 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
       if (g.kind == QS_GATE_I) continue;
       if (single(g)) {
         const int q = g.t[0], j = last[q];
-        if (j >= 0 && single(c->gates[j])) {
+        if (j >= 0 && single(c->gates[j]) && seg_of((size_t)j) == seg_of(i)) {
           int r = run_of[j];
           if (r < 0) {
             r = (int)P.runs.size();
@@ -349,7 +353,7 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
     }
     return it;
   };
-  std::vector<PlanItem> fwd, rev;
+  std::vector<std::vector<PlanItem>> fwd(n_seg), rev(n_seg);
   std::vector<int> run_index(G, -1);  // head gate -> its run
   for (size_t r = 0; r < P.runs.size(); ++r) run_index[P.runs[r][0]] = (int)r;
   for (size_t i = 0; i < G; ++i) {
@@ -361,13 +365,20 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
       it.ops.clear();
       it.ops.push_back(ItemOp{(uint8_t)(P.run_diag[r] ? OP_DIAG : OP_DENSE1), 0, P.run_off[r], -1, 0.0});
     }
-    fwd.push_back(it);
+    fwd[seg_of(i)].push_back(it);
   }
   for (size_t i = G; i-- > 0;)
-    if (c->gates[i].kind != QS_GATE_I || c->gates[i].param >= 0) rev.push_back(make_item(i, true));
+    if (c->gates[i].kind != QS_GATE_I || c->gates[i].param >= 0) rev[seg_of(i)].push_back(make_item(i, true));
   SlotMap none;
-  QS_TRY(plan_items(fwd, pp, PF_LOAD_PSI | PF_STORE_PSI, &P.fwd, &none));
-  QS_TRY(plan_items(rev, pp, PF_LOAD_PSI | PF_LOAD_LAM | PF_STORE_PSI | PF_STORE_LAM, &P.rev, &P.rev_slots));
+  for (int sg = 0; sg < n_seg; ++sg) {
+    if (!fwd[sg].empty()) QS_TRY(plan_items(fwd[sg], pp, PF_LOAD_PSI | PF_STORE_PSI, &P.fwd, &none));
+    P.fwd_seg_end.push_back((int)P.fwd.passes.size());
+  }
+  for (int sg = n_seg - 1; sg >= 0; --sg) {
+    if (!rev[sg].empty())
+      QS_TRY(plan_items(rev[sg], pp, PF_LOAD_PSI | PF_LOAD_LAM | PF_STORE_PSI | PF_STORE_LAM, &P.rev, &P.rev_slots));
+    P.rev_seg_end.push_back((int)P.rev.passes.size());
+  }
   QS_TRY(P.fwd.upload(st));
   QS_TRY(P.rev.upload(st));
   QS_TRY(build_csr(P.rev_slots, std::max(P.n_params, 1), &P.d_row, &P.d_sidx, &P.d_w, st));
@@ -752,6 +763,7 @@ qs_status qs_circuit_finalize(qs_circuit* c, qs_dtype dtype, const qs_options* o
              "tile_bits must be 0 or 6..13");
     QS_CHECK(opts->low_bits >= 0 && opts->low_bits <= kMaxTileBits, "low_bits must be 0..13");
     QS_CHECK(opts->fuse == 0 || opts->fuse == 1 || opts->fuse == -1, "fuse must be -1, 0 or 1");
+    QS_CHECK(opts->checkpoint >= 0, "checkpoint must be >= 0");
     c->opts = *opts;
   }
   cudaDeviceSynchronize();
@@ -909,6 +921,47 @@ qs_status qs_inner_product(const qs_state* bra, const qs_state* ket, double* out
   return QS_OK;
 }
 
+namespace {
+
+// Forward passes of a plan on psi; with checkpoints, psi is saved after every
+// inner segment boundary.
+qs_status forward_sweep(CircuitPlan& P, qs_state* psi, double* d_part, cudaStream_t st) {
+  const size_t bytes = amp_bytes(psi->dt) << psi->ne;
+  const int nseg = (int)P.fwd_seg_end.size();
+  if (nseg > 1 && (int)P.ckpt.size() != nseg - 1) {
+    for (void* b : P.ckpt) cudaFree(b);
+    P.ckpt.assign(nseg - 1, nullptr);
+    for (auto& b : P.ckpt) QS_CUDA(cudaMalloc(&b, bytes));
+  }
+  int b = 0;
+  for (int sg = 0; sg < nseg; ++sg) {
+    QS_TRY(run_passes(P.fwd, b, P.fwd_seg_end[sg], psi->dt, psi->ptr, nullptr, P.d_coef, nullptr, d_part, psi->ne, 0,
+                      P.grid1, P.grid2, st));
+    b = P.fwd_seg_end[sg];
+    if (sg + 1 < nseg) QS_CUDA(cudaMemcpyAsync(P.ckpt[sg], psi->ptr, bytes, cudaMemcpyDeviceToDevice, st));
+  }
+  return QS_OK;
+}
+
+// Reverse passes on (psi, lam); with checkpoints, psi is reloaded from the
+// saved state at every inner segment boundary before that segment is undone.
+qs_status reverse_sweep(CircuitPlan& P, qs_state* psi, qs_state* lam, double* d_part, cudaStream_t st) {
+  const size_t bytes = amp_bytes(psi->dt) << psi->ne;
+  const int nseg = (int)P.rev_seg_end.size();
+  int b = 0;
+  for (int r = 0; r < nseg; ++r) {
+    const int sg = nseg - 1 - r;
+    if (r > 0 && (int)P.ckpt.size() == nseg - 1)
+      QS_CUDA(cudaMemcpyAsync(psi->ptr, P.ckpt[sg], bytes, cudaMemcpyDeviceToDevice, st));
+    QS_TRY(run_passes(P.rev, b, P.rev_seg_end[r], psi->dt, psi->ptr, lam->ptr, P.d_coef, nullptr, d_part, psi->ne, 0,
+                      P.grid1, P.grid2, st));
+    b = P.rev_seg_end[r];
+  }
+  return QS_OK;
+}
+
+}  // namespace
+
 qs_status qs_expectation_with_grad(qs_state* psi, qs_state* lam, qs_circuit* c, const qs_ham* h, const double* params,
                                    int n_params, double* energy, double* grad) {
   QS_TRY(check_state(psi));
@@ -940,13 +993,11 @@ qs_status qs_expectation_with_grad(qs_state* psi, qs_state* lam, qs_circuit* c, 
   double* d_E = d_slot + n_slots;
   double* d_grad = d_E + 1;
   double* d_hpart = d_grad + std::max(n_params, 1);
-  QS_TRY(run_passes(P.fwd, 0, (int)P.fwd.passes.size(), psi->dt, psi->ptr, nullptr, P.d_coef, nullptr, d_part,
-                    psi->ne, 0, P.grid1, P.grid2, st));
+  QS_TRY(forward_sweep(P, psi, d_part, st));
   QS_TRY(launch_ham_apply(psi->dt, psi->ptr, lam->ptr, psi->ne, h->d_groups, h->n_groups, h->d_terms, d_hpart, hgrid,
                           st));
   QS_TRY(launch_reduce_slots(d_hpart, 1, hgrid, nullptr, d_E, st));
-  QS_TRY(run_passes(P.rev, 0, (int)P.rev.passes.size(), psi->dt, psi->ptr, lam->ptr, P.d_coef, nullptr, d_part,
-                    psi->ne, 0, P.grid1, P.grid2, st));
+  QS_TRY(reverse_sweep(P, psi, lam, d_part, st));
   QS_TRY(launch_reduce_slots(d_part, n_slots, P.grid2, nullptr, d_slot, st));
   QS_TRY(launch_param_gather(d_slot, P.d_row, P.d_sidx, P.d_w, c->n_params, d_grad, st));
   QS_CUDA(cudaMemcpyAsync(energy, d_E, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -997,16 +1048,14 @@ qs_status qs_expectation_with_grad_multi(qs_state* psi, qs_state* lam, qs_circui
   const size_t bytes = amp_bytes(psi->dt) << psi->ne;
   if (!psi->save) QS_CUDA(cudaMalloc(&psi->save, bytes));
   // one forward sweep; each Hamiltonian restarts the reverse sweep from its copy
-  QS_TRY(run_passes(P.fwd, 0, (int)P.fwd.passes.size(), psi->dt, psi->ptr, nullptr, P.d_coef, nullptr, d_part,
-                    psi->ne, 0, P.grid1, P.grid2, st));
+  QS_TRY(forward_sweep(P, psi, d_part, st));
   QS_CUDA(cudaMemcpyAsync(psi->save, psi->ptr, bytes, cudaMemcpyDeviceToDevice, st));
   for (int h = 0; h < n_ham; ++h) {
     if (h > 0) QS_CUDA(cudaMemcpyAsync(psi->ptr, psi->save, bytes, cudaMemcpyDeviceToDevice, st));
     QS_TRY(launch_ham_apply(psi->dt, psi->ptr, lam->ptr, psi->ne, hams[h]->d_groups, hams[h]->n_groups,
                             hams[h]->d_terms, d_hpart, hgrid, st));
     QS_TRY(launch_reduce_slots(d_hpart, 1, hgrid, nullptr, d_E + h, st));
-    QS_TRY(run_passes(P.rev, 0, (int)P.rev.passes.size(), psi->dt, psi->ptr, lam->ptr, P.d_coef, nullptr, d_part,
-                      psi->ne, 0, P.grid1, P.grid2, st));
+    QS_TRY(reverse_sweep(P, psi, lam, d_part, st));
     if (c->n_params > 0) {
       QS_TRY(launch_reduce_slots(d_part, n_slots, P.grid2, nullptr, d_slot, st));
       QS_TRY(launch_param_gather(d_slot, P.d_row, P.d_sidx, P.d_w, c->n_params, d_grad + (size_t)h * np, st));

@@ -44,7 +44,16 @@ struct CircuitPlan {
   double* d_w = nullptr;
   int n_params = 0;
   int grid1 = 1, grid2 = 1;
+  // adjoint checkpoints: segment ends (pass indices) of the forward plan in
+  // circuit order and of the reverse plan in reverse order, and one saved state
+  // per inner segment boundary
+  std::vector<int> fwd_seg_end, rev_seg_end;
+  std::vector<void*> ckpt;
   void release() {
+    for (void* b : ckpt) cudaFree(b);
+    ckpt.clear();
+    fwd_seg_end.clear();
+    rev_seg_end.clear();
     fwd.free_device();
     rev.free_device();
     if (d_coef) cudaFree(d_coef);

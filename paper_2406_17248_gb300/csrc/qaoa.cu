@@ -52,9 +52,29 @@ struct qs_qaoa {
   bool il = false;
   void* d_il_priv = nullptr;
   int* d_max = nullptr;  // qs_qaoa_max_cut result
+  // adjoint checkpoints: psi saved after these forward passes, reloaded before
+  // the reverse pass that undoes the next one
+  std::vector<int> ck_after;
+  std::vector<void*> ckpt;
 };
 
 namespace {
+
+// ---------------------------------------------------------------------------- checkpoints
+
+// Reload psi into the interleaved reverse buffer: amplitude x is
+// (psi.re, lam.re, psi.im, lam.im) at il0[x] for x < half, il1[x - half] after.
+__global__ void il_reload_kernel(float4* __restrict__ il0, float4* __restrict__ il1, uint64_t half,
+                                 const float2* __restrict__ ck, uint64_t N) {
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
+    float4* e = x < half ? il0 + x : il1 + (x - half);
+    float4 v = *e;
+    const float2 p = __ldcs(ck + x);
+    v.x = p.x;
+    v.z = p.y;
+    *e = v;
+  }
+}
 
 // ---------------------------------------------------------------------------- schedule
 
@@ -389,6 +409,7 @@ qs_status qs_qaoa_create(int n_qubits, const int* edges, int n_edges, int p, dou
     QS_CHECK(opts->tile_bits == 0 || (opts->tile_bits >= kMinTileBits && opts->tile_bits <= kMaxTileBits),
              "tile_bits must be 0 or 6..13");
     QS_CHECK(opts->low_bits >= 0 && opts->low_bits <= kMaxTileBits, "low_bits must be 0..13");
+    QS_CHECK(opts->checkpoint >= 0, "checkpoint must be >= 0");
   }
 
   qs_qaoa* q = new qs_qaoa;
@@ -476,6 +497,9 @@ qs_status qs_qaoa_create(int n_qubits, const int* edges, int n_edges, int p, dou
   }
   q->n_fwd = K - 1;
   q->rev_passes = K - 1;
+  if (opts && opts->checkpoint > 0)  // about two forward passes per layer
+    for (int i = 0; i + 1 < K - 1; ++i)
+      if ((i + 1) % (2 * opts->checkpoint) == 0) q->ck_after.push_back(i);
   // energy plan: the forward passes with the energy appended to the last
   for (int i = 0; i < K; ++i) {
     std::vector<QOp> ops = sched[i].ops;
@@ -522,6 +546,7 @@ qs_status qs_qaoa_destroy(qs_qaoa* q) {
   if (q->d_gpass) cudaFree(q->d_gpass);
   if (q->d_epass) cudaFree(q->d_epass);
   if (q->d_il_priv) cudaFree(q->d_il_priv);
+  for (void* b : q->ckpt) cudaFree(b);
   for (int* pi : {q->g_row, q->g_sidx, q->e_row, q->e_sidx})
     if (pi) cudaFree(pi);
   for (double* pd : {q->g_w, q->e_w})
@@ -582,8 +607,10 @@ qs_status qaoa_check(qs_qaoa* q, qs_state* psi, const double* gamma, const doubl
 }
 
 qs_status run_qpasses(qs_qaoa* q, const std::vector<QPassDesc>& passes, const std::vector<int>& ns,
-                      const QPassDesc* d_passes, void* psi, void* lam, double* partials, cudaStream_t st) {
-  for (size_t i = 0; i < passes.size(); ++i) {
+                      const QPassDesc* d_passes, void* psi, void* lam, double* partials, cudaStream_t st,
+                      size_t begin = 0, size_t end = (size_t)-1) {
+  end = std::min(end, passes.size());
+  for (size_t i = begin; i < end; ++i) {
     QaoaLaunch L;
     L.il[0] = lam;  // the interleaved reverse sweep reuses lam's buffer as its first half
     L.il[1] = q->d_il_priv;
@@ -660,7 +687,43 @@ qs_status qs_qaoa_expectation_with_grad(qs_qaoa* q, qs_state* psi, qs_state* lam
   double* d_part = psi->scratch;
   double* d_slot = d_part + part;
   double* d_out = d_slot + n_slots;
-  QS_TRY(run_qpasses(q, q->gpass, q->gns, q->d_gpass, psi->ptr, lam->ptr, d_part, st));
+  if (q->ck_after.empty()) {
+    QS_TRY(run_qpasses(q, q->gpass, q->gns, q->d_gpass, psi->ptr, lam->ptr, d_part, st));
+  } else {
+    // checkpoints: psi saved after the chosen forward passes and reloaded before
+    // the reverse pass that undoes the following one (gradient plan order:
+    // forward 0..K-2, turnaround K-1, reverse of pass i at index 2K-2-i)
+    const size_t bytes = amp_bytes(q->dt) << q->n;
+    if (q->ckpt.size() != q->ck_after.size()) {
+      for (void* b : q->ckpt) cudaFree(b);
+      q->ckpt.assign(q->ck_after.size(), nullptr);
+      for (auto& b : q->ckpt) QS_CUDA(cudaMalloc(&b, bytes));
+    }
+    const int K = q->n_fwd + 1;
+    size_t b = 0;
+    for (size_t j = 0; j < q->ck_after.size(); ++j) {
+      const size_t e = (size_t)q->ck_after[j] + 1;
+      QS_TRY(run_qpasses(q, q->gpass, q->gns, q->d_gpass, psi->ptr, lam->ptr, d_part, st, b, e));
+      QS_CUDA(cudaMemcpyAsync(q->ckpt[j], psi->ptr, bytes, cudaMemcpyDeviceToDevice, st));
+      b = e;
+    }
+    for (size_t jj = q->ck_after.size(); jj-- > 0;) {
+      const size_t e = (size_t)(2 * K - 2 - q->ck_after[jj]);
+      QS_TRY(run_qpasses(q, q->gpass, q->gns, q->d_gpass, psi->ptr, lam->ptr, d_part, st, b, e));
+      if (q->il) {
+        const uint64_t N = 1ull << q->n;
+        const int grid = (int)std::min<uint64_t>((N + 255) / 256, 152 * 16);
+        il_reload_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<float4*>(lam->ptr),
+                                               reinterpret_cast<float4*>(q->d_il_priv), N / 2,
+                                               reinterpret_cast<const float2*>(q->ckpt[jj]), N);
+        QS_CUDA(cudaGetLastError());
+      } else {
+        QS_CUDA(cudaMemcpyAsync(psi->ptr, q->ckpt[jj], bytes, cudaMemcpyDeviceToDevice, st));
+      }
+      b = e;
+    }
+    QS_TRY(run_qpasses(q, q->gpass, q->gns, q->d_gpass, psi->ptr, lam->ptr, d_part, st, b, q->gpass.size()));
+  }
   QS_TRY(launch_reduce_slots(d_part, n_slots, q->grid2, nullptr, d_slot, st));
   QS_TRY(launch_param_gather(d_slot, q->g_row, q->g_sidx, q->g_w, n_out, d_out, st));
   std::vector<double> h(n_out);

@@ -111,7 +111,7 @@ class QSimError(RuntimeError):
 
 
 class Options(C.Structure):
-    _fields_ = [("fuse", C.c_int), ("tile_bits", C.c_int), ("low_bits", C.c_int)]
+    _fields_ = [("fuse", C.c_int), ("tile_bits", C.c_int), ("low_bits", C.c_int), ("checkpoint", C.c_int)]
 
 
 _lib = None
@@ -245,8 +245,9 @@ class Circuit:
         _check(lib().qs_circuit_add(self.h, KIND[kind], t, len(targets), c, len(ctrls), param, coef, const, m))
         return self
 
-    def finalize(self, dtype: int = C64, fuse: int = 0, tile_bits: int = 0, low_bits: int = 0):
-        o = Options(fuse, tile_bits, low_bits)
+    def finalize(self, dtype: int = C64, fuse: int = 0, tile_bits: int = 0, low_bits: int = 0, checkpoint: int = 0):
+        """checkpoint > 0: adjoint state checkpoints every `checkpoint` gates."""
+        o = Options(fuse, tile_bits, low_bits, checkpoint)
         _check(lib().qs_circuit_finalize(self.h, dtype, C.byref(o)))
         return self
 
@@ -264,7 +265,7 @@ class Circuit:
         """Pick the tile shape by timing (qs_circuit_autotune); overwrites `state`.
         Returns {"tile_bits", "low_bits", "ms"}."""
         pr = np.ascontiguousarray(params if params is not None else np.zeros(0), dtype=np.float64)
-        o = Options(0, 0, 0)
+        o = Options(0, 0, 0, 0)
         ms = C.c_double()
         _check(lib().qs_circuit_autotune(self.h, state.h, _dptr(pr) if pr.size else None, int(pr.size), reps,
                                          C.byref(o), C.byref(ms)))
@@ -660,11 +661,12 @@ class QAOA:
     """MaxCut QAOA engine: |+>^n, p layers of exp(-i gs gamma C) then RX(beta)."""
 
     def __init__(self, n: int, edges, p: int, gamma_scale: float = 1.0, dtype: int = C64,
-                 tile_bits: int = 0, low_bits: int = 0):
+                 tile_bits: int = 0, low_bits: int = 0, checkpoint: int = 0):
+        """checkpoint > 0: adjoint state checkpoints every `checkpoint` layers."""
         self.n, self.p, self.dtype = n, p, dtype
         e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
         self._edges = e
-        o = Options(0, tile_bits, low_bits)
+        o = Options(0, tile_bits, low_bits, checkpoint)
         h = C.c_void_p()
         _check(lib().qs_qaoa_create(n, e.ctypes.data_as(_PI), int(e.size // 2), p, gamma_scale, dtype,
                                     C.byref(o), C.byref(h)))

@@ -236,7 +236,8 @@ def run_ours(args, ws, rank, local):
         from paper_2406_17248_gb300 import inputs as I
         a = I.uniform_params(2 * p, 1000 + rank, 0.0, float(np.pi))
         gam, bet = a[:p], a[p:]
-    q = Q.QAOA(n, edges, p, gamma_scale=0.5, dtype=Q.C64, tile_bits=args.tile_bits, low_bits=args.low_bits)
+    q = Q.QAOA(n, edges, p, gamma_scale=0.5, dtype=Q.C64, tile_bits=args.tile_bits, low_bits=args.low_bits,
+               checkpoint=args.checkpoint)
     info = q.info()
     psi, lam = Q.State(n, Q.C64), Q.State(n, Q.C64)
     stream = torch.cuda.current_stream()
@@ -1069,6 +1070,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="default workload: skip the gate sweep and batch lines")
     ap.add_argument("--block-k", type=int, default=5)
     ap.add_argument("--gate-dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--checkpoint", type=int, default=0, help="QAOA: adjoint state checkpoints every K layers")
     args = ap.parse_args()
     if args.workload == "batch":
         return run_batch_workload(args)

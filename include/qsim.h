@@ -443,6 +443,11 @@ QS_API qs_status qs_gnn_set_weights(qs_gnn* g, const float* w, int on_device);
 /* Copy out the float32 master weights and/or their bfloat16 bit patterns
  * (either pointer may be NULL).  Host copies synchronise the stream. */
 QS_API qs_status qs_gnn_get_weights(qs_gnn* g, float* w, uint16_t* w_bf16, int on_device);
+/* Training state for checkpoint/resume: the float32 master weights, the Adam
+ * moments m and v (host float[n_weights] each) and the Adam step count.  get
+ * synchronises the stream; set re-forms the bfloat16 copy and synchronises. */
+QS_API qs_status qs_gnn_get_state(qs_gnn* g, float* w, float* m, float* v, int* step);
+QS_API qs_status qs_gnn_set_state(qs_gnn* g, const float* w, const float* m, const float* v, int step);
 /* dev_out[g * out_dim + o] = y_o of graph g, device float32.  Asynchronous. */
 QS_API qs_status qs_gnn_forward(qs_gnn* g, const qs_graphs* graphs, float* dev_out);
 /* dev_grad[n_weights] = sum over graphs of dL/dw given dev_dout[g * out_dim + o]
@@ -492,6 +497,15 @@ QS_API qs_status qs_adam_f64(int n, double* dev_w, double* dev_m, double* dev_v,
 QS_API qs_status qs_expectation_noalloc(const void* dev_psi, int n_qubits, qs_dtype dtype, int n_terms,
                                         const uint64_t* xmask, const uint64_t* zmask, const double* coef,
                                         void* cuda_stream, double* energy);
+
+/* ------------------------------------------------------- failure detection */
+
+/* Self-test of the bounded device-side waits (the tensor-core kernel's MMA
+ * completion wait): one CTA polls an mbarrier that nothing arrives on, a bounded
+ * number of times, and gives up with nothing in flight.  Returns
+ * QS_ERR_TIMEOUT with *timed_out = 1 (the expected outcome); the context stays
+ * usable.  Synchronises the device. */
+QS_API qs_status qs_selftest_wait_timeout(int* timed_out);
 
 /* ----------------------------------------------------------------- tracing */
 

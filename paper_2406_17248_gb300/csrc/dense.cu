@@ -364,6 +364,26 @@ qs_status launch_tc(float2* psi, const DenseGeom& G, const double2* dU, int* d_e
 
 }  // namespace
 
+// Self-test of the bounded-wait path the tensor-core kernel relies on: one CTA
+// polls an mbarrier that nothing arrives on, `limit` times, then records the
+// timeout.  No asynchronous work is in flight, so giving up leaves nothing behind.
+__global__ void wait_selftest_kernel(long long limit, int* status) {
+  __shared__ __align__(8) uint64_t mbar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  bool ok = false;
+  for (long long it = 0; it < limit; ++it)
+    if (mbar_try_wait(smem_u32(&mbar), 0)) {
+      ok = true;
+      break;
+    }
+  __syncthreads();
+  if (threadIdx.x == 0) *status = ok ? 0 : 1;
+}
+
 extern "C" {
 
 qs_status qs_apply_matrix(qs_state* s, int k, const int* targets, const double* matrix, int engine) {
@@ -437,6 +457,25 @@ qs_status qs_apply_matrix(qs_state* s, int k, const int* targets, const double* 
     rec->bytes = 2.0 * (double)amp_bytes(s->dt) * (double)(1ull << s->ne);
     rec->kind = QS_TRACE_DENSE_CC;
     QS_CUDA(cudaEventRecord(rec->end, s->st));
+  }
+  return QS_OK;
+}
+
+qs_status qs_selftest_wait_timeout(int* timed_out) {
+  QS_CHECK(timed_out != nullptr, "null argument");
+  int* d = nullptr;
+  QS_CUDA(cudaMalloc(&d, sizeof(int)));
+  QS_CUDA(cudaMemset(d, 0xff, sizeof(int)));
+  wait_selftest_kernel<<<1, 32>>>(1 << 16, d);
+  cudaError_t e = cudaGetLastError();
+  int h = -1;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  QS_CUDA(e);
+  *timed_out = h;
+  if (h == 1) {
+    set_error("bounded wait ran out (self-test)");
+    return QS_ERR_TIMEOUT;
   }
   return QS_OK;
 }

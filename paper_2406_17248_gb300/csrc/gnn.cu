@@ -690,6 +690,32 @@ qs_status qs_gnn_get_weights(qs_gnn* g, float* w, uint16_t* w_bf16, int on_devic
   return QS_OK;
 }
 
+qs_status qs_gnn_get_state(qs_gnn* g, float* w, float* m, float* v, int* step) {
+  QS_CHECK(g != nullptr && w != nullptr && m != nullptr && v != nullptr && step != nullptr, "null argument");
+  const size_t bytes = (size_t)g->D.P * 4;
+  QS_CUDA(cudaMemcpyAsync(w, g->d_w, bytes, cudaMemcpyDeviceToHost, g->st));
+  QS_CUDA(cudaMemcpyAsync(m, g->d_m, bytes, cudaMemcpyDeviceToHost, g->st));
+  QS_CUDA(cudaMemcpyAsync(v, g->d_v, bytes, cudaMemcpyDeviceToHost, g->st));
+  QS_CUDA(cudaStreamSynchronize(g->st));
+  *step = g->step;
+  return QS_OK;
+}
+
+qs_status qs_gnn_set_state(qs_gnn* g, const float* w, const float* m, const float* v, int step) {
+  QS_CHECK(g != nullptr && w != nullptr && m != nullptr && v != nullptr, "null argument");
+  QS_CHECK(step >= 0, "step must be >= 0");
+  const int P = g->D.P;
+  const size_t bytes = (size_t)P * 4;
+  QS_CUDA(cudaMemcpyAsync(g->d_w, w, bytes, cudaMemcpyHostToDevice, g->st));
+  QS_CUDA(cudaMemcpyAsync(g->d_m, m, bytes, cudaMemcpyHostToDevice, g->st));
+  QS_CUDA(cudaMemcpyAsync(g->d_v, v, bytes, cudaMemcpyHostToDevice, g->st));
+  to_bf16_kernel<<<blocks_for(P, 256), 256, 0, g->st>>>(P, g->d_w, g->d_wb);
+  QS_CUDA(cudaGetLastError());
+  QS_CUDA(cudaStreamSynchronize(g->st));
+  g->step = step;
+  return QS_OK;
+}
+
 qs_status qs_gnn_forward(qs_gnn* g, const qs_graphs* graphs, float* dev_out) {
   QS_CHECK(g != nullptr && graphs != nullptr, "null argument");
   QS_CHECK(graphs->n_graphs == 0 || dev_out != nullptr, "null output");

@@ -92,6 +92,8 @@ SIGNATURES = [
     ("qs_gnn_destroy", [_VP]),
     ("qs_gnn_set_weights", [_VP, _VP, _I]),
     ("qs_gnn_get_weights", [_VP, _VP, _VP, _I]),
+    ("qs_gnn_get_state", [_VP, _VP, _VP, _VP, _PI]),
+    ("qs_gnn_set_state", [_VP, _VP, _VP, _VP, _I]),
     ("qs_gnn_forward", [_VP, _VP, _VP]),
     ("qs_gnn_backward", [_VP, _VP, _VP, _VP]),
     ("qs_gnn_adam_step", [_VP, _VP, C.c_float, C.c_float, C.c_float, C.c_float]),
@@ -99,6 +101,7 @@ SIGNATURES = [
     ("qs_mse", [_I, _VP, _VP, _VP, _VP, _VP]),
     ("qs_adam_f64", [_I, _VP, _VP, _VP, _VP, _I, _D, _D, _D, _D, _I, _VP]),
     ("qs_expectation_noalloc", [_VP, _I, _I, _I, _PU64, _PU64, _PD, _VP, _PD]),
+    ("qs_selftest_wait_timeout", [_PI]),
     ("qs_trace_enable", [_I]),
     ("qs_trace_read", [_I, _PI, _PD, _PD, _PI]),
 ]
@@ -795,6 +798,24 @@ class GNN:
             if w.numel() != self.n_weights:
                 raise ValueError("wrong number of weights")
             _check(lib().qs_gnn_set_weights(self.h, _dev(w), 1))
+
+    def save(self, path: str):
+        """Checkpoint the training state (weights, Adam moments, step) to an .npz file."""
+        w, m, v = (np.zeros(self.n_weights, dtype=np.float32) for _ in range(3))
+        step = C.c_int()
+        _check(lib().qs_gnn_get_state(self.h, w.ctypes.data_as(C.c_void_p), m.ctypes.data_as(C.c_void_p),
+                                      v.ctypes.data_as(C.c_void_p), C.byref(step)))
+        np.savez(path, w=w, m=m, v=v, step=step.value,
+                 dims=np.array([self.hidden, self.layers, self.out_dim], dtype=np.int64))
+
+    def load(self, path: str):
+        """Resume from a file written by save() (same dimensions)."""
+        z = np.load(path)
+        if tuple(int(x) for x in z["dims"]) != (self.hidden, self.layers, self.out_dim):
+            raise ValueError("checkpoint dimensions differ from this network's")
+        arrs = [np.ascontiguousarray(z[k], dtype=np.float32) for k in ("w", "m", "v")]
+        _check(lib().qs_gnn_set_state(self.h, *(a.ctypes.data_as(C.c_void_p) for a in arrs), int(z["step"])))
+        return self
 
     def get_weights(self):
         """(float32 master weights, bfloat16 bit patterns as uint16) on the host."""

@@ -253,3 +253,31 @@ def test_fused_train_step_equals_separate_calls(Q):
     y_or = G.forward(_bf16_bits_to_f64(wbc), *I.pack_graphs(graphs))
     l_or, _ = G.mse(y_or, targets.astype(np.float64))
     assert abs(loss_a.item() - l_or) <= 1e-4 * l_or
+
+
+def test_training_state_checkpoint_and_resume(Q, tmp_path):
+    """save() after three steps, then three more steps, equals load() into a fresh
+    network followed by the same three steps, bit for bit (weights, bfloat16
+    copy and Adam moments restored with the step count)."""
+    dims = dict(hidden=64, layers=3, out_dim=8)
+    w0 = _random_weights(5, **dims)
+    graphs = I.graph_set(24, 13, (6, 26))
+    targets = np.random.default_rng(3).normal(size=(len(graphs), 8)).astype(np.float32)
+    gb = Q.Graphs.from_graphs(graphs)
+    t = torch.as_tensor(targets).cuda()
+    a = Q.GNN(64, 3, 8)
+    a.set_weights(w0)
+    for _ in range(3):
+        a.train_step(gb, t, 1e-3)
+    path = str(tmp_path / "gnn.npz")
+    a.save(path)
+    for _ in range(3):
+        a.train_step(gb, t, 1e-3)
+    b = Q.GNN(64, 3, 8).load(path)
+    for _ in range(3):
+        b.train_step(gb, t, 1e-3)
+    wa, wba = a.get_weights()
+    wb_, wbb = b.get_weights()
+    assert np.array_equal(wa, wb_) and np.array_equal(wba, wbb)
+    with pytest.raises(ValueError):
+        Q.GNN(32, 3, 8).load(path)

@@ -455,12 +455,15 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? QS_TILE_C64_MIN
             case OP_GRADDIAG: {
               const bool g0 = op.dglb[0] >= 0 && ((toff >> op.dglb[0]) & 1ull);
               const bool g1 = op.dglb[1] >= 0 && ((toff >> op.dglb[1]) & 1ull);
+              // the four diagonal entries (every diagonal op's block has four
+              // slots) in registers: a select per amplitude, not a load
+              const V D0 = M[0], D1 = M[1], D2 = M[2], D3 = M[3];
 #pragma unroll
               for (int j = 0; j < RN; ++j) {
                 if (!(ok && ((uint32_t)j & jc) == jc)) continue;
                 const uint32_t b0 = op.dloc[0] >= 0 ? (TLOC(j) >> op.dloc[0]) & 1u : (uint32_t)g0;
                 const uint32_t b1 = op.dloc[1] >= 0 ? (TLOC(j) >> op.dloc[1]) & 1u : (uint32_t)g1;
-                const V d = M[b0 + 2 * b1];
+                const V d = b1 ? (b0 ? D3 : D2) : (b0 ? D1 : D0);
                 if (op.type == OP_DIAG) {
                   a[j] = cmul(d, a[j]);
                   if (NS == 2 && (op.flags & OPF_LAM)) b[j] = cmul(d, b[j]);

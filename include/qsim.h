@@ -350,6 +350,14 @@ QS_API qs_status qs_qaoa_expectation(qs_qaoa* q, qs_state* psi, const double* ga
 QS_API qs_status qs_qaoa_expectation_with_grad(qs_qaoa* q, qs_state* psi, qs_state* lam, const double* gamma,
                                         const double* beta, double* energy, double* dgamma, double* dbeta);
 
+/* One evaluation without handles, in the shape of the QuPack QAOA call (§6.2):
+ * graph, depth and angles in; energy and gradients out (host arrays of p
+ * doubles).  Creates the engine and two library-owned states on the legacy
+ * default stream and frees them before returning; synchronises. */
+QS_API qs_status qs_qaoa_evaluate(int n_qubits, const int* edges, int n_edges, int p, double gamma_scale,
+                                  const double* gamma, const double* beta, qs_dtype dtype, double* energy,
+                                  double* dgamma, double* dbeta);
+
 /* ----------------------------------------------------------------- batches */
 
 /* Many independent instances (circuit, Hamiltonian, parameters) evaluated

@@ -737,4 +737,19 @@ qs_status qs_qaoa_expectation_with_grad(qs_qaoa* q, qs_state* psi, qs_state* lam
   return QS_OK;
 }
 
+qs_status qs_qaoa_evaluate(int n_qubits, const int* edges, int n_edges, int p, double gamma_scale,
+                           const double* gamma, const double* beta, qs_dtype dtype, double* energy, double* dgamma,
+                           double* dbeta) {
+  qs_qaoa* q = nullptr;
+  qs_state *psi = nullptr, *lam = nullptr;
+  qs_status s = qs_qaoa_create(n_qubits, edges, n_edges, p, gamma_scale, dtype, nullptr, &q);
+  if (s == QS_OK) s = qs_state_create(n_qubits, dtype, nullptr, 0, nullptr, &psi);
+  if (s == QS_OK) s = qs_state_create(n_qubits, dtype, nullptr, 0, nullptr, &lam);
+  if (s == QS_OK) s = qs_qaoa_expectation_with_grad(q, psi, lam, gamma, beta, energy, dgamma, dbeta);
+  qs_state_destroy(lam);
+  qs_state_destroy(psi);
+  qs_qaoa_destroy(q);
+  return s;
+}
+
 }  // extern "C"

@@ -80,6 +80,7 @@ SIGNATURES = [
     ("qs_qaoa_evolve", [_VP, _VP, _PD, _PD]),
     ("qs_qaoa_expectation", [_VP, _VP, _PD, _PD, _PD]),
     ("qs_qaoa_expectation_with_grad", [_VP, _VP, _VP, _PD, _PD, _PD, _PD, _PD]),
+    ("qs_qaoa_evaluate", [_I, _PI, _I, _I, _D, _PD, _PD, _I, _PD, _PD, _PD]),
     ("qs_batch_create", [_I, _PI, _PI, _VP, _PI, _PU64, _PU64, _PD, _PI, _I, _VP, _PVP]),
     ("qs_batch_destroy", [_VP]),
     ("qs_batch_info", [_VP, _PI, _PI, _PI]),
@@ -659,6 +660,18 @@ def trace_read(max_records: int = 65536):
 
 
 # --------------------------------------------------------------------------- QAOA
+
+def qaoa_evaluate(n: int, edges, p: int, gamma, beta, gamma_scale: float = 1.0, dtype: int = C64):
+    """One energy + gradient evaluation without handles (qs_qaoa_evaluate)."""
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    E = C.c_double()
+    dg, db = np.zeros(p), np.zeros(p)
+    _check(lib().qs_qaoa_evaluate(n, e.ctypes.data_as(_PI), int(e.size // 2), p, gamma_scale, _dptr(g), _dptr(b),
+                                  dtype, C.byref(E), _dptr(dg), _dptr(db)))
+    return E.value, dg, db
+
 
 class QAOA:
     """MaxCut QAOA engine: |+>^n, p layers of exp(-i gs gamma C) then RX(beta)."""

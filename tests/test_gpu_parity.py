@@ -322,3 +322,16 @@ def test_autotuned_plan_stays_exact(Q, dt):
     E, G = Q.expectation_with_grad(psi, lam, c, Q.Hamiltonian(ham), params)
     E0, G0 = O.adjoint_gradient(circ, ham, params, O.zero_state(n))
     assert abs(E - E0) <= TOL[dt] * scale(ham) and np.max(np.abs(G - G0)) <= TOL[dt] * scale(ham)
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_qaoa_one_shot_call_reproduces_printed_qupack_values(Q, dt):
+    """qs_qaoa_evaluate (no handles, the shape of the QuPack call of §6.2) on the
+    paper's K5 depth-10 example: the printed expectation and 20 gradients."""
+    g = json.load(open(os.path.join(GOLD, "qupack_qaoa_k5.json")))
+    n, p = g["n_qubits"], g["depth"]
+    E, dg, db = Q.qaoa_evaluate(n, I.complete_graph(n), p, [g["gamma"]] * p, [g["beta"]] * p, 1.0, dt)
+    tol = TOL[dt] * 10 * p
+    assert abs(E - g["expectation"]) < tol
+    assert np.abs(dg - np.array(g["gamma_grad"])).max() < tol
+    assert np.abs(db - np.array(g["beta_grad"])).max() < tol

@@ -106,6 +106,20 @@ __device__ __forceinline__ uint32_t off_of(const uint32_t (&rm)[kRegBits]) {
   return o;
 }
 
+// 16-bit pattern over the register index j of one diagonal bit: local bit
+// `dloc` (-1: the bit is outside the tile, with value g).  A local bit held in
+// register bit i gives the fixed pattern of bit i of j; any other local bit is
+// constant for the thread's sub-cube (all ones or all zeros).
+__device__ __forceinline__ uint32_t diag_pattern(int dloc, bool g, uint32_t l0, const uint32_t (&rm)[kRegBits]) {
+  if (dloc < 0) return g ? 0xFFFFu : 0u;
+  const uint32_t bit = 1u << dloc;
+  constexpr uint32_t kPat[4] = {0xAAAAu, 0xCCCCu, 0xF0F0u, 0xFF00u};
+#pragma unroll
+  for (int i = 0; i < kRegBits; ++i)
+    if (rm[i] == bit) return kPat[i];
+  return (l0 & bit) ? 0xFFFFu : 0u;
+}
+
 // JC: the op has controls among the register bits (mask jc over the register
 // index); without them the whole loop is predicated by `ok` alone.
 template <class V, int RB, bool JC>
@@ -458,17 +472,50 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? QS_TILE_C64_MIN
               // the four diagonal entries (every diagonal op's block has four
               // slots) in registers: a select per amplitude, not a load
               const V D0 = M[0], D1 = M[1], D2 = M[2], D3 = M[3];
+              // complex64 (ALU-bound): each diagonal bit as a pattern over the
+              // register index j -- a register bit varies with j, any other bit is
+              // constant here, and with both constant one factor serves all j;
+              // complex128 (FP64-bound) measured faster with per-j bit extraction
+              const uint32_t P0 = diag_pattern(op.dloc[0], g0, l0, rm);
+              const uint32_t P1 = diag_pattern(op.dloc[1], g1, l0, rm);
+              if (sizeof(T) == 8) {
 #pragma unroll
-              for (int j = 0; j < RN; ++j) {
-                if (!(ok && ((uint32_t)j & jc) == jc)) continue;
-                const uint32_t b0 = op.dloc[0] >= 0 ? (TLOC(j) >> op.dloc[0]) & 1u : (uint32_t)g0;
-                const uint32_t b1 = op.dloc[1] >= 0 ? (TLOC(j) >> op.dloc[1]) & 1u : (uint32_t)g1;
-                const V d = b1 ? (b0 ? D3 : D2) : (b0 ? D1 : D0);
-                if (op.type == OP_DIAG) {
-                  a[j] = cmul(d, a[j]);
-                  if (NS == 2 && (op.flags & OPF_LAM)) b[j] = cmul(d, b[j]);
-                } else if (NS == 2) {
-                  contrib += 2 * re_conj_mul(b[j], cmul(d, a[j]));
+                for (int j = 0; j < RN; ++j) {
+                  if (!(ok && ((uint32_t)j & jc) == jc)) continue;
+                  const uint32_t b0 = op.dloc[0] >= 0 ? (TLOC(j) >> op.dloc[0]) & 1u : (uint32_t)g0;
+                  const uint32_t b1 = op.dloc[1] >= 0 ? (TLOC(j) >> op.dloc[1]) & 1u : (uint32_t)g1;
+                  const V d = b1 ? (b0 ? D3 : D2) : (b0 ? D1 : D0);
+                  if (op.type == OP_DIAG) {
+                    a[j] = cmul(d, a[j]);
+                    if (NS == 2 && (op.flags & OPF_LAM)) b[j] = cmul(d, b[j]);
+                  } else if (NS == 2) {
+                    contrib += 2 * re_conj_mul(b[j], cmul(d, a[j]));
+                  }
+                }
+              } else if ((P0 == 0u || P0 == 0xFFFFu) && (P1 == 0u || P1 == 0xFFFFu)) {
+                const V d = P1 ? (P0 ? D3 : D2) : (P0 ? D1 : D0);  // one factor for all
+#pragma unroll
+                for (int j = 0; j < RN; ++j) {
+                  if (!(ok && ((uint32_t)j & jc) == jc)) continue;
+                  if (op.type == OP_DIAG) {
+                    a[j] = cmul(d, a[j]);
+                    if (NS == 2 && (op.flags & OPF_LAM)) b[j] = cmul(d, b[j]);
+                  } else if (NS == 2) {
+                    contrib += 2 * re_conj_mul(b[j], cmul(d, a[j]));
+                  }
+                }
+              } else {
+#pragma unroll
+                for (int j = 0; j < RN; ++j) {
+                  if (!(ok && ((uint32_t)j & jc) == jc)) continue;
+                  const bool b0 = (P0 >> j) & 1u, b1 = (P1 >> j) & 1u;
+                  const V d = b1 ? (b0 ? D3 : D2) : (b0 ? D1 : D0);
+                  if (op.type == OP_DIAG) {
+                    a[j] = cmul(d, a[j]);
+                    if (NS == 2 && (op.flags & OPF_LAM)) b[j] = cmul(d, b[j]);
+                  } else if (NS == 2) {
+                    contrib += 2 * re_conj_mul(b[j], cmul(d, a[j]));
+                  }
                 }
               }
               has_contrib = op.type == OP_GRADDIAG;

@@ -421,6 +421,10 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? QS_TILE_C64_MIN
         for (int o = PH.op_begin; o < PH.op_end; ++o) {
           const DevOp op = ops_staged ? s_ops[o - op_lo] : args.ops[o];
           const bool ok = active && ((l0 & op.lc) == op.lc) && ((toff & op.gc) == op.gc);
+          // an op that only transforms amplitudes is skipped outright where it
+          // does not apply (ops with sums keep every lane for the warp shuffle)
+          if (!ok && op.type <= OP_RX) continue;
+          if (!ok && (op.type == OP_X || op.type == OP_COST)) continue;
           const uint32_t jc = op.jc;
           const V* M = coef + op.coef;
           T contrib = 0;

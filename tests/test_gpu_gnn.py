@@ -288,7 +288,7 @@ def test_learned_initialiser_gains_over_linear_ramp(Q):
     simulator (batched engine), the network trained by its own kernels, then on
     held-out larger graphs the network's angles start closer to the optimum than
     the plain linear-ramp initialisation (the fallback) and reach ratio 0.9 in
-    fewer Adam steps, with the simulator's energy as the judge."""
+    fewer Adam steps, the simulator's energy deciding the ratio."""
     from paper_2406_17248_gb300.qaoa_init import Initialiser, linear_ramp, optimised_angles, steps_to_ratio
     p = 4
     train = I.graph_set(1024, 5, (10, 12))

@@ -216,7 +216,55 @@ __device__ __forceinline__ V lin2f(V m0, V a, V m1, V b) {
   return r;
 }
 
+// Exact product i^k a (k = 0..3): a swap of the components and sign-bit flips,
+// done on the integer pipe (complex128 gates whose entries are 0, +-1 or +-i
+// then need no FP64 arithmetic, which bounds the other complex128 kernels).
+__device__ __forceinline__ double flip_sign(double v, uint32_t neg) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
+}
+__device__ __forceinline__ float flip_sign(float v, uint32_t neg) {
+  return __int_as_float(__float_as_int(v) ^ (int)(neg << 31));
+}
+template <class V>
+__device__ __forceinline__ V mul_ik(uint32_t k, V a) {
+  V r;
+  r.x = flip_sign((k & 1u) ? a.y : a.x, ((k + 1u) >> 1) & 1u);  // k = 1, 2: -
+  r.y = flip_sign((k & 1u) ? a.x : a.y, (k >> 1) & 1u);         // k = 2, 3: -
+  return r;
+}
+
+// Anti-diagonal gate with entries i^k01 (row 0) and i^k10 (row 1): X, Y and
+// their controlled forms move amplitudes without arithmetic.
+template <class T>
+__global__ void gate1_perm_kernel(typename V2<T>::V* __restrict__ psi, uint64_t items, int t, FixedBits F,
+                                  uint32_t k01, uint32_t k10) {
+  using V = typename V2<T>::V;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t Tb = 1ull << t;
+  for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < items; i0 += stride * kGateUnroll) {
+    V a[kGateUnroll], b[kGateUnroll];
+    uint64_t x[kGateUnroll];
+#pragma unroll
+    for (int u = 0; u < kGateUnroll; ++u) {
+      const uint64_t i = i0 + u * stride;
+      x[u] = i < items ? deposit(i, F) : 0;
+      if (i < items) {
+        a[u] = __ldcs(psi + x[u]);
+        b[u] = __ldcs(psi + (x[u] | Tb));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kGateUnroll; ++u) {
+      if (i0 + u * stride >= items) continue;
+      __stcs(psi + x[u], mul_ik(k01, b[u]));
+      __stcs(psi + (x[u] | Tb), mul_ik(k10, a[u]));
+    }
+  }
+}
+
 // One pair per item (complex128, or complex64 with bit 0 fixed by a control).
+// FORM 3: [[h, h], [h, -h]] with real h (Hadamard): the product h b is shared
+// by both outputs, 3 instead of 4 operations per component.
 template <class T, int FORM>
 __global__ void gate1_pair_kernel(typename V2<T>::V* __restrict__ psi, uint64_t items, int t, FixedBits F,
                                   typename V2<T>::V m00, typename V2<T>::V m01, typename V2<T>::V m10,
@@ -239,8 +287,21 @@ __global__ void gate1_pair_kernel(typename V2<T>::V* __restrict__ psi, uint64_t 
 #pragma unroll
     for (int u = 0; u < kGateUnroll; ++u) {
       if (i0 + u * stride >= items) continue;
-      __stcs(psi + x[u], lin2f<FORM>(m00, a[u], m01, b[u]));
-      __stcs(psi + (x[u] | Tb), lin2f<FORM>(m11, b[u], m10, a[u]));
+      if constexpr (FORM == 3) {
+        const T h = m00.x;
+        V hb, y0, y1;
+        hb.x = h * b[u].x;
+        hb.y = h * b[u].y;
+        y0.x = fma(h, a[u].x, hb.x);
+        y0.y = fma(h, a[u].y, hb.y);
+        y1.x = fma(h, a[u].x, -hb.x);
+        y1.y = fma(h, a[u].y, -hb.y);
+        __stcs(psi + x[u], y0);
+        __stcs(psi + (x[u] | Tb), y1);
+      } else {
+        __stcs(psi + x[u], lin2f<FORM>(m00, a[u], m01, b[u]));
+        __stcs(psi + (x[u] | Tb), lin2f<FORM>(m11, b[u], m10, a[u]));
+      }
     }
   }
 }
@@ -286,6 +347,41 @@ __global__ void diag_fast_kernel(typename V2<T>::V* __restrict__ psi, uint64_t i
       }
     }
   }
+}
+
+// Diagonal whose entries are all powers of i (Z, S, CZ ...): amplitude x gets
+// i^k with k = bits 2b..2b+1 of `codes`, b = bit t0 + 2 bit t1 of x.
+template <class T>
+__global__ void diag_unit_kernel(typename V2<T>::V* __restrict__ psi, uint64_t items, int nt, int t0, int t1,
+                                 FixedBits F, uint32_t codes) {
+  using V = typename V2<T>::V;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < items; i0 += stride * kGateUnroll) {
+    uint64_t x[kGateUnroll];
+    V a[kGateUnroll];
+#pragma unroll
+    for (int u = 0; u < kGateUnroll; ++u) {
+      const uint64_t i = i0 + u * stride;
+      x[u] = i < items ? deposit(i, F) : 0;
+      if (i < items) a[u] = __ldcs(psi + x[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kGateUnroll; ++u) {
+      if (i0 + u * stride >= items) continue;
+      uint32_t b = (uint32_t)((x[u] >> t0) & 1);
+      if (nt == 2) b |= (uint32_t)((x[u] >> t1) & 1) << 1;
+      __stcs(psi + x[u], mul_ik((codes >> (2 * b)) & 3u, a[u]));
+    }
+  }
+}
+
+// k with (re, im) = i^k exactly, else -1.
+int unit_code(double re, double im) {
+  if (im == 0.0 && re == 1.0) return 0;
+  if (re == 0.0 && im == 1.0) return 1;
+  if (im == 0.0 && re == -1.0) return 2;
+  if (re == 0.0 && im == -1.0) return 3;
+  return -1;
 }
 
 int gate_grid(uint64_t work) {
@@ -730,7 +826,16 @@ qs_status launch_gate_dense(qs_dtype dt, void* psi, int n, int nt, const int* t,
         // complex128 is bound by the FP64 rate: use the cheapest form the matrix allows
         const bool real = mat[1] == 0 && mat[3] == 0 && mat[5] == 0 && mat[7] == 0;
         const bool rxf = mat[1] == 0 && mat[7] == 0 && mat[2] == 0 && mat[4] == 0;
-        if (real)
+        const bool hada = real && mat[0] == mat[2] && mat[0] == mat[4] && mat[6] == -mat[0];
+        const int k01 = unit_code(mat[2], mat[3]), k10 = unit_code(mat[4], mat[5]);
+        const bool perm = mat[0] == 0 && mat[1] == 0 && mat[6] == 0 && mat[7] == 0 && k01 >= 0 && k10 >= 0;
+        if (perm)
+          gate1_perm_kernel<double><<<gate_grid(pairs), kThreads, 0, st>>>((double2*)psi, pairs, q, F, (uint32_t)k01,
+                                                                          (uint32_t)k10);
+        else if (hada)
+          gate1_pair_kernel<double, 3><<<gate_grid(pairs), kThreads, 0, st>>>((double2*)psi, pairs, q, F, m00, m01,
+                                                                             m10, m11);
+        else if (real)
           gate1_pair_kernel<double, 1><<<gate_grid(pairs), kThreads, 0, st>>>((double2*)psi, pairs, q, F, m00, m01,
                                                                              m10, m11);
         else if (rxf)
@@ -796,10 +901,19 @@ qs_status launch_gate_diag(qs_dtype dt, void* psi, int n, int nt, const int* t, 
                                                                               d[1], d[2], d[3]);
       } else {
         double2 d[4];
-        for (int i = 0; i < 4; ++i)
+        uint32_t codes = 0;
+        bool unit = true;
+        for (int i = 0; i < 4; ++i) {
           d[i] = i < (1 << nt) ? make_double2(diag[2 * i], diag[2 * i + 1]) : make_double2(1.0, 0.0);
-        diag_fast_kernel<double, false><<<gate_grid(amps), kThreads, 0, st>>>((double2*)psi, amps, nt, t0, t1, F, d[0],
-                                                                             d[1], d[2], d[3]);
+          const int k = unit_code(d[i].x, d[i].y);
+          unit = unit && k >= 0;
+          codes |= (uint32_t)(k < 0 ? 0 : k) << (2 * i);
+        }
+        if (unit)
+          diag_unit_kernel<double><<<gate_grid(amps), kThreads, 0, st>>>((double2*)psi, amps, nt, t0, t1, F, codes);
+        else
+          diag_fast_kernel<double, false><<<gate_grid(amps), kThreads, 0, st>>>((double2*)psi, amps, nt, t0, t1, F,
+                                                                               d[0], d[1], d[2], d[3]);
       }
       QS_CUDA(cudaGetLastError());
       return QS_OK;

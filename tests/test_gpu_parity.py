@@ -335,3 +335,43 @@ def test_qaoa_one_shot_call_reproduces_printed_qupack_values(Q, dt):
     assert abs(E - g["expectation"]) < tol
     assert np.abs(dg - np.array(g["gamma_grad"])).max() < tol
     assert np.abs(db - np.array(g["beta_grad"])).max() < tol
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n_ctrl", [7, 8, 9])
+def test_many_controls_per_gate_kernels(Q, dt, n_ctrl):
+    """Single-gate kernels at the edge of their fixed-bit table (target +
+    controls <= 8 bits take the fast kernels, more fall back to the generic
+    ones): multi-controlled X, RY and phase gates on qubit 0 and qubit 11."""
+    n = 12
+    rng = np.random.default_rng(n_ctrl)
+    gates = [I.Gate("H", (q,)) for q in range(n)]
+    for t in (0, 11):
+        ctrls = tuple(int(c) for c in rng.choice([q for q in range(n) if q != t], n_ctrl, replace=False))
+        gates += [I.Gate("X", (t,), ctrls), I.Gate("RY", (t,), ctrls, const=0.7), I.Gate("PS", (t,), ctrls, const=1.1),
+                  I.Gate("RZ", (t,), ctrls, const=-0.4)]
+    circ = I.Circuit(n, gates)
+    want = O.evolve(circ, [], O.zero_state(n))
+    got, _ = run_circuit(Q, circ, [], dt, fuse=-1)
+    assert np.abs(got - want).max() < TOL[dt]
+
+
+def test_c128_exact_forms_per_gate(Q):
+    """Complex128 gates whose entries are 0, +-1, +-i (X, Y, Z, S, SDG and their
+    controlled forms: swaps and sign flips only) and the Hadamard form, through
+    the per-gate kernels, against the oracle on a random state."""
+    n = 11
+    rng = np.random.default_rng(5)
+    psi0 = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    psi0 /= np.linalg.norm(psi0)
+    gates = []
+    for kind in ("X", "Y", "Z", "S", "SDG", "H"):
+        for t in (0, 1, 6, 10):
+            gates.append(I.Gate(kind, (t,)))
+            c = (t + 3) % n
+            gates.append(I.Gate(kind, (t,), (c,)))
+            gates.append(I.Gate(kind, (t,), (c, (t + 5) % n)))
+    circ = I.Circuit(n, gates)
+    want = O.evolve(circ, [], psi0)
+    got, _ = run_circuit(Q, circ, [], 1, psi0=psi0, fuse=-1)
+    assert np.abs(got - want).max() < 1e-12

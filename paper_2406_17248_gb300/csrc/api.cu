@@ -85,6 +85,13 @@ bool gate_diagonal(int k) {
   }
 }
 
+// Gates whose unitary is real for every angle, and diagonal gates whose entries
+// are all in {1, i, -1, -i}.
+bool real_kind(int k) {
+  return k == QS_GATE_I || k == QS_GATE_X || k == QS_GATE_Z || k == QS_GATE_H || k == QS_GATE_RY;
+}
+bool unit_diag_kind(int k) { return k == QS_GATE_I || k == QS_GATE_Z || k == QS_GATE_S || k == QS_GATE_SDG; }
+
 // Unitary of one gate on its targets (basis index bit(t0) + 2 bit(t1)), row-major.
 // Definitions: §2.3.2 fixed gates, §2.3.3 R_P(theta) = cos(theta/2) I - i sin(theta/2) P.
 void gate_unitary(const HostGate& g, double th, cd* U, int* dim) {
@@ -339,9 +346,14 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
     // keeps them as 2x2 matrices (the extra op cost the issue-bound complex64
     // interpreter more than it saved: 5541 -> 4625), and so does the two-state
     // reverse kernel (its registers are at the limit)
-    const bool rx = g.kind == QS_GATE_RX, x = g.kind == QS_GATE_X && !reverse && dt == QS_C128;
-    const uint8_t apply_type =
-        cls == GC_DENSE1 ? (rx ? OP_RX : x ? OP_X : OP_DENSE1) : cls == GC_DENSE2 ? OP_DENSE2 : OP_DIAG;
+    // For the same reason complex128 forward passes apply real matrices (H, RY)
+    // with real arithmetic and diagonals of +-1, +-i (Z, S, CZ) as sign flips.
+    const bool c128f = !reverse && dt == QS_C128;
+    const bool rx = g.kind == QS_GATE_RX, x = g.kind == QS_GATE_X && c128f;
+    const bool real = c128f && real_kind(g.kind), unit = c128f && unit_diag_kind(g.kind);
+    const uint8_t apply_type = cls == GC_DENSE1   ? (rx ? OP_RX : x ? OP_X : real ? OP_REAL1 : OP_DENSE1)
+                               : cls == GC_DENSE2 ? OP_DENSE2
+                                                  : (unit ? OP_UDIAG : OP_DIAG);
     if (!reverse) {
       it.ops.push_back(ItemOp{apply_type, 0, P.off_u[i], -1, 0.0});
     } else {
@@ -362,8 +374,16 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
     const int r = run_index[i];
     if (r >= 0) {  // the run's product replaces the head gate's op
       it.kind = P.run_diag[r] ? IK_DIAG : IK_DENSE1;
+      // products of real matrices are real, products of i^k are i^k: exactly,
+      // in complex arithmetic (the other parts stay exact zeros)
+      bool real = dt == QS_C128, unit = dt == QS_C128;
+      for (int j : P.runs[r]) {
+        real = real && real_kind(c->gates[j].kind);
+        unit = unit && unit_diag_kind(c->gates[j].kind);
+      }
+      const uint8_t ty = P.run_diag[r] ? (unit ? OP_UDIAG : OP_DIAG) : (real ? OP_REAL1 : OP_DENSE1);
       it.ops.clear();
-      it.ops.push_back(ItemOp{(uint8_t)(P.run_diag[r] ? OP_DIAG : OP_DENSE1), 0, P.run_off[r], -1, 0.0});
+      it.ops.push_back(ItemOp{ty, 0, P.run_off[r], -1, 0.0});
     }
     fwd[seg_of(i)].push_back(it);
   }

@@ -171,6 +171,51 @@ __device__ __forceinline__ void op_x(V (&a)[RN], uint32_t jc, bool ok) {
   }
 }
 
+// 2x2 matrix with real entries (the real parts of M): 4 instead of 8 products per pair.
+template <class V, int RB, bool JC>
+__device__ __forceinline__ void op_real1(V (&a)[RN], const V* M, uint32_t jc, bool ok) {
+  const auto m00 = M[0].x, m01 = M[1].x, m10 = M[2].x, m11 = M[3].x;
+#pragma unroll
+  for (int j = 0; j < RN; ++j) {
+    if (j & (1 << RB)) continue;
+    const int j1 = j | (1 << RB);
+    if (ok && (!JC || ((uint32_t)j & jc) == jc)) {
+      const V x0 = a[j], x1 = a[j1];
+      V y0, y1;
+      y0.x = fmaT(m01, x1.x, m00 * x0.x);
+      y0.y = fmaT(m01, x1.y, m00 * x0.y);
+      y1.x = fmaT(m11, x1.x, m10 * x0.x);
+      y1.y = fmaT(m11, x1.y, m10 * x0.y);
+      a[j] = y0;
+      a[j1] = y1;
+    }
+  }
+}
+
+// Exact product i^k a (k = 0..3): a swap of the components and sign-bit flips
+// on the integer pipe.
+__device__ __forceinline__ double flip_sign(double v, uint32_t neg) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
+}
+__device__ __forceinline__ float flip_sign(float v, uint32_t neg) {
+  return __int_as_float(__float_as_int(v) ^ (int)(neg << 31));
+}
+template <class V>
+__device__ __forceinline__ V mul_ik(uint32_t k, V a) {
+  V r;
+  r.x = flip_sign((k & 1u) ? a.y : a.x, ((k + 1u) >> 1) & 1u);  // k = 1, 2: -
+  r.y = flip_sign((k & 1u) ? a.x : a.y, (k >> 1) & 1u);         // k = 2, 3: -
+  return r;
+}
+
+// k of an entry i^k of a unit diagonal, from its bit pattern (the planner emits
+// OP_UDIAG only for entries that are exactly 1, i, -1 or -i).
+__device__ __forceinline__ uint32_t unit_code_of(double2 d) {
+  const long long one = 0x3FF0000000000000ll, minus_one = (long long)0xBFF0000000000000ull;
+  const long long re = __double_as_longlong(d.x), im = __double_as_longlong(d.y);
+  return re == one ? 0u : im == one ? 1u : re == minus_one ? 2u : 3u;
+}
+
 template <class V, int RB0, int RB1, bool JC>
 __device__ __forceinline__ void op_dense2(V (&a)[RN], const V* M, uint32_t jc, bool ok) {
 #pragma unroll
@@ -424,7 +469,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? QS_TILE_C64_MIN
           // an op that only transforms amplitudes is skipped outright where it
           // does not apply (ops with sums keep every lane for the warp shuffle)
           if (!ok && op.type <= OP_RX) continue;
-          if (!ok && (op.type == OP_X || op.type == OP_COST)) continue;
+          if (!ok && (op.type >= OP_X || op.type == OP_COST)) continue;
           const uint32_t jc = op.jc;
           const V* M = coef + op.coef;
           T contrib = 0;
@@ -445,6 +490,30 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? QS_TILE_C64_MIN
 #define CALL(R) if (jc) { op_x<V, R, true>(a, jc, ok); } else { op_x<V, R, false>(a, jc, ok); }
                 QS_RB_SWITCH(op.rb0, CALL)
 #undef CALL
+              }
+              break;
+            }
+            case OP_REAL1: {  // complex128 one-state passes only (where the planner emits it)
+              if constexpr (NS == 1 && sizeof(T) == 8) {
+#define CALL(R) if (jc) { op_real1<V, R, true>(a, M, jc, ok); } else { op_real1<V, R, false>(a, M, jc, ok); }
+                QS_RB_SWITCH(op.rb0, CALL)
+#undef CALL
+              }
+              break;
+            }
+            case OP_UDIAG: {  // complex128 one-state passes only: entries i^k, no FP64 arithmetic
+              if constexpr (NS == 1 && sizeof(T) == 8) {
+                const bool g0 = op.dglb[0] >= 0 && ((toff >> op.dglb[0]) & 1ull);
+                const bool g1 = op.dglb[1] >= 0 && ((toff >> op.dglb[1]) & 1ull);
+                const uint32_t codes = unit_code_of(M[0]) | (unit_code_of(M[1]) << 2) | (unit_code_of(M[2]) << 4) |
+                                       (unit_code_of(M[3]) << 6);
+#pragma unroll
+                for (int j = 0; j < RN; ++j) {
+                  if (!(ok && ((uint32_t)j & jc) == jc)) continue;
+                  const uint32_t b0 = op.dloc[0] >= 0 ? (TLOC(j) >> op.dloc[0]) & 1u : (uint32_t)g0;
+                  const uint32_t b1 = op.dloc[1] >= 0 ? (TLOC(j) >> op.dloc[1]) & 1u : (uint32_t)g1;
+                  a[j] = mul_ik((codes >> (2 * (b0 | (b1 << 1)))) & 3u, a[j]);
+                }
               }
               break;
             }

@@ -39,7 +39,9 @@ enum OpType : uint8_t {
   OP_COST = 9,      // psi_x *= lut[cut(x)]
   OP_GRADCOST = 10, // acc += C(x) Im(conj(lam_x) psi_x), C = n_edges - 2 cut
   OP_ENERGY = 11,   // acc += C(x) |psi_x|^2 and lam_x = C(x) psi_x
-  OP_X = 12         // X on rb0, complex128 one-state passes: a swap of the amplitude pairs (controls as OP_DENSE1)
+  OP_X = 12,        // X on rb0, complex128 one-state passes: a swap of the amplitude pairs (controls as OP_DENSE1)
+  OP_REAL1 = 13,    // as OP_DENSE1 with real entries (H, RY; complex128 one-state passes): half the FP64 work
+  OP_UDIAG = 14     // as OP_DIAG with entries in {1, i, -1, -i} (Z, S, CZ; complex128 one-state passes): no FP64 work
 };
 
 enum OpFlags : uint8_t { OPF_LAM = 1 };  // apply to lam as well as psi

@@ -375,3 +375,31 @@ def test_c128_exact_forms_per_gate(Q):
     want = O.evolve(circ, [], psi0)
     got, _ = run_circuit(Q, circ, [], 1, psi0=psi0, fuse=-1)
     assert np.abs(got - want).max() < 1e-12
+
+
+@pytest.mark.parametrize("opts", PLAN_OPTS[:5])
+def test_c128_real_and_unit_ops_fused(Q, opts):
+    """Complex128 tile passes with the real-matrix op (H, RY, X, Z runs) and the
+    unit-diagonal op (Z, S, SDG runs, CZ, controlled S), including diagonal and
+    control qubits outside the tile, against the oracle."""
+    n = 14
+    rng = np.random.default_rng(9)
+    psi0 = I.random_state(n, 77)
+    gates = []
+    for _ in range(120):
+        t = int(rng.integers(n))
+        r = rng.random()
+        if r < 0.25:  # a run of real one-qubit gates on t
+            for k in rng.choice(["H", "RY", "X", "Z"], 3):
+                gates.append(I.Gate(str(k), (t,), const=float(rng.uniform(-3, 3)) if k == "RY" else 0.0))
+        elif r < 0.45:  # a run of unit diagonals on t
+            for k in rng.choice(["Z", "S", "SDG"], 3):
+                gates.append(I.Gate(str(k), (t,)))
+        else:
+            c = int((t + 1 + rng.integers(n - 1)) % n)
+            k = str(rng.choice(["H", "RY", "Z", "S", "SDG", "X", "RX"]))
+            gates.append(I.Gate(k, (t,), (c,), const=float(rng.uniform(-3, 3)) if k in ("RY", "RX") else 0.0))
+    circ = I.Circuit(n, gates)
+    want = O.evolve(circ, [], psi0)
+    got, _ = run_circuit(Q, circ, [], 1, psi0, **opts)
+    assert np.abs(got - want).max() < TOL[1]

@@ -284,9 +284,15 @@ QS_API qs_status qs_dm_expectation(const qs_state* rho, const qs_ham* h, double*
  * Flood 2014; the same generator as qs_sample).  The mean of the trajectory
  * energies estimates tr(rho H) of the density-matrix simulator.
  *
- * Each trajectory runs in one CTA's shared memory: n_qubits 1..14 (complex64)
- * or 1..13 (complex128) for energies; with gradients psi and lam both fit:
- * 1..13 and 1..12.  cuda_stream: the engine's stream (NULL: legacy default). */
+ * n_qubits 1..34.  A trajectory runs in one CTA's shared memory while its
+ * state fits (n_qubits <= 14 complex64 or 13 complex128 for energies; with
+ * gradients, psi and lam both: 13 and 12), many trajectories per launch.
+ * Larger states run one trajectory after another on the fused tile passes in
+ * HBM: the gates between damping / Kraus sites are planned once as circuits,
+ * a Pauli / depolarizing site is a one-qubit matrix gate set to the sampled
+ * Pauli, and the weights at a damping / Kraus site come from the qubit's
+ * reduced density matrix (FP64 sums), with the same draws and the same rule.
+ * cuda_stream: the engine's stream (NULL: legacy default). */
 typedef struct qs_traj qs_traj;
 QS_API qs_status qs_traj_create(int n_qubits, qs_dtype dtype, void* cuda_stream, qs_traj** out);
 QS_API qs_status qs_traj_destroy(qs_traj* t);
@@ -314,7 +320,8 @@ QS_API qs_status qs_traj_run(qs_traj* t, const qs_ham* h, const double* params, 
                              unsigned char* choices);
 /* The same on device buffers (d_params double[n_params], d_energies
  * double[n_traj], d_grad_mean double[n_params] or NULL), enqueued on the
- * engine's stream without synchronising. */
+ * engine's stream without synchronising while the state fits in shared
+ * memory; larger states run the host loop above and synchronise. */
 QS_API qs_status qs_traj_run_device(qs_traj* t, const qs_ham* h, const double* d_params, uint64_t seed,
                                     long long first, int n_traj, double* d_energies, double* d_grad_mean);
 /* The final state of trajectory `traj` into `out` (n_qubits, same dtype). */

@@ -112,5 +112,10 @@ size_t traj_smem_bytes(qs_dtype dt, bool grad, int n, int n_gates, int n_params)
 // out[c] = (sum over r of rows[r * n_cols + c]) / n_rows, rows summed in order.
 qs_status launch_row_mean(const double* rows, int n_rows, int n_cols, double* out, cudaStream_t st);
 size_t batch_smem_bytes(qs_dtype dt, int smem_amps, int smem_gates, int smem_params);
+// Reduced density matrix of qubit q of psi (2^n amplitudes): partials[4][grid] =
+// per-CTA FP64 sums of |a0|^2, |a1|^2, Re a0 conj(a1), Im a0 conj(a1) over the
+// pairs (a0, a1) = (psi[x], psi[x | 2^q]).
+qs_status launch_qubit_rdm(qs_dtype dt, const void* psi, int n, int q, double* partials, int grid,
+                           cudaStream_t st);
 
 }  // namespace qs

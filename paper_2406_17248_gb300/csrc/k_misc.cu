@@ -222,9 +222,6 @@ __device__ __forceinline__ V lin2f(V m0, V a, V m1, V b) {
 __device__ __forceinline__ double flip_sign(double v, uint32_t neg) {
   return __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
 }
-__device__ __forceinline__ float flip_sign(float v, uint32_t neg) {
-  return __int_as_float(__float_as_int(v) ^ (int)(neg << 31));
-}
 template <class V>
 __device__ __forceinline__ V mul_ik(uint32_t k, V a) {
   V r;
@@ -538,6 +535,35 @@ __global__ void norm2_kernel(const typename V2<T>::V* __restrict__ a, int n, dou
   s_d += s;
   const double r = block_sum(s_d, sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = r;
+}
+
+// Reduced density matrix of qubit q, FP64 sums over the pairs (a0, a1) =
+// (psi[x], psi[x | 2^q]) with bit q of x clear: partials[k * grid + block] for
+// k = 0: sum |a0|^2, 1: sum |a1|^2, 2: Re sum a0 conj(a1), 3: Im sum a0 conj(a1).
+template <class T>
+__global__ void qubit_rdm_kernel(const typename V2<T>::V* __restrict__ a, int n, int q, double* partials) {
+  __shared__ double sh[32];
+  const uint64_t P = 1ull << (n - 1), Q = 1ull << q;
+  double r00 = 0, r11 = 0, re = 0, im = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < P; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t x0 = insert0(i, q);
+    const auto u = a[x0], v = a[x0 | Q];
+    const double ux = u.x, uy = u.y, vx = v.x, vy = v.y;
+    r00 += ux * ux + uy * uy;
+    r11 += vx * vx + vy * vy;
+    re += ux * vx + uy * vy;
+    im += uy * vx - ux * vy;
+  }
+  const double s0 = block_sum(r00, sh);
+  const double s1 = block_sum(r11, sh);
+  const double s2 = block_sum(re, sh);
+  const double s3 = block_sum(im, sh);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = s0;
+    partials[gridDim.x + blockIdx.x] = s1;
+    partials[2 * gridDim.x + blockIdx.x] = s2;
+    partials[3 * gridDim.x + blockIdx.x] = s3;
+  }
 }
 
 // One warp per slot, fixed order: lanes take strided partials, then a fixed tree.
@@ -985,6 +1011,16 @@ qs_status launch_inner(qs_dtype dt, const void* a, const void* b, int n, double*
     inner_kernel<float><<<grid, kThreads, 0, st>>>((const float2*)a, (const float2*)b, n, partials);
   else
     inner_kernel<double><<<grid, kThreads, 0, st>>>((const double2*)a, (const double2*)b, n, partials);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_qubit_rdm(qs_dtype dt, const void* psi, int n, int q, double* partials, int grid,
+                           cudaStream_t st) {
+  if (dt == QS_C64)
+    qubit_rdm_kernel<float><<<grid, kThreads, 0, st>>>((const float2*)psi, n, q, partials);
+  else
+    qubit_rdm_kernel<double><<<grid, kThreads, 0, st>>>((const double2*)psi, n, q, partials);
   QS_CUDA(cudaGetLastError());
   return QS_OK;
 }

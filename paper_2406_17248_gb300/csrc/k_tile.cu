@@ -197,9 +197,6 @@ __device__ __forceinline__ void op_real1(V (&a)[RN], const V* M, uint32_t jc, bo
 __device__ __forceinline__ double flip_sign(double v, uint32_t neg) {
   return __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
 }
-__device__ __forceinline__ float flip_sign(float v, uint32_t neg) {
-  return __int_as_float(__float_as_int(v) ^ (int)(neg << 31));
-}
 template <class V>
 __device__ __forceinline__ V mul_ik(uint32_t k, V a) {
   V r;

@@ -10,6 +10,17 @@
 
 using namespace qs;
 
+// A segment of the large-state path: the gates up to a damping / Kraus site (or
+// the end), planned once as a fused circuit, with a one-qubit MATRIX gate at
+// each Pauli / depolarizing site inside it whose entries are set to the sampled
+// Pauli before every trajectory (the plan depends on the gate's kind, not its
+// entries, so it stays valid).
+struct TrajSeg {
+  qs_circuit* c = nullptr;
+  int site_after = -1;               // the state-dependent site that ends it; -1: the end
+  std::vector<int> ph_gate, ph_site;  // placeholder gate index in c, and its site
+};
+
 struct qs_traj {
   int n = 0;
   qs_dtype dt = QS_C64;
@@ -33,6 +44,11 @@ struct qs_traj {
   uint8_t* d_choice = nullptr;
   size_t cap_choice = 0;
   int* d_queue = nullptr;
+  // states too large for one CTA's shared memory: fused tile passes in HBM
+  std::vector<TrajSeg> segs;
+  bool segs_valid = false;
+  qs_state* lpsi = nullptr;
+  qs_state* llam = nullptr;
 };
 
 namespace {
@@ -66,6 +82,171 @@ void set_op(BChannel& C, int k, double a_re, double a_im, double b_re, double b_
             double d_re, double d_im) {
   const double v[8] = {a_re, a_im, b_re, b_im, c_re, c_im, d_re, d_im};
   for (int e = 0; e < 8; ++e) C.K[k][e] = v[e];
+}
+
+// ------------------------------------------------------------------ large states
+
+// The uniform of site s of trajectory t, counter c = t * n_sites + s: the
+// published splitmix64 finaliser (Steele, Lea & Flood 2014) of
+// seed + (c + 1) * 0x9E3779B97F4A7C15, top 53 bits (the same numbers the
+// shared-memory engine draws).
+double traj_uniform_host(uint64_t seed, uint64_t c) {
+  uint64_t z = seed + c * 0x9E3779B97F4A7C15ull + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 0x1.0p-53;
+}
+
+// The smallest branch whose running weight sum exceeds u * total, else the last
+// branch with a positive weight.
+int choose_branch(const double* w, int nk, double u) {
+  double total = 0.0;
+  for (int k = 0; k < nk; ++k) total += w[k];
+  const double thr = u * total;
+  int c = -1;
+  double cum = 0.0;
+  for (int k = 0; k < nk; ++k) {
+    cum += w[k];
+    if (c < 0 && cum > thr) c = k;
+  }
+  if (c < 0)
+    for (int k = 0; k < nk; ++k)
+      if (w[k] > 0) c = k;
+  return c < 0 ? 0 : c;
+}
+
+void free_segs(qs_traj* t) {
+  for (auto& S : t->segs) qs_circuit_destroy(S.c);
+  t->segs.clear();
+  t->segs_valid = false;
+}
+
+qs_status build_segs(qs_traj* t) {
+  if (t->segs_valid) return QS_OK;
+  free_segs(t);
+  auto open = [&]() {
+    t->segs.emplace_back();
+    return qs_circuit_create(t->n, &t->segs.back().c);
+  };
+  QS_TRY(open());
+  static const double kEye[8] = {1, 0, 0, 0, 0, 0, 1, 0};
+  for (const BGate& g : t->gates) {
+    if (g.kind == kGateChannel) {
+      const BChannel& C = t->ch[g.param];
+      if (C.fixed) {
+        TrajSeg& S = t->segs.back();
+        const int q = C.qubit;
+        QS_TRY(qs_circuit_add(S.c, QS_GATE_MATRIX, &q, 1, nullptr, 0, -1, 1.0, 0.0, kEye));
+        S.ph_gate.push_back((int)S.c->gates.size() - 1);
+        S.ph_site.push_back(g.param);
+      } else {
+        t->segs.back().site_after = g.param;
+        QS_TRY(open());
+      }
+      continue;
+    }
+    const int tg[2] = {g.t0, g.t1};
+    int ctr[64], nc = 0;
+    for (int q = 0; q < t->n; ++q)
+      if ((g.cmask >> q) & 1ull) ctr[nc++] = q;
+    QS_TRY(qs_circuit_add(t->segs.back().c, g.kind, tg, g.nt, ctr, nc, g.param, g.coef, g.constant, nullptr));
+  }
+  for (auto& S : t->segs) QS_TRY(qs_circuit_finalize(S.c, t->dt, nullptr));
+  t->segs_valid = true;
+  return QS_OK;
+}
+
+// Branch weights of a damping / Kraus site on the current state:
+// ||K psi||^2 = sum_r sum_ab K_ra conj(K_rb) rho_ab, rho the site qubit's
+// reduced density matrix (FP64 sums on the device).
+qs_status site_weights(qs_traj* t, const BChannel& C, double* w) {
+  qs_state* s = t->lpsi;
+  const int grid = ham_grid_size(s->ne);
+  QS_TRY(ensure_scratch(s, 4 * (size_t)grid + 4));
+  double* part = s->scratch;
+  double* out = part + 4 * (size_t)grid;
+  QS_TRY(launch_qubit_rdm(s->dt, s->ptr, s->ne, C.qubit, part, grid, s->st));
+  QS_TRY(launch_reduce_slots(part, 4, grid, nullptr, out, s->st));
+  double r[4];
+  QS_CUDA(cudaMemcpyAsync(r, out, sizeof(r), cudaMemcpyDeviceToHost, s->st));
+  QS_CUDA(cudaStreamSynchronize(s->st));
+  // rho_ab as (re, im): rho00, rho01, rho10, rho11
+  const double rho[4][2] = {{r[0], 0.0}, {r[2], r[3]}, {r[2], -r[3]}, {r[1], 0.0}};
+  for (int k = 0; k < C.n_kraus; ++k) {
+    double acc = 0.0;
+    for (int row = 0; row < 2; ++row)
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          const double kr = C.K[k][2 * (2 * row + a)], ki = C.K[k][2 * (2 * row + a) + 1];
+          const double lr = C.K[k][2 * (2 * row + b)], li = -C.K[k][2 * (2 * row + b) + 1];  // conj(K_rb)
+          const double pr = kr * lr - ki * li, pi = kr * li + ki * lr;
+          acc += pr * rho[2 * a + b][0] - pi * rho[2 * a + b][1];
+        }
+    w[k] = acc;
+  }
+  return QS_OK;
+}
+
+// Trajectories on the fused tile engine, one after another (host results):
+// the Pauli sites' branches are drawn up front and set into their placeholder
+// gates; at a damping / Kraus site the weights come from site_weights and the
+// state is replaced by K_c psi / sqrt(w_c) (a one-qubit gate kernel).  With
+// gradients (Pauli / depolarizing sites only: one segment, unitary) each
+// trajectory is one adjoint evaluation of its circuit.
+qs_status run_large(qs_traj* t, const qs_ham* h, const double* params, uint64_t seed, long long first, int n_traj,
+                    double* energies, double* grad_mean, unsigned char* choices, qs_state* state_out) {
+  QS_TRY(build_segs(t));
+  if (!t->lpsi) QS_TRY(qs_state_create(t->n, t->dt, nullptr, 0, t->st, &t->lpsi));
+  if (grad_mean && !t->llam) QS_TRY(qs_state_create(t->n, t->dt, nullptr, 0, t->st, &t->llam));
+  const int S = (int)t->ch.size(), np = t->n_params;
+  std::vector<double> g((size_t)std::max(np, 1)), acc((size_t)std::max(np, 1), 0.0);
+  std::vector<int> pick((size_t)std::max(S, 1), 0);
+  for (int i = 0; i < n_traj; ++i) {
+    const uint64_t tr = (uint64_t)(first + i);
+    for (auto& seg : t->segs)
+      for (size_t k = 0; k < seg.ph_gate.size(); ++k) {
+        const int site = seg.ph_site[k];
+        const BChannel& C = t->ch[site];
+        const int c = choose_branch(C.w, C.n_kraus, traj_uniform_host(seed, tr * (uint64_t)S + (uint64_t)site));
+        pick[site] = c;
+        seg.c->gates[seg.ph_gate[k]].matrix.assign(C.K[c], C.K[c] + 8);
+      }
+    double e = 0.0;
+    QS_TRY(qs_state_set_basis(t->lpsi, 0));
+    if (grad_mean) {
+      QS_TRY(qs_expectation_with_grad(t->lpsi, t->llam, t->segs[0].c, h, params, np, &e, g.data()));
+      for (int p = 0; p < np; ++p) acc[p] += g[p];
+    } else {
+      for (auto& seg : t->segs) {
+        if (!seg.c->gates.empty()) QS_TRY(qs_apply_circuit(t->lpsi, seg.c, params, np));
+        if (seg.site_after < 0) continue;
+        const int site = seg.site_after;
+        const BChannel& C = t->ch[site];
+        double w[kTrajMaxKraus] = {0, 0, 0, 0};
+        QS_TRY(site_weights(t, C, w));
+        const int c = choose_branch(w, C.n_kraus, traj_uniform_host(seed, tr * (uint64_t)S + (uint64_t)site));
+        pick[site] = c;
+        const double sc = w[c] > 0 ? 1.0 / std::sqrt(w[c]) : 0.0;
+        double M[8];
+        for (int e2 = 0; e2 < 8; ++e2) M[e2] = C.K[c][e2] * sc;
+        const int q = C.qubit;
+        QS_TRY(launch_gate_dense(t->dt, t->lpsi->ptr, t->lpsi->ne, 1, &q, 0, M, t->lpsi->st));
+      }
+      if (h) QS_TRY(qs_expectation(t->lpsi, h, &e));
+    }
+    if (energies) energies[i] = e;
+    if (choices)
+      for (int site = 0; site < S; ++site) choices[(size_t)i * S + site] = (unsigned char)pick[site];
+  }
+  if (grad_mean)
+    for (int p = 0; p < np; ++p) grad_mean[p] = acc[p] / n_traj;
+  if (state_out) QS_TRY(qs_state_copy(state_out, t->lpsi));
+  return QS_OK;
+}
+
+bool use_large(const qs_traj* t, bool grad) {
+  return traj_grid_size(t->dt, grad, t->n, (int)t->gates.size(), t->n_params) <= 0;
 }
 
 // Launch n_traj trajectories starting at global index `first`.
@@ -117,7 +298,7 @@ extern "C" {
 
 qs_status qs_traj_create(int n_qubits, qs_dtype dtype, void* cuda_stream, qs_traj** out) {
   QS_CHECK(out != nullptr, "out is null");
-  QS_CHECK(n_qubits >= 1 && n_qubits <= 14, "trajectories hold 1..14 qubits (shared memory)");
+  QS_CHECK(n_qubits >= 1 && n_qubits <= kMaxQubits, "n_qubits must be in 1..34");
   QS_CHECK(dtype == QS_C64 || dtype == QS_C128, "invalid dtype");
   qs_traj* t = new qs_traj;
   t->n = n_qubits;
@@ -138,6 +319,9 @@ qs_status qs_traj_destroy(qs_traj* t) {
   cudaFree(t->d_gmean);
   cudaFree(t->d_choice);
   cudaFree(t->d_queue);
+  free_segs(t);
+  qs_state_destroy(t->lpsi);
+  qs_state_destroy(t->llam);
   delete t;
   return QS_OK;
 }
@@ -177,6 +361,7 @@ qs_status qs_traj_add_gate(qs_traj* t, int kind, const int* targets, int n_t, co
   t->gates.push_back(g);
   t->n_params = std::max(t->n_params, param_idx + 1);
   t->dirty = true;
+  t->segs_valid = false;
   return QS_OK;
 }
 
@@ -251,6 +436,7 @@ qs_status qs_traj_add_channel(qs_traj* t, int kind, int qubit, const double* p, 
   t->gates.push_back(g);
   t->ch.push_back(C);
   t->dirty = true;
+  t->segs_valid = false;
   return QS_OK;
 }
 
@@ -270,6 +456,7 @@ qs_status qs_traj_run(qs_traj* t, const qs_ham* h, const double* params, int n_p
   QS_CHECK(h != nullptr && energies != nullptr, "null Hamiltonian or energies");
   QS_CHECK(n_params == t->n_params && (n_params == 0 || params != nullptr), "n_params differs from the circuit's");
   for (int i = 0; i < n_params; ++i) QS_CHECK(std::isfinite(params[i]), "non-finite parameter");
+  if (use_large(t, grad)) return run_large(t, h, params, seed, first, n_traj, energies, grad_mean, choices, nullptr);
   QS_TRY(ensure(&t->d_params, &t->cap_params, (size_t)n_params));
   QS_TRY(ensure(&t->d_energy, &t->cap_energy, (size_t)n_traj));
   if (grad) QS_TRY(ensure(&t->d_gmean, &t->cap_gmean, (size_t)n_params));
@@ -293,6 +480,18 @@ qs_status qs_traj_run_device(qs_traj* t, const qs_ham* h, const double* d_params
   QS_TRY(check_run(t, h, n_traj, first, grad));
   QS_CHECK(h != nullptr && d_energies != nullptr, "null Hamiltonian or energies");
   QS_CHECK(t->n_params == 0 || d_params != nullptr, "null parameters");
+  if (use_large(t, grad)) {  // host loop over trajectories; results copied to the device buffers
+    std::vector<double> p((size_t)std::max(t->n_params, 1)), e((size_t)n_traj), gm((size_t)std::max(t->n_params, 1));
+    if (t->n_params)
+      QS_CUDA(cudaMemcpyAsync(p.data(), d_params, t->n_params * sizeof(double), cudaMemcpyDeviceToHost, t->st));
+    QS_CUDA(cudaStreamSynchronize(t->st));
+    QS_TRY(run_large(t, h, p.data(), seed, first, n_traj, e.data(), grad ? gm.data() : nullptr, nullptr, nullptr));
+    QS_CUDA(cudaMemcpyAsync(d_energies, e.data(), n_traj * sizeof(double), cudaMemcpyHostToDevice, t->st));
+    if (grad && t->n_params)
+      QS_CUDA(cudaMemcpyAsync(d_grad_mean, gm.data(), t->n_params * sizeof(double), cudaMemcpyHostToDevice, t->st));
+    QS_CUDA(cudaStreamSynchronize(t->st));
+    return QS_OK;
+  }
   return run(t, h, d_params, seed, first, n_traj, d_energies, grad, d_grad_mean, nullptr, nullptr);
 }
 
@@ -302,6 +501,10 @@ qs_status qs_traj_state(qs_traj* t, const double* params, int n_params, uint64_t
   QS_TRY(check_state(out));
   QS_CHECK(out->n == t->n && out->dt == t->dt, "state n/dtype differs from the trajectory engine");
   QS_CHECK(n_params == t->n_params && (n_params == 0 || params != nullptr), "n_params differs from the circuit's");
+  if (use_large(t, false)) {
+    QS_CUDA(cudaStreamSynchronize(out->st));
+    return run_large(t, nullptr, params, seed, traj, 1, nullptr, nullptr, nullptr, out);
+  }
   QS_TRY(ensure(&t->d_params, &t->cap_params, (size_t)n_params));
   QS_TRY(ensure(&t->d_energy, &t->cap_energy, 1));
   if (n_params)

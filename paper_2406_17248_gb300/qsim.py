@@ -574,7 +574,9 @@ class Trajectories:
         return out[0] if len(out) == 1 else tuple(out)
 
     def run_device(self, ham: Hamiltonian, params, n_traj: int, seed: int, energies, grad_mean=None, first: int = 0):
-        """Device (torch float64 CUDA tensors) variant: no copies, no synchronisation."""
+        """Device (torch float64 CUDA tensors) variant: no copies and no
+        synchronisation while the state fits in shared memory (larger states
+        run trajectory by trajectory and synchronise)."""
         _check(lib().qs_traj_run_device(self.h, ham.h, C.c_void_p(params.data_ptr()) if params.numel() else None,
                                         seed, first, n_traj, C.c_void_p(energies.data_ptr()),
                                         C.c_void_p(grad_mean.data_ptr()) if grad_mean is not None else None))

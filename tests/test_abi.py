@@ -77,8 +77,8 @@ def test_null_handles_are_rejected(lib):
 
 def test_trajectory_argument_checks_run_on_the_host(lib):
     h = C.c_void_p()
-    assert lib.qs_traj_create(15, 0, None, C.byref(h)) == 1
-    assert b"1..14 qubits" in lib.qs_last_error()
+    assert lib.qs_traj_create(35, 0, None, C.byref(h)) == 1
+    assert b"1..34" in lib.qs_last_error()
     assert lib.qs_traj_create(3, 0, None, C.byref(h)) == 0
     t = (C.c_int * 1)(3)
     assert lib.qs_traj_add_gate(h, Q.KIND["X"], t, 1, None, 0, -1, 1.0, 0.0) == 1

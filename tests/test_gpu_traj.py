@@ -4,7 +4,8 @@ is further than the state's rounding from a branch boundary; always for Pauli
 and depolarizing channels, whose weights are constants), the final state of
 each trajectory, the trajectory energies, the mean adjoint gradient of
 Pauli-channel trajectories, convergence of the mean to tr(rho H), 64-bit
-trajectory counters, and the size limits.
+trajectory counters, the largest shared-memory states, and states beyond
+shared memory on the fused tile passes.
 
 Tolerances: amplitudes and energies 5e-5 (complex64) / 1e-11 (complex128)
 times max(1, sum |c_k|) for energies, as in the other parity tests."""
@@ -169,9 +170,59 @@ def test_largest_shared_memory_trajectories(Q, dt, n, grad):
         assert np.abs(out[1] - np.mean(gs, axis=0)).max() < tol
 
 
-def test_too_large_for_shared_memory_is_refused(Q):
-    circ = I.hea_circuit(14, 1)
-    eng = Q.trajectories_from(circ, {0: [("depolarizing", (0.1,), 0)]}, 1)
+@pytest.mark.parametrize("dt", [0, 1])
+def test_large_state_trajectories_match_oracle(Q, dt):
+    """States beyond one CTA's shared memory run on the fused tile passes: every
+    channel kind (the damping / Kraus weights from the qubit's reduced density
+    matrix), against the oracle's branches, states and energies."""
+    n = 15
+    circ, params, ch = _mixed_noise(n, 1, 5)
+    eng = Q.trajectories_from(circ, ch, dt)
     assert eng.info()["grid_energy"] == 0
-    with pytest.raises(Q.QSimError, match="too many qubits"):
-        eng.run(Q.Hamiltonian(I.chain_zz_x(14)), np.zeros(circ.n_params), 2, 1)
+    seed = 99
+    ham = I.chain_zz_x(n, 0.5)
+    e, branches = eng.run(Q.Hamiltonian(ham), params, 6, seed, first=3, choices=True)
+    checked = 0
+    for i in range(6):
+        psi, choices, margins = T.trajectory(circ, params, ch, seed, 3 + i)
+        if min(margins) < MARGIN[dt]:
+            continue
+        checked += 1
+        assert list(branches[i]) == choices, i
+        assert abs(e[i] - O.expectation(psi, ham)) < TOL[dt] * float(np.abs(ham.coef).sum()), i
+        s = Q.State(n, dt)
+        eng.state(params, seed, 3 + i, s)
+        assert np.abs(s.get_qs().astype(np.complex128) - psi).max() < TOL[dt], i
+    assert checked >= 4
+
+
+@pytest.mark.parametrize("dt,n", [(0, 14), (1, 13)])
+def test_large_state_pauli_gradients_match_oracle(Q, dt, n):
+    """Gradients beyond shared memory (psi and lam do not both fit): each
+    trajectory one adjoint evaluation of its circuit on the tile passes, through
+    the host and the device-buffer entry points."""
+    import torch
+    circ = I.hea_circuit(n, 1)
+    params = I.uniform_params(circ.n_params, 12)
+    ham = I.chain_zz_x(n, 0.6)
+    ch = {i: [("depolarizing", (0.15,), i % n), ("pauli", (0.05, 0.1, 0.02), (i + 5) % n)]
+          for i in range(0, len(circ.gates), 4)}
+    eng = Q.trajectories_from(circ, ch, dt)
+    assert eng.info()["grid_grad"] == 0
+    n_t, seed = 4, 41
+    e, g, branches = eng.run(Q.Hamiltonian(ham), params, n_t, seed, first=2, grad=True, choices=True)
+    es, gs = [], []
+    for i in range(n_t):
+        eo, go, co, _ = T.trajectory_energy_and_grad(circ, ham, params, ch, seed, 2 + i)
+        assert list(branches[i]) == co, i
+        es.append(eo)
+        gs.append(go)
+    tol = TOL[dt] * max(1.0, float(np.abs(ham.coef).sum()))
+    assert np.abs(e - np.array(es)).max() < tol
+    assert np.abs(g - np.mean(gs, axis=0)).max() < tol
+    d_p = torch.tensor(params, dtype=torch.float64, device="cuda")
+    d_e = torch.zeros(n_t, dtype=torch.float64, device="cuda")
+    d_g = torch.zeros(circ.n_params, dtype=torch.float64, device="cuda")
+    eng.run_device(Q.Hamiltonian(ham), d_p, n_t, seed, d_e, d_g, first=2)
+    assert np.abs(d_e.cpu().numpy() - np.array(es)).max() < tol
+    assert np.abs(d_g.cpu().numpy() - np.mean(gs, axis=0)).max() < tol

@@ -10,11 +10,12 @@
 // with every float32 operand split into a tf32 head and a tf32 tail
 // (x = h + t) and three products h.h + h.t + t.h accumulated in float32 in
 // tensor memory: the dropped t.t term and the tail rounding are ~2^-21
-// relative, float32 accuracy overall.  One CTA of 128 threads takes tiles of
-// 128 rows: each thread gathers its row from HBM, splits it and stores it in
-// the no-swizzle K-major core-matrix layout; one thread issues the MMAs and
-// commits them to an mbarrier; each warp reads its 32 TMEM lanes back
-// (tcgen05.ld 32x32b) and stores the rows' outputs in place.  Every other
+// relative, float32 accuracy overall.  One CTA of 256 threads takes tiles of
+// 128 rows, two threads per row: each gathers half of its row from HBM, splits
+// it and stores it in the no-swizzle K-major core-matrix layout; one thread
+// issues the MMAs and commits them to an mbarrier; each warp reads its 32 TMEM
+// lanes back (tcgen05.ld 32x32b, the columns of its half) and stores those
+// outputs in place.  Every other
 // case (complex128, other k, small n) runs on the CUDA cores in the state's
 // own precision.
 #include <cuda_runtime.h>
@@ -31,7 +32,10 @@ namespace {
 
 constexpr int kDenseMaxK = 6;
 constexpr int kTcRows = 128;     // rows (MMA M) per tile
-constexpr int kTcThreads = 128;  // one thread per row; warp w owns TMEM lanes 32w..32w+31
+// two threads per row: thread t takes row t & 127 and half t >> 7 of its
+// amplitudes; warp w reads TMEM lanes 32 (w % 4) .. + 31 (its lane quarter),
+// columns of its half
+constexpr int kTcThreads = 256;
 constexpr long long kWaitLimit = 1ll << 26;  // bounded mbarrier polling
 
 // ------------------------------------------------------------------ PTX helpers
@@ -155,6 +159,8 @@ __global__ void __launch_bounds__(kTcThreads) dense_tc_kernel(float2* __restrict
   __shared__ int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = tid & (kTcRows - 1), half = tid / kTcRows;
+  constexpr int KH = KB / 2;  // amplitudes per thread
   // B[n][kk] = W[kk][n], W = real form of U^T (see the file comment); split h/t
   for (int e = tid; e < KR * KR; e += kTcThreads) {
     const int n = e / KR, kk = e % KR;
@@ -190,17 +196,17 @@ __global__ void __launch_bounds__(kTcThreads) dense_tc_kernel(float2* __restrict
   // Software pipeline: the rows of the next tile are loaded into registers
   // while the tensor cores work on this one and its results are stored.
   uint64_t tile = blockIdx.x;
-  float2 x[KB];
+  float2 x[KH];
   uint64_t base = 0;
   if (tile < n_tiles) {
-    base = deposit_other(G, tile * kTcRows + tid);
+    base = deposit_other(G, tile * kTcRows + row);
 #pragma unroll
-    for (int j = 0; j < KB; ++j) x[j] = psi[base | G.tgt_off[j]];
+    for (int j = 0; j < KH; ++j) x[j] = psi[base | G.tgt_off[half * KH + j]];
   }
   for (; tile < n_tiles; tile += gridDim.x) {
-    // split this thread's row into tf32 head and tail, K-major core-matrix layout
+    // split this thread's half row into tf32 head and tail, K-major core-matrix layout
 #pragma unroll
-    for (int c = 0; c < KB / 2; ++c) {
+    for (int c = 0; c < KH / 2; ++c) {
       const float2 p0 = x[2 * c], p1 = x[2 * c + 1];
       float4 h, t;
       h.x = tf32_round(p0.x);
@@ -211,7 +217,7 @@ __global__ void __launch_bounds__(kTcThreads) dense_tc_kernel(float2* __restrict
       t.y = tf32_round(p0.y - h.y);
       t.z = tf32_round(p1.x - h.z);
       t.w = tf32_round(p1.y - h.w);
-      const uint32_t off = op_offset(tid, 4 * c, KR);
+      const uint32_t off = op_offset(row, half * KB + 4 * c, KR);
       *reinterpret_cast<float4*>(a_hi + off) = h;
       *reinterpret_cast<float4*>(a_lo + off) = t;
     }
@@ -234,14 +240,14 @@ __global__ void __launch_bounds__(kTcThreads) dense_tc_kernel(float2* __restrict
     // next tile's rows in flight during the MMAs and the stores below
     const uint64_t next = tile + gridDim.x;
     uint64_t nbase = 0;
-    float2 xn[KB];
+    float2 xn[KH];
     if (next < n_tiles) {
-      nbase = deposit_other(G, next * kTcRows + tid);
+      nbase = deposit_other(G, next * kTcRows + row);
 #pragma unroll
-      for (int j = 0; j < KB; ++j) xn[j] = psi[nbase | G.tgt_off[j]];
+      for (int j = 0; j < KH; ++j) xn[j] = psi[nbase | G.tgt_off[half * KH + j]];
     } else {
 #pragma unroll
-      for (int j = 0; j < KB; ++j) xn[j] = make_float2(0.f, 0.f);
+      for (int j = 0; j < KH; ++j) xn[j] = make_float2(0.f, 0.f);
     }
     // every thread waits for the MMAs (bounded)
     bool ok = false;
@@ -258,10 +264,11 @@ __global__ void __launch_bounds__(kTcThreads) dense_tc_kernel(float2* __restrict
       break;
     }
     tc_fence_after();
-    // rows back from tensor memory: lane (32 warp + l) = row, columns 2i, 2i+1 = output i
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    // rows back from tensor memory: lane 32 (warp % 4) + l = row, columns 2i,
+    // 2i + 1 = output i, this half's outputs only
+    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll
-    for (int c0 = 0; c0 < KR; c0 += 16) {
+    for (int c0 = half * KB; c0 < half * KB + KB; c0 += 16) {
       float v[16];
       tmem_ld16(trow + c0, v);
 #pragma unroll
@@ -271,7 +278,7 @@ __global__ void __launch_bounds__(kTcThreads) dense_tc_kernel(float2* __restrict
     __syncthreads();
     base = nbase;
 #pragma unroll
-    for (int j = 0; j < KB; ++j) x[j] = xn[j];
+    for (int j = 0; j < KH; ++j) x[j] = xn[j];
   }
   tc_fence_after();
   __syncthreads();
@@ -353,7 +360,19 @@ qs_status launch_tc(float2* psi, const DenseGeom& G, const double2* dU, int* d_e
   QS_CUDA(cudaGetDevice(&dev));
   QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   QS_CUDA(cudaFuncSetAttribute(dense_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+  // all of the unified L1 / shared memory as shared memory, so that two CTAs fit
+  QS_CUDA(cudaFuncSetAttribute(dense_tc_kernel<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared));
   QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_tc_kernel<K>, kTcThreads, Cfg::SMEM));
+  // the CTAs the SM's shared memory holds (the query above has returned one
+  // where two fit); CTAs beyond the resident ones would only wait their turn
+  int smem_sm = 0, reserved = 0;
+  cudaFuncAttributes fa{};
+  QS_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  QS_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+  QS_CUDA(cudaFuncGetAttributes(&fa, dense_tc_kernel<K>));
+  const size_t per_cta = Cfg::SMEM + fa.sharedSizeBytes + (size_t)reserved;
+  per_sm = std::max(per_sm, (int)((size_t)smem_sm / per_cta));
   // tensor memory: at most 512 columns per SM among resident CTAs
   per_sm = std::max(1, std::min(per_sm, 512 / Cfg::TMEM_COLS));
   const uint64_t grid = std::min<uint64_t>(n_tiles, (uint64_t)sms * per_sm);

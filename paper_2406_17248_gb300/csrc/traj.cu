@@ -241,7 +241,11 @@ qs_status run_large(qs_traj* t, const qs_ham* h, const double* params, uint64_t 
   }
   if (grad_mean)
     for (int p = 0; p < np; ++p) grad_mean[p] = acc[p] / n_traj;
-  if (state_out) QS_TRY(qs_state_copy(state_out, t->lpsi));
+  if (state_out) {  // the copy runs on the output's stream: the trajectory's work first
+    QS_CUDA(cudaStreamSynchronize(t->lpsi->st));
+    QS_TRY(qs_state_copy(state_out, t->lpsi));
+    QS_CUDA(cudaStreamSynchronize(state_out->st));
+  }
   return QS_OK;
 }
 

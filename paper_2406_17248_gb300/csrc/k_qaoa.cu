@@ -44,10 +44,6 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
@@ -605,7 +601,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) qaoa_il_kernel(QArgs args) {
     const int nc = per_layer * P.n_layers;
     for (int i = threadIdx.x; i < nc; i += blockDim.x) s_coef[i] = g[i];
   }
-  const int m = P.m, c = P.c;
+  const int m = P.m;
   const uint32_t flags = P.flags;
   const uint32_t tile_n = 1u << m;
   unsigned char* base = smem + ((n_coef * sizeof(float2) + 127) & ~(size_t)127);
@@ -617,7 +613,6 @@ __global__ void __launch_bounds__(kTileThreads, 1) qaoa_il_kernel(QArgs args) {
   uint32_t* s_base = reinterpret_cast<uint32_t*>(s_accd + kQaoaMaxAcc * kTileThreads);
 
   const int tid = threadIdx.x;
-  const uint32_t lowmask = (1u << c) - 1u;
   const uint64_t n_tiles = 1ull << (args.n - m);
   const int n_edges = args.n_edges;
 

@@ -480,7 +480,7 @@ qs_status qs_qaoa_create(int n_qubits, const int* edges, int n_edges, int p, dou
     ops.push_back({QO_ENERGY, sched[K - 1].ops.back().layer, -1});
     const std::vector<QOp> r = reverse_ops(sched[K - 1].ops);
     ops.insert(ops.end(), r.begin(), r.end());
-    const uint32_t out = (q->il && K > 1) ? PF_STORE_IL : PF_STORE_LAM;
+    const uint32_t out = (q->il && K > 1) ? (uint32_t)PF_STORE_IL : (uint32_t)PF_STORE_LAM;
     const uint32_t fl = (K == 1 ? PF_GEN_PLUS : PF_LOAD_PSI) | out | PF_NEED_CUT;
     if ((s = build_qpass(B, sched[K - 1].S, ops, fl, &D, &q->gslots)) != QS_OK) return fail(s);
     q->gpass.push_back(D);

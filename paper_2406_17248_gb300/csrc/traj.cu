@@ -1,6 +1,9 @@
 // Host side of the Monte-Carlo trajectory engine (§3.3: the state-vector
 // simulator treats channels by sampling, and the average over sampled runs is
-// the noisy result): circuit and channel tables, argument checks, launches.
+// the noisy result): circuit and channel tables, argument checks, launches of
+// the shared-memory trajectory kernel, and, for states too large for one CTA's
+// shared memory, the loop that runs trajectories one by one on the fused tile
+// passes.
 #include <algorithm>
 #include <cmath>
 #include <vector>

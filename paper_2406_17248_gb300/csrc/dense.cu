@@ -260,7 +260,14 @@ __global__ void __launch_bounds__(kTcThreads) dense_tc_kernel(float2* __restrict
     if (!ok) atomicExch(&s_abort, 1);
     __syncthreads();
     if (s_abort) {
-      if (tid == 0) atomicExch(err, 1);
+      if (tid == 0) {
+        atomicExch(err, 1);
+        // the committed MMAs may still be reading shared memory and writing
+        // tensor memory: wait for their commit once more (bounded) before the
+        // tensor memory is freed below
+        for (long long it = 0; it < kWaitLimit; ++it)
+          if (mbar_try_wait(smem_u32(mbar), phase ^ 1u)) break;
+      }
       break;
     }
     tc_fence_after();

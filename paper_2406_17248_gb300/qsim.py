@@ -162,7 +162,8 @@ class State:
         ne = max(n, 4)
         tdt = torch.complex64 if dtype == C64 else torch.complex128
         self.buffer = torch.empty(1 << ne, dtype=tdt, device=device or "cuda")
-        self._stream = stream
+        # the stream the library's state handle enqueues on (fixed at creation)
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         _check(lib().qs_state_create(n, dtype, C.c_void_p(self.buffer.data_ptr()),
                                      self.buffer.numel() * self.buffer.element_size(),
@@ -630,7 +631,10 @@ def apply_matrix(state: State, targets, matrix, engine: int = 0) -> State:
 def expectation_noalloc(state: State, ham: I.PauliSum, stream=None) -> float:
     """<psi|H|psi> through qs_expectation_noalloc: no device allocation by the
     library (its working memory is a fixed array inside the library), for callers
-    whose device memory belongs to another allocator."""
+    whose device memory belongs to another allocator.  Runs on the state's own
+    stream unless another is given, behind the state's pending work."""
+    if stream is None:
+        stream = state._stream
     x = np.ascontiguousarray(ham.xmask, dtype=np.uint64)
     z = np.ascontiguousarray(ham.zmask, dtype=np.uint64)
     cf = np.ascontiguousarray(ham.coef, dtype=np.float64)

@@ -1,7 +1,9 @@
 """GPU parity of the density-matrix simulator against the FP64 density-matrix
 oracle: rho after noisy circuits (every channel kind, custom Kraus included),
 tr(rho H), the noiseless case against the state-vector oracle, and a 14-qubit
-density matrix (a 28-qubit vector) against the state-vector oracle."""
+density matrix (a 28-qubit vector) against the state-vector oracle.
+Tolerances: the rule of tests/tolerance.py, rho as a vector of 4^n entries
+(its Frobenius norm is that vector's 2-norm), tr(rho) as the energy of H = I."""
 import numpy as np
 import pytest
 
@@ -9,9 +11,9 @@ from oracle import dm_oracle as D
 from oracle import qsim_oracle as O
 from paper_2406_17248_gb300 import inputs as I
 
-pytestmark = pytest.mark.gpu
+from tolerance import TOL, check, energy_tol, state_err
 
-TOL = {0: 5e-5, 1: 1e-11}
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
@@ -49,11 +51,11 @@ def test_noisy_circuit_matches_oracle(Q, dt):
     c.apply(s, params)
     want = D.run(circ, params, ch, n)
     want = D.apply_channel(want, n, D.channel_kraus("amplitude_damping", (g,)), 1)
-    assert np.max(np.abs(_rho(Q, s, n) - want)) <= TOL[dt]
+    check(f"dm noisy rho dt={dt}", state_err(_rho(Q, s, n), want), TOL[dt])
     for seed in range(3):
         ham = I.random_pauli_sum(n, 10, seed)
         E = Q.dm_expectation(s, Q.Hamiltonian(ham))
-        assert abs(E - D.expectation(want, ham)) <= TOL[dt] * max(1.0, float(np.abs(ham.coef).sum()))
+        check(f"dm noisy energy {seed} dt={dt}", abs(E - D.expectation(want, ham)), energy_tol(dt, ham))
 
 
 @pytest.mark.parametrize("dt", [0, 1])
@@ -65,9 +67,10 @@ def test_noiseless_density_matrix_equals_pure_state(Q, dt):
     s = Q.State(2 * n, dt).set_basis(0)
     c.apply(s, params)
     psi = O.evolve(circ, params, O.zero_state(n))
-    assert np.max(np.abs(_rho(Q, s, n) - np.outer(psi, psi.conj()))) <= TOL[dt]
+    check(f"dm noiseless rho dt={dt}", state_err(_rho(Q, s, n), np.outer(psi, psi.conj())), TOL[dt])
     ham = I.chain_zz_x(n, 0.5)
-    assert abs(Q.dm_expectation(s, Q.Hamiltonian(ham)) - O.expectation(psi, ham)) <= TOL[dt] * 11
+    check(f"dm noiseless energy dt={dt}", abs(Q.dm_expectation(s, Q.Hamiltonian(ham)) - O.expectation(psi, ham)),
+          energy_tol(dt, ham))
 
 
 def test_density_matrix_14_qubits(Q):
@@ -84,11 +87,10 @@ def test_density_matrix_14_qubits(Q):
     s = Q.State(2 * n, Q.C64).set_basis(0)
     Q.dm_circuit_from(circ).finalize(Q.C64).apply(s, params)
     E0 = O.expectation(O.evolve(circ, params, O.zero_state(n)), ham)
-    sc = float(np.abs(ham.coef).sum())
-    assert abs(Q.dm_expectation(s, H) - E0) <= TOL[0] * sc
+    check("dm14 noiseless energy", abs(Q.dm_expectation(s, H) - E0), energy_tol(0, ham))
     layer_end = [i for i, g in enumerate(circ.gates) if g.kind == "X" and g.targets == (n - 1,)]
     ch = {i: [("depolarizing", (0.05,), q) for q in range(n)] for i in layer_end}
     s.set_basis(0)
     Q.dm_circuit_from(circ, ch).finalize(Q.C64).apply(s, params)
-    assert abs(Q.dm_expectation(s, one) - 1.0) <= 1e-4
+    check("dm14 noisy trace", abs(Q.dm_expectation(s, one) - 1.0), TOL[0])
     assert abs(Q.dm_expectation(s, H)) < abs(E0)

@@ -357,6 +357,25 @@ QS_API qs_status qs_qaoa_expectation(qs_qaoa* q, qs_state* psi, const double* ga
 QS_API qs_status qs_qaoa_expectation_with_grad(qs_qaoa* q, qs_state* psi, qs_state* lam, const double* gamma,
                                         const double* beta, double* energy, double* dgamma, double* dbeta);
 
+/* Plan of the complex64 two-shape QAOA passes (options fuse = 2, tile_bits,
+ * low_bits; host only, no device work), for inspection and host-side tests.
+ * which: 0 = energy+gradient plan (forward passes, turnaround, reverse passes),
+ * 1 = energy plan.  rec: long long[max_passes * QS_XPLAN_REC]; per pass:
+ * [0] kernel (0: psi alone, 1: psi and lam interleaved), [1] flags (1 start
+ * from |+>, 2 load psi with lam = 0, 4 store, 8 step-1 gradients, 16 step-3
+ * gradients), [2] tile qubit mask, [3] phases, [4] step-1 coefficient offset,
+ * [5] step-3 offset, [6] diagonal LUT offset (-1 none; offsets index the
+ * per-layer table lut[|E|+1], lut_dag[|E|+1], (cos b/2, sin b/2),
+ * (cos b/2, -sin b/2)), [7..9] output slot of accumulators 0..2 (-1 none),
+ * [10] tile bits, [11] low bits, then per phase 7 entries: step-1 register
+ * mask, step-3 register mask, diagonal (0 none, 1 cost, 2 cost gradient and
+ * cost^dag, 3 energy), the qubits of register bits 0..3.  slot_out/slot_w:
+ * output (0 = E, 1 + l = dgamma_l, 1 + p + l = dbeta_l) and weight per slot. */
+#define QS_XPLAN_REC 68
+QS_API qs_status qs_qaoa_xplan(int n_qubits, const int* edges, int n_edges, int p, double gamma_scale, int tile_bits,
+                               int low_bits, int which, long long* rec, int max_passes, int* n_passes,
+                               int* slot_out, double* slot_w, int max_slots, int* n_slots);
+
 /* One evaluation without handles, in the shape of the QuPack QAOA call (§6.2):
  * graph, depth and angles in; energy and gradients out (host arrays of p
  * doubles).  Creates the engine and two library-owned states on the legacy

@@ -23,6 +23,7 @@
 
 #include "handles.h"
 #include "qaoa_pass.h"
+#include "qaoa_x_plan.h"
 
 using cd = std::complex<double>;
 using namespace qs;
@@ -56,6 +57,18 @@ struct qs_qaoa {
   // the reverse pass that undoes the next one
   std::vector<int> ck_after;
   std::vector<void*> ckpt;
+  // complex64 passes with separate forward (psi alone, mf tile bits, cf low
+  // bits) and reverse (psi/lam interleaved, mr, cr) tile shapes; cut values
+  // are formed in the kernels, d_cut is only made for qs_qaoa_max_cut
+  bool xp = false;
+  int xmf = 0, xcf = 0, xmr = 0, xcr = 0;
+  std::vector<XPass> xg, xe;       // gradient plan, energy plan
+  std::vector<int> xg_two, xe_two; // kernel of each pass: 0 psi alone, 1 psi/lam
+  XPass* d_xg = nullptr;
+  XPass* d_xe = nullptr;
+  uint8_t* d_xfs = nullptr;
+  int xgrid_f = 1, xgrid_r = 1, xstride = 1;
+  double xbytes_grad = 0, xbytes_energy = 0;
 };
 
 namespace {
@@ -385,6 +398,78 @@ double pass_bytes(uint32_t f, double S, double N) {
          ((f & PF_NEED_CUT) ? N : 0.0);
 }
 
+// ---------------------------------------------------------------------------- two-shape complex64 passes
+
+qs_status build_x_engine(qs_qaoa* q, const std::vector<std::pair<int, int>>& es, const qs_options* opts) {
+  const int eng = opts ? opts->fuse : 0;
+  const int mr = (eng == 2 && opts->tile_bits) ? opts->tile_bits : 12;
+  const int cr = (eng == 2 && opts->low_bits) ? opts->low_bits : 3;
+  QS_CHECK(mr >= 9 && mr <= 12, "tile_bits of the complex64 two-shape QAOA passes must be 9..12");
+  QS_CHECK(cr >= 2 && cr <= mr - 4, "low_bits of the complex64 two-shape QAOA passes must be 2..tile_bits-4");
+  QS_CHECK(!(opts && opts->checkpoint), "QAOA checkpoints need the general passes (fuse = 1)");
+  const int n = q->n, p = q->p;
+  QS_CHECK(n > mr + 1, "the complex64 two-shape QAOA passes need n_qubits > tile_bits + 1");
+  XBuild B;
+  B.n = n;
+  B.p = p;
+  B.mf = mr + 1;
+  B.cf = cr + 1;
+  B.mr = mr;
+  B.cr = cr;
+  B.n_edges = q->n_edges;
+  B.edges = es;
+  XPlans X;
+  QS_TRY(qx_make_plans(B, q->gs, &X));
+  q->xmf = B.mf;
+  q->xcf = B.cf;
+  q->xmr = mr;
+  q->xcr = cr;
+  q->xg = X.grad;
+  q->xg_two = X.grad_two;
+  q->xe = X.energy;
+  q->xe_two = X.energy_two;
+  q->gslots = X.gslots;
+  q->eslots = X.eslots;
+  q->xgrid_f = qx_grid(0, B.mf, q->n_edges, 0, 1ull << (n - B.mf));
+  q->xgrid_r = qx_grid(1, mr, q->n_edges, 0, 1ull << (n - mr));
+  if (q->xgrid_f < 1 || q->xgrid_r < 1) {
+    set_error("qaoa: the two-shape tiles do not fit in shared memory");
+    return QS_ERR_UNSUPPORTED;
+  }
+  q->xstride = std::max(q->xgrid_f, q->xgrid_r);
+  QS_CUDA(cudaMalloc(&q->d_xg, q->xg.size() * sizeof(XPass)));
+  QS_CUDA(cudaMalloc(&q->d_xe, q->xe.size() * sizeof(XPass)));
+  QS_CUDA(cudaMalloc(&q->d_xfs, X.fs.size()));
+  QS_CUDA(cudaMemcpy(q->d_xg, q->xg.data(), q->xg.size() * sizeof(XPass), cudaMemcpyHostToDevice));
+  QS_CUDA(cudaMemcpy(q->d_xe, q->xe.data(), q->xe.size() * sizeof(XPass), cudaMemcpyHostToDevice));
+  QS_CUDA(cudaMemcpy(q->d_xfs, X.fs.data(), X.fs.size(), cudaMemcpyHostToDevice));
+  {
+    std::vector<int> ev;
+    for (const auto& e : es) {
+      ev.push_back(e.first);
+      ev.push_back(e.second);
+    }
+    QS_CUDA(cudaMalloc(&q->d_edges, sizeof(int) * ev.size()));
+    QS_CUDA(cudaMemcpy(q->d_edges, ev.data(), sizeof(int) * ev.size(), cudaMemcpyHostToDevice));
+  }
+  // psi and lam interleaved in one buffer of 16 bytes per amplitude (lam's own
+  // buffer is left unused by these passes)
+  QS_CUDA(cudaMalloc(&q->d_il_priv, (size_t)16 << n));
+  q->il = true;
+  const CoefLayout L = layout_for(q->n_edges);
+  q->n_coef = L.per_layer * p;
+  QS_CUDA(cudaMalloc(&q->d_coef, (size_t)q->n_coef * 16));
+  QS_TRY(build_csr(q->gslots, 1 + 2 * p, &q->g_row, &q->g_sidx, &q->g_w, nullptr));
+  QS_TRY(build_csr(q->eslots, 1, &q->e_row, &q->e_sidx, &q->e_w, nullptr));
+  q->xbytes_grad = X.bytes_grad;
+  q->xbytes_energy = X.bytes_energy;
+  q->n_fwd = X.n_fwd - 1;
+  q->rev_passes = X.n_rev;
+  q->bytes_per_eval = X.bytes_grad;
+  q->xp = true;
+  return QS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -410,6 +495,9 @@ qs_status qs_qaoa_create(int n_qubits, const int* edges, int n_edges, int p, dou
              "tile_bits must be 0 or 6..13");
     QS_CHECK(opts->low_bits >= 0 && opts->low_bits <= kMaxTileBits, "low_bits must be 0..13");
     QS_CHECK(opts->checkpoint >= 0, "checkpoint must be >= 0");
+    QS_CHECK(opts->fuse >= 0 && opts->fuse <= 2,
+             "QAOA fuse option must be 0 (automatic), 1 (general passes) or 2 (two-shape passes)");
+    QS_CHECK(opts->fuse != 2 || dtype == QS_C64, "the two-shape QAOA passes are complex64 only");
   }
 
   qs_qaoa* q = new qs_qaoa;
@@ -419,6 +507,34 @@ qs_status qs_qaoa_create(int n_qubits, const int* edges, int n_edges, int p, dou
   q->n_edges = n_edges;
   q->gs = gamma_scale;
   q->dt = dtype;
+  // engine: fuse 2 = complex64 two-shape passes, 1 = general passes, 0 = automatic
+  // (two-shape passes for complex64 from 18 qubits when no tile option is set)
+  const int eng = opts ? opts->fuse : 0;
+  const bool want_x = dtype == QS_C64 &&
+                      (eng == 2 || (eng == 0 && n_qubits >= 18 &&
+                                    !(opts && (opts->tile_bits || opts->low_bits || opts->checkpoint))));
+  if (want_x) {
+    const qs_status xs = build_x_engine(q, es, opts);
+    if (xs == QS_OK) {
+      *out = q;
+      return QS_OK;
+    }
+    if (eng == 2) {
+      qs_qaoa_destroy(q);
+      return xs;
+    }
+    // automatic choice: fall back to the general passes
+    qs_qaoa* fresh = new qs_qaoa;
+    fresh->n = q->n;
+    fresh->ne = q->ne;
+    fresh->p = q->p;
+    fresh->n_edges = q->n_edges;
+    fresh->gs = q->gs;
+    fresh->dt = q->dt;
+    qs_qaoa_destroy(q);
+    q = fresh;
+    (void)cudaGetLastError();
+  }
   int mm = (opts && opts->tile_bits) ? opts->tile_bits : (dtype == QS_C64 ? 12 : 11);
   // double-buffered psi + lam tiles must fit twice in shared memory
   mm = std::max(kRegBits, std::min({mm, dtype == QS_C64 ? 12 : 11, q->n}));
@@ -546,6 +662,9 @@ qs_status qs_qaoa_destroy(qs_qaoa* q) {
   if (q->d_gpass) cudaFree(q->d_gpass);
   if (q->d_epass) cudaFree(q->d_epass);
   if (q->d_il_priv) cudaFree(q->d_il_priv);
+  if (q->d_xg) cudaFree(q->d_xg);
+  if (q->d_xe) cudaFree(q->d_xe);
+  if (q->d_xfs) cudaFree(q->d_xfs);
   for (void* b : q->ckpt) cudaFree(b);
   for (int* pi : {q->g_row, q->g_sidx, q->e_row, q->e_sidx})
     if (pi) cudaFree(pi);
@@ -565,6 +684,10 @@ qs_status qs_qaoa_info(const qs_qaoa* q, int* fwd_passes, int* rev_passes, doubl
 
 qs_status qs_qaoa_max_cut(qs_qaoa* q, int* max_cut) {
   QS_CHECK(q != nullptr && max_cut != nullptr, "null argument");
+  if (!q->d_cut) {  // the two-shape passes form cut values in the kernels: build the array now
+    QS_CUDA(cudaMalloc(&q->d_cut, 1ull << q->n));
+    QS_TRY(launch_cut_values(q->d_cut, q->n, q->d_edges, q->n_edges, nullptr));
+  }
   if (!q->d_max) QS_CUDA(cudaMalloc(&q->d_max, sizeof(int)));
   QS_TRY(launch_max_u8(q->d_cut, 1ull << q->n, q->d_max, nullptr));
   QS_CUDA(cudaMemcpy(max_cut, q->d_max, sizeof(int), cudaMemcpyDeviceToHost));
@@ -635,6 +758,42 @@ qs_status run_qpasses(qs_qaoa* q, const std::vector<QPassDesc>& passes, const st
   return QS_OK;
 }
 
+qs_status run_xpasses(qs_qaoa* q, const std::vector<XPass>& passes, const std::vector<int>& two,
+                      const XPass* d_passes, void* psi, void* lam, double* partials, cudaStream_t st) {
+  const double S = 8.0 * (double)(1ull << q->n);
+  for (size_t i = 0; i < passes.size(); ++i) {
+    XLaunch L;
+    L.psi = reinterpret_cast<float2*>(psi);
+    L.il = reinterpret_cast<float4*>(q->d_il_priv);  // (psi, lam) interleaved, 16 bytes per amplitude
+    L.coef = reinterpret_cast<const float2*>(q->d_coef);
+    L.fs = q->d_xfs;
+    L.partials = partials;
+    L.stride = q->xstride;
+    L.grid = two[i] ? q->xgrid_r : q->xgrid_f;
+    L.n = q->n;
+    L.n_edges = q->n_edges;
+    TraceRec* rec = trace_begin(st);
+    QS_TRY(launch_qx_pass(two[i], d_passes + i, passes[i], L, st));
+    if (rec) {
+      const uint32_t f = passes[i].flags;
+      double b = 0;
+      if (!two[i]) {
+        b = ((f & XF_GEN_PLUS) ? 0 : S) + ((f & XF_STORE) ? S : 0);
+        rec->kind = QS_TRACE_QAOA_FWD;
+      } else if (f & XF_LOAD_PSI) {
+        b = S + ((f & XF_STORE) ? 2 * S : 0);
+        rec->kind = QS_TRACE_QAOA_TWO;
+      } else {
+        b = 2 * S + ((f & XF_STORE) ? 2 * S : 0);
+        rec->kind = QS_TRACE_QAOA_IL;
+      }
+      rec->bytes = b;
+      QS_CUDA(cudaEventRecord(rec->end, st));
+    }
+  }
+  return QS_OK;
+}
+
 qs_status qaoa_energy(qs_qaoa* q, qs_state* psi, const double* gamma, const double* beta, double* energy) {
   QS_TRY(qaoa_check(q, psi, gamma, beta));
   cudaStream_t st = psi->st;
@@ -642,6 +801,22 @@ qs_status qaoa_energy(qs_qaoa* q, qs_state* psi, const double* gamma, const doub
   QS_TRY(upload_table(q->host_coef, q->dt, q->d_coef, st, psi->host_out));
   const int n_slots = (int)q->eslots.out.size();
   const size_t part = (size_t)std::max(n_slots, 1) * q->grid2;
+  if (q->xp) {
+    const size_t xpart = (size_t)std::max(n_slots, 1) * q->xstride;
+    QS_TRY(ensure_scratch(psi, xpart + n_slots + 8));
+    double* d_part = psi->scratch;
+    double* d_slot = d_part + xpart;
+    double* d_out = d_slot + n_slots;
+    QS_CUDA(cudaMemsetAsync(d_part, 0, xpart * sizeof(double), st));
+    QS_TRY(run_xpasses(q, q->xe, q->xe_two, q->d_xe, psi->ptr, nullptr, d_part, st));
+    QS_TRY(launch_reduce_slots(d_part, n_slots, q->xstride, nullptr, d_slot, st));
+    QS_TRY(launch_param_gather(d_slot, q->e_row, q->e_sidx, q->e_w, 1, d_out, st));
+    if (energy) {
+      QS_CUDA(cudaMemcpyAsync(energy, d_out, sizeof(double), cudaMemcpyDeviceToHost, st));
+      QS_CUDA(cudaStreamSynchronize(st));
+    }
+    return QS_OK;
+  }
   QS_TRY(ensure_scratch(psi, part + n_slots + 8));
   double* d_part = psi->scratch;
   double* d_slot = d_part + part;
@@ -682,12 +857,16 @@ qs_status qs_qaoa_expectation_with_grad(qs_qaoa* q, qs_state* psi, qs_state* lam
   QS_TRY(upload_table(q->host_coef, q->dt, q->d_coef, st, psi->host_out));
   const int n_slots = (int)q->gslots.out.size();
   const int n_out = 1 + 2 * q->p;
-  const size_t part = (size_t)std::max(n_slots, 1) * q->grid2;
+  const size_t part = (size_t)std::max(n_slots, 1) * (q->xp ? q->xstride : q->grid2);
   QS_TRY(ensure_scratch(psi, part + n_slots + n_out + 8));
   double* d_part = psi->scratch;
   double* d_slot = d_part + part;
   double* d_out = d_slot + n_slots;
-  if (q->ck_after.empty()) {
+  if (q->xp) {
+    QS_CUDA(cudaMemsetAsync(d_part, 0, part * sizeof(double), st));
+    QS_TRY(run_xpasses(q, q->xg, q->xg_two, q->d_xg, psi->ptr, lam->ptr, d_part, st));
+    QS_TRY(launch_reduce_slots(d_part, n_slots, q->xstride, nullptr, d_slot, st));
+  } else if (q->ck_after.empty()) {
     QS_TRY(run_qpasses(q, q->gpass, q->gns, q->d_gpass, psi->ptr, lam->ptr, d_part, st));
   } else {
     // checkpoints: psi saved after the chosen forward passes and reloaded before
@@ -724,7 +903,7 @@ qs_status qs_qaoa_expectation_with_grad(qs_qaoa* q, qs_state* psi, qs_state* lam
     }
     QS_TRY(run_qpasses(q, q->gpass, q->gns, q->d_gpass, psi->ptr, lam->ptr, d_part, st, b, q->gpass.size()));
   }
-  QS_TRY(launch_reduce_slots(d_part, n_slots, q->grid2, nullptr, d_slot, st));
+  if (!q->xp) QS_TRY(launch_reduce_slots(d_part, n_slots, q->grid2, nullptr, d_slot, st));
   QS_TRY(launch_param_gather(d_slot, q->g_row, q->g_sidx, q->g_w, n_out, d_out, st));
   std::vector<double> h(n_out);
   QS_CUDA(cudaMemcpyAsync(h.data(), d_out, n_out * sizeof(double), cudaMemcpyDeviceToHost, st));

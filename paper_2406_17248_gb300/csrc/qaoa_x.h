@@ -1,0 +1,84 @@
+// Descriptors of the complex64 QAOA passes with separate forward and reverse
+// tile shapes (host planner <-> kernels).
+//
+// A pass stages one tile (2^m amplitudes over a bit set S that holds the low c
+// qubits) in shared memory and runs phases over it.  In a phase every thread
+// holds 16 amplitudes (4 register bits) of one sub-cube and applies, in order:
+//   step 1: RX on the register bits in m1 (coefficient c1),
+//   a diagonal step (cost phase, its gradient, or the energy),
+//   step 3: RX on the register bits in m3 (coefficient c3).
+// The cost value C(x) = |E| - 2 cut(x) of an amplitude is not read from memory:
+// cut(x) = fs[local index] + g(tile) + sum over the local bits set of w_i(tile),
+// where fs counts the edges inside S, and g, w_i come from the edges that leave S
+// and the tile's fixed (complement) bits.
+#pragma once
+
+#include "qsim_internal.h"
+
+namespace qs {
+
+constexpr int kXMaxPhases = 8;
+constexpr int kXMaxM = 13;
+constexpr int kXMaxComp = 40;
+
+enum XDiag : uint8_t {
+  XD_NONE = 0,
+  XD_COST = 1,       // psi *= lut[cut]
+  XD_COST_GRAD = 2,  // acc += C Im(conj(lam) psi); then psi, lam *= lut[cut]
+  XD_ENERGY = 3      // acc += C |psi|^2 (two-state kernel: also lam = C psi)
+};
+
+enum XFlags : uint32_t {
+  XF_GEN_PLUS = 1u,   // forward: the tile starts as |+> (nothing loaded)
+  XF_LOAD_PSI = 2u,   // two-state kernel: psi from the plain state, lam = 0
+  XF_STORE = 4u,      // store the tile (from the last phase's registers)
+  XF_GRAD1 = 8u,      // two-state kernel: step 1 accumulates Im <lam|X_q|psi>
+  XF_GRAD3 = 16u      // two-state kernel: step 3 accumulates Im <lam|X_q|psi>
+};
+
+struct XPhase {
+  uint64_t gbit[4];  // global (qubit) bit of each register bit
+  uint16_t spos[4];  // swizzled shared-memory position of each register bit
+  uint16_t lbit[4];  // local-index bit of each register bit
+  int8_t q[kXMaxM];  // sub-cube local bits, lane order
+  uint8_t nq;
+  uint8_t m1, m3;    // register-bit masks of steps 1 and 3
+  uint8_t diag;      // XDiag (at most one phase of a pass has one)
+  uint8_t pad[2];
+};
+
+struct XPass {
+  int m, c, n_phases;
+  uint32_t flags;
+  int c1, c3, cd;    // coefficient-table offsets (complex64 entries): step-1 (c, s), step-3 (c, s), diag LUT
+  int slot[3];       // output slot of accumulator 0 (step 1), 1 (diag), 2 (step 3); -1: none
+  int fs_off;        // byte offset of this pass's in-tile edge-count table (2^m bytes)
+  int ncomp;         // complement (tile-index) bits
+  int n_cc;          // complement nodes with complement neighbours above them
+  int pad;
+  int8_t comp[kXMaxComp];
+  uint8_t ccnode[kXMaxComp];
+  uint64_t ccmask[kXMaxComp];  // complement neighbours (above) of ccnode[k]
+  uint64_t wmask[kXMaxM];      // complement neighbours of tile (local) bit i
+  uint64_t hiA[64], hiB[64];   // global bits of local bits c..c+5 and c+6..c+11
+  XPhase ph[kXMaxPhases];
+};
+
+struct XLaunch {
+  float2* psi;                 // plain complex64 state
+  float4* il;                  // interleaved (psi.re, lam.re, psi.im, lam.im) per amplitude, 2^n entries
+  const float2* coef;
+  const uint8_t* fs;
+  double* partials;
+  int stride, grid, n, n_edges;
+};
+
+// two_state = 0: forward kernel (psi alone, 8-byte elements); 1: psi and lam
+// interleaved (16-byte elements).  Returns the resident CTAs per SM (0: does
+// not fit) for a tile of 2^m amplitudes.
+int qx_occupancy(int two_state, int m, int n_edges, int n_phases);
+int qx_grid(int two_state, int m, int n_edges, int n_phases, uint64_t n_tiles);
+qs_status launch_qx_pass(int two_state, const XPass* d_pass, const XPass& h_pass, const XLaunch& L,
+                         cudaStream_t st);
+
+}  // namespace qs

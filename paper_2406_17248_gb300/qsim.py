@@ -80,6 +80,7 @@ SIGNATURES = [
     ("qs_qaoa_evolve", [_VP, _VP, _PD, _PD]),
     ("qs_qaoa_expectation", [_VP, _VP, _PD, _PD, _PD]),
     ("qs_qaoa_expectation_with_grad", [_VP, _VP, _VP, _PD, _PD, _PD, _PD, _PD]),
+    ("qs_qaoa_xplan", [_I, _PI, _I, _I, _D, _I, _I, _I, C.POINTER(C.c_longlong), _I, _PI, _PI, _PD, _I, _PI]),
     ("qs_qaoa_evaluate", [_I, _PI, _I, _I, _D, _PD, _PD, _I, _PD, _PD, _PD]),
     ("qs_batch_create", [_I, _PI, _PI, _VP, _PI, _PU64, _PU64, _PD, _PI, _I, _VP, _PVP]),
     ("qs_batch_destroy", [_VP]),
@@ -628,6 +629,33 @@ def apply_matrix(state: State, targets, matrix, engine: int = 0) -> State:
     return state
 
 
+XPLAN_REC = 68
+
+
+def qaoa_xplan(n: int, edges, p: int, gamma_scale: float = 1.0, tile_bits: int = 0, low_bits: int = 0,
+               which: int = 0):
+    """The complex64 two-shape QAOA plan (qs_qaoa_xplan, host only): a list of
+    pass records (dicts) and the slot table [(output, weight)]."""
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    maxp, maxs = 512, 4096
+    rec = (C.c_longlong * (maxp * XPLAN_REC))()
+    so = (C.c_int * maxs)()
+    sw = (C.c_double * maxs)()
+    npass, nslot = C.c_int(), C.c_int()
+    _check(lib().qs_qaoa_xplan(n, e.ctypes.data_as(_PI), int(e.size // 2), p, gamma_scale, tile_bits, low_bits,
+                               which, rec, maxp, C.byref(npass), so, sw, maxs, C.byref(nslot)))
+    out = []
+    for i in range(npass.value):
+        r = rec[i * XPLAN_REC:(i + 1) * XPLAN_REC]
+        d = dict(two=r[0], flags=r[1], S=r[2], n_phases=r[3], c1=r[4], c3=r[5], cd=r[6], slot=r[7:10],
+                 m=r[10], c=r[11], phases=[])
+        for ph in range(r[3]):
+            q = r[12 + 7 * ph:12 + 7 * ph + 7]
+            d["phases"].append(dict(m1=q[0], m3=q[1], diag=q[2], reg=list(q[3:7])))
+        out.append(d)
+    return out, [(so[i], sw[i]) for i in range(nslot.value)]
+
+
 def expectation_noalloc(state: State, ham: I.PauliSum, stream=None) -> float:
     """<psi|H|psi> through qs_expectation_noalloc: no device allocation by the
     library (its working memory is a fixed array inside the library), for callers
@@ -683,12 +711,14 @@ class QAOA:
     """MaxCut QAOA engine: |+>^n, p layers of exp(-i gs gamma C) then RX(beta)."""
 
     def __init__(self, n: int, edges, p: int, gamma_scale: float = 1.0, dtype: int = C64,
-                 tile_bits: int = 0, low_bits: int = 0, checkpoint: int = 0):
-        """checkpoint > 0: adjoint state checkpoints every `checkpoint` layers."""
+                 tile_bits: int = 0, low_bits: int = 0, checkpoint: int = 0, engine: int = 0):
+        """checkpoint > 0: adjoint state checkpoints every `checkpoint` layers.
+        engine: 0 automatic, 1 the general tile passes, 2 the complex64
+        two-shape passes (tile_bits / low_bits then give the reverse tile)."""
         self.n, self.p, self.dtype = n, p, dtype
         e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
         self._edges = e
-        o = Options(0, tile_bits, low_bits, checkpoint)
+        o = Options(engine, tile_bits, low_bits, checkpoint)
         h = C.c_void_p()
         _check(lib().qs_qaoa_create(n, e.ctypes.data_as(_PI), int(e.size // 2), p, gamma_scale, dtype,
                                     C.byref(o), C.byref(h)))

@@ -403,3 +403,28 @@ def test_c128_real_and_unit_ops_fused(Q, opts):
     want = O.evolve(circ, [], psi0)
     got, _ = run_circuit(Q, circ, [], 1, psi0, **opts)
     check(f"c128 real/unit fused {opts}", state_err(got, want), TOL[1])
+
+
+@pytest.mark.parametrize("n,p,tb,lb,gs", [(14, 2, 9, 2, 0.5), (15, 3, 9, 3, 1.0), (16, 3, 10, 3, 0.5),
+                                          (18, 4, 11, 3, 0.5), (20, 8, 12, 3, 0.5), (21, 2, 12, 3, 1.0)])
+def test_qaoa_two_shape_passes(Q, n, p, tb, lb, gs):
+    """The complex64 passes with separate forward and reverse tile shapes (the
+    engine bench.py times at 30 qubits), forced with small tiles so that many
+    tiles and passes run: energy, gradients and the evolved state against the
+    oracle."""
+    edges = I.random_regular_graph(n, 3 if n % 2 == 0 else 4, seed=n)
+    ang = I.uniform_params(2 * p, n + 1, 0.0, np.pi)
+    E0, dg0, db0 = O.qaoa_expectation_with_grad(n, edges, ang[:p], ang[p:], gs)
+    q = Q.QAOA(n, edges, p, gamma_scale=gs, dtype=0, tile_bits=tb, low_bits=lb, engine=2)
+    psi, lam = Q.State(n, 0), Q.State(n, 0)
+    E, dg, db = q.expectation_with_grad(psi, lam, ang[:p], ang[p:])
+    te, tg, tb_ = qaoa_grad_tols(0, n, len(edges), gs)
+    tag = f"qaoa two-shape n={n} p={p}"
+    check(tag + " energy", abs(E - E0), te)
+    check(tag + " dgamma", np.abs(dg - dg0), tg)
+    check(tag + " dbeta", np.abs(db - db0), tb_)
+    check(tag + " energy-only", abs(q.expectation(psi, ang[:p], ang[p:]) - E0), te)
+    want = O.qaoa_layers_state(n, edges, ang[:p], ang[p:], gs)
+    check(tag + " state", state_err(psi.get_qs(), want), TOL[0])
+    # max cut from the lazily built cut-value array
+    assert q.max_cut() == O.maxcut_brute_force(n, edges)

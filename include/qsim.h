@@ -369,9 +369,13 @@ QS_API qs_status qs_qaoa_expectation_with_grad(qs_qaoa* q, qs_state* psi, qs_sta
  * (cos b/2, -sin b/2)), [7..9] output slot of accumulators 0..2 (-1 none),
  * [10] tile bits, [11] low bits, then per phase 7 entries: step-1 register
  * mask, step-3 register mask, diagonal (0 none, 1 cost, 2 cost gradient and
- * cost^dag, 3 energy), the qubits of register bits 0..3.  slot_out/slot_w:
- * output (0 = E, 1 + l = dgamma_l, 1 + p + l = dbeta_l) and weight per slot. */
-#define QS_XPLAN_REC 68
+ * cost^dag, 3 energy), the qubits of register bits 0..3 (8 phase slots), then
+ * at [68] and [85] the tile's load and store tensor maps, 17 entries each:
+ * log2 of 8-byte words per amplitude, local bits covered by one box, and per
+ * dimension 0..4 its first word-index bit, its width in bits and the box width
+ * in bits.  slot_out/slot_w: output (0 = E, 1 + l = dgamma_l, 1 + p + l =
+ * dbeta_l) and weight per slot. */
+#define QS_XPLAN_REC 102
 QS_API qs_status qs_qaoa_xplan(int n_qubits, const int* edges, int n_edges, int p, double gamma_scale, int tile_bits,
                                int low_bits, int which, long long* rec, int max_passes, int* n_passes,
                                int* slot_out, double* slot_w, int max_slots, int* n_slots);

@@ -8,16 +8,21 @@
 //   qx_kernel<true>:  psi and lam interleaved per amplitude as
 //                     (psi.re, lam.re, psi.im, lam.im), so one packed f32x2
 //                     FMA updates both states; the turnaround and reverse sweep.
-// A CTA of 2^(m-4) threads loops over tiles with the next tile's 16-byte
-// cp.async copies in flight.  Each phase gives every thread the 16 amplitudes of
-// one sub-cube (4 register bits), runs straight-line code for its steps (no op
-// interpreter), and writes back to shared memory; the last phase stores to HBM
-// straight from registers.  Tile buffers are aligned to their size in the
-// shared window, so an element's address is the XOR of a per-thread base and a
-// per-register-index offset (the tile swizzle is linear over GF(2)).  C(x) is
-// assembled per amplitude from a per-pass table of in-tile edge counts and
-// per-tile linear terms (computed by warp 0 for the next tile while the current
-// one is processed), so no cut-value array is read.
+// A CTA holds 2^(m-4) compute threads and one producer warp, and loops over
+// tiles through a ring of three tile buffers.  The producer moves whole rows
+// (runs of 2^c contiguous amplitudes) between HBM and shared memory with bulk
+// asynchronous copies completing on mbarriers, so no compute warp ever issues
+// a global load or store and HBM back-pressure never stalls the arithmetic.
+// Each phase gives every compute thread the 16 amplitudes of one sub-cube, runs
+// straight-line code for its steps (one compiled body per step shape), and
+// writes back to shared memory.  Tiles are plain copies of the HBM rows (bulk
+// copies do not swizzle); where a phase's register bits include bank-column
+// bits, a lane XOR-relabels its register index so the lanes of a quarter warp
+// still hit distinct banks.  C(x) is assembled per amplitude from a per-pass
+// table of in-tile edge counts and per-tile linear terms (computed by warp 0
+// two tiles ahead), so no cut-value array is read.
+#include <cuda.h>
+
 #include <cmath>
 #include <type_traits>
 
@@ -29,15 +34,9 @@ namespace qs {
 namespace {
 
 constexpr int kXN = 16;  // amplitudes per thread per phase
-constexpr int kXNB = 2;  // tile buffers
+constexpr int kXNB = 3;  // tile buffers: the current tile, the next one landing, the one after issued
 
 __device__ __forceinline__ uint32_t xsh(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void xcp16(uint32_t s, const void* gmem) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void xcommit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void xwait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void xwait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 __device__ __forceinline__ float2 lds64(uint32_t a) {
   float2 v;
   asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a));
@@ -48,6 +47,11 @@ __device__ __forceinline__ float4 lds128(uint32_t a) {
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
   return v;
 }
+__device__ __forceinline__ uint32_t ldsu8(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u8 %0, [%1];\n" : "=r"(v) : "r"(a));
+  return v;
+}
 __device__ __forceinline__ void sts64(uint32_t a, float x, float y) {
   asm volatile("st.shared.v2.f32 [%0], {%1, %2};\n" ::"r"(a), "f"(x), "f"(y));
 }
@@ -56,6 +60,7 @@ __device__ __forceinline__ void sts128(uint32_t a, float x, float y, float z, fl
 }
 
 struct XArgs {
+  CUtensorMap tm[2];  // tile copies: [0] load, [1] store
   const XPass* pass;
   float2* psi;
   float4* il;
@@ -87,10 +92,10 @@ __device__ __forceinline__ void xrx1(float2 (&a)[kXN], float c, float s) {
 }
 // ---------------------------------------------------------------- two-state steps
 // RE = (psi.re, lam.re), IM = (psi.im, lam.im): RX(c, s) on both states at once
-template <int RB>
-__device__ __forceinline__ void xrx2(float2 (&RE)[kXN], float2 (&IM)[kXN], float2 c2, float2 s2, float2 ms2) {
+template <int RB, int N>
+__device__ __forceinline__ void xrx2(float2 (&RE)[N], float2 (&IM)[N], float2 c2, float2 s2, float2 ms2) {
 #pragma unroll
-  for (int j = 0; j < kXN; ++j) {
+  for (int j = 0; j < N; ++j) {
     if (j & (1 << RB)) continue;
     const int j1 = j | (1 << RB);
     const float2 r0 = RE[j], i0 = IM[j], r1 = RE[j1], i1 = IM[j1];
@@ -101,11 +106,11 @@ __device__ __forceinline__ void xrx2(float2 (&RE)[kXN], float2 (&IM)[kXN], float
   }
 }
 // Im <lam|X_RB|psi> over the sub-cube (four independent partial sums)
-template <int RB>
-__device__ __forceinline__ float xgx2(const float2 (&RE)[kXN], const float2 (&IM)[kXN]) {
+template <int RB, int N>
+__device__ __forceinline__ float xgx2(const float2 (&RE)[N], const float2 (&IM)[N]) {
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
-  for (int j = 0; j < kXN; ++j) {
+  for (int j = 0; j < N; ++j) {
     if (j & (1 << RB)) continue;
     const int j1 = j | (1 << RB);
     s0 = __fmaf_rn(RE[j].y, IM[j1].x, s0);
@@ -124,18 +129,15 @@ __device__ __forceinline__ void xacc(float& hi, float& lo, float x) {  // compen
 
 // Per-phase context of one thread (all values uniform across the phase code).
 struct XPh {
-  uint32_t pb;                  // shared address of the sub-cube base element
+  uint32_t tb;                  // shared address of the tile buffer
+  uint32_t pb;                  // byte offset of the sub-cube base element in the tile
   uint32_t sp0, sp1, sp2, sp3;  // byte offsets of the register bits (XOR)
-  uint32_t l0, lb0, lb1, lb2, lb3;
+  uint32_t l0, lb0, lb1, lb2, lb3;  // l0: local index of register index 0 (relabel bits included)
   int cutb, w0, w1, w2, w3;     // cut value = fs[l0 | L(j)] + cutb + W(j)
-  const uint8_t* fs;
-  const float2* lut;
+  uint32_t fs, lut;             // shared addresses of the edge-count table and the LUT
   int ne;
   float2 cs1, cs3;
-  bool last, store;
   float plus;
-  char* gbase;                  // HBM address of the sub-cube base (last phase)
-  uint64_t gb0, gb1, gb2, gb3;  // byte offsets of the register bits in HBM
 };
 
 // Register-index sums: L(j) = OR of the local bits, S(j) = XOR of the shared
@@ -144,9 +146,9 @@ struct XPh {
 #define XL(j) ((((j) & 1) ? h.lb0 : 0u) | (((j) & 2) ? h.lb1 : 0u) | (((j) & 4) ? h.lb2 : 0u) | (((j) & 8) ? h.lb3 : 0u))
 #define XS(j) ((((j) & 1) ? h.sp0 : 0u) ^ (((j) & 2) ? h.sp1 : 0u) ^ (((j) & 4) ? h.sp2 : 0u) ^ (((j) & 8) ? h.sp3 : 0u))
 #define XW(j) ((((j) & 1) ? h.w0 : 0) + (((j) & 2) ? h.w1 : 0) + (((j) & 4) ? h.w2 : 0) + (((j) & 8) ? h.w3 : 0))
-#define XG(j) ((((j) & 1) ? h.gb0 : 0ull) + (((j) & 2) ? h.gb1 : 0ull) + (((j) & 4) ? h.gb2 : 0ull) + (((j) & 8) ? h.gb3 : 0ull))
 // cut value of element j, kept inside the LUT (0..|E|) whatever the tables hold
-#define XCUT(j) ((int)min((unsigned)((int)h.fs[h.l0 | XL(j)] + h.cutb + XW(j)), (unsigned)h.ne))
+#define XCUT(j) ((int)min((unsigned)((int)ldsu8(h.fs + (h.l0 ^ XL(j))) + h.cutb + XW(j)), (unsigned)h.ne))
+
 
 // RX on the first K register bits
 template <int K>
@@ -156,8 +158,8 @@ __device__ __forceinline__ void xrx1_k(float2 (&a)[kXN], float2 cs) {
   if (K > 2) xrx1<2>(a, cs.x, cs.y);
   if (K > 3) xrx1<3>(a, cs.x, cs.y);
 }
-template <int K>
-__device__ __forceinline__ float xrx2_k(float2 (&RE)[kXN], float2 (&IM)[kXN], float2 cs) {
+template <int K, int N>
+__device__ __forceinline__ float xrx2_k(float2 (&RE)[N], float2 (&IM)[N], float2 cs) {
   const float2 c2 = make_float2(cs.x, cs.x), s2 = make_float2(cs.y, cs.y), ms2 = make_float2(-cs.y, -cs.y);
   float g = 0.f;
   if (K > 0) {
@@ -188,13 +190,13 @@ __device__ __forceinline__ void xphase1(const XPh& h, float (&acc)[3]) {
     for (int j = 0; j < kXN; ++j) a[j] = make_float2(h.plus, 0.f);
   } else {
 #pragma unroll
-    for (int j = 0; j < kXN; ++j) a[j] = lds64(h.pb ^ XS(j));
+    for (int j = 0; j < kXN; ++j) a[j] = lds64(h.tb + (h.pb ^ XS(j)));
   }
   xrx1_k<K1>(a, h.cs1);
   if (DG == XD_COST) {
 #pragma unroll
     for (int j = 0; j < kXN; ++j) {
-      const float2 d = h.lut[XCUT(j)];
+      const float2 d = lds64(h.lut + 8u * XCUT(j));
       const float2 x = a[j];
       a[j].x = __fmaf_rn(d.x, x.x, -d.y * x.y);
       a[j].y = __fmaf_rn(d.x, x.y, d.y * x.x);
@@ -211,29 +213,19 @@ __device__ __forceinline__ void xphase1(const XPh& h, float (&acc)[3]) {
     acc[1] += e0 + e1;
   }
   xrx1_k<K3>(a, h.cs3);
-  if (!h.last) {
 #pragma unroll
-    for (int j = 0; j < kXN; ++j) sts64(h.pb ^ XS(j), a[j].x, a[j].y);
-  } else if (h.store) {
-    if (h.gb0 == 8) {  // register bit 0 is qubit 0: pairs are adjacent in HBM
-#pragma unroll
-      for (int j = 0; j < kXN; j += 2)
-        __stcs(reinterpret_cast<float4*>(h.gbase + XG(j)), make_float4(a[j].x, a[j].y, a[j + 1].x, a[j + 1].y));
-    } else {
-#pragma unroll
-      for (int j = 0; j < kXN; ++j) __stcs(reinterpret_cast<float2*>(h.gbase + XG(j)), a[j]);
-    }
-  }
+  for (int j = 0; j < kXN; ++j) sts64(h.tb + (h.pb ^ XS(j)), a[j].x, a[j].y);
 }
 
 // One phase of the two-state kernel: the mixer steps take Im <lam|X_q|psi>
 // into acc[0] (step 1) and acc[2] (step 3) before rotating both states.
 template <int K1, int DG, int K3>
 __device__ __forceinline__ void xphase2(const XPh& h, float (&acc)[3]) {
-  float2 RE[kXN], IM[kXN];
+  constexpr int N = 1 << qx_reg_bits(true);
+  float2 RE[N], IM[N];
 #pragma unroll
-  for (int j = 0; j < kXN; ++j) {
-    const float4 e = lds128(h.pb ^ XS(j));
+  for (int j = 0; j < N; ++j) {
+    const float4 e = lds128(h.tb + (h.pb ^ XS(j)));
     RE[j] = make_float2(e.x, e.y);
     IM[j] = make_float2(e.z, e.w);
   }
@@ -241,13 +233,13 @@ __device__ __forceinline__ void xphase2(const XPh& h, float (&acc)[3]) {
   if (DG == XD_COST_GRAD) {
     float g0 = 0.f, g1 = 0.f;
 #pragma unroll
-    for (int j = 0; j < kXN; ++j) {
+    for (int j = 0; j < N; ++j) {
       const int k = XCUT(j);
       const float C = (float)(h.ne - 2 * k);
       const float im = __fmaf_rn(RE[j].y, IM[j].x, -IM[j].y * RE[j].x);  // Im(conj(lam) psi)
       if (j & 1) g1 = __fmaf_rn(C, im, g1);
       else g0 = __fmaf_rn(C, im, g0);
-      const float2 d = h.lut[k];
+      const float2 d = lds64(h.lut + 8u * (uint32_t)k);
       const float2 dr = make_float2(d.x, d.x), di = make_float2(d.y, d.y), mdi = make_float2(-d.y, -d.y);
       const float2 r = RE[j], i = IM[j];
       RE[j] = __ffma2_rn(dr, r, __fmul2_rn(mdi, i));
@@ -257,7 +249,7 @@ __device__ __forceinline__ void xphase2(const XPh& h, float (&acc)[3]) {
   } else if (DG == XD_ENERGY) {
     float e0 = 0.f, e1 = 0.f;
 #pragma unroll
-    for (int j = 0; j < kXN; ++j) {
+    for (int j = 0; j < N; ++j) {
       const float C = (float)(h.ne - 2 * XCUT(j));
       const float pr = __fmaf_rn(RE[j].x, RE[j].x, IM[j].x * IM[j].x);
       if (j & 1) e1 = __fmaf_rn(C, pr, e1);
@@ -268,14 +260,8 @@ __device__ __forceinline__ void xphase2(const XPh& h, float (&acc)[3]) {
     acc[1] += e0 + e1;
   }
   if (K3 > 0) acc[2] += xrx2_k<K3>(RE, IM, h.cs3);
-  if (!h.last) {
 #pragma unroll
-    for (int j = 0; j < kXN; ++j) sts128(h.pb ^ XS(j), RE[j].x, RE[j].y, IM[j].x, IM[j].y);
-  } else if (h.store) {
-#pragma unroll
-    for (int j = 0; j < kXN; ++j)
-      __stcs(reinterpret_cast<float4*>(h.gbase + XG(j)), make_float4(RE[j].x, RE[j].y, IM[j].x, IM[j].y));
-  }
+  for (int j = 0; j < N; ++j) sts128(h.tb + (h.pb ^ XS(j)), RE[j].x, RE[j].y, IM[j].x, IM[j].y);
 }
 
 // Phase code: K1 + 5 DIAG + 25 K3 (+ 125 for the |+> start of the forward sweep).
@@ -311,83 +297,140 @@ __device__ __forceinline__ bool xdispatch2(int code, const XPh& h, float (&acc)[
   }
 }
 
+// Bulk (TMA engine) copies of contiguous runs: HBM -> shared memory completing
+// on an mbarrier's transaction count, and shared memory -> HBM in bulk groups.
+// five-dimensional tiled tensor copies (TMA); the tensor map lives in kernel parameter space
+__device__ __forceinline__ void tma_load5(uint32_t dst, const CUtensorMap* map, const int (&x)[5], uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];\n" ::"r"(dst),
+      "l"(map), "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store5(const CUtensorMap* map, const int (&x)[5], uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];\n" ::"l"(
+                   map),
+               "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// mbarrier helpers (shared::cta addresses).  Waits are bounded: on timeout
+// they return false and the kernel records a fault instead of hanging.
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared.b64 st, [%0];\n}\n" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(uint32_t a, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(a), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+  for (long long it = 0; it < (1ll << 26); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void xbar_compute(int nthreads) {  // named barrier of the compute warps
+  asm volatile("bar.sync 1, %0;\n" ::"r"(nthreads) : "memory");
+}
+
+// Block: T = 2^(m-R) compute threads plus one producer warp.  The producer
+// moves every tile between HBM and shared memory (16-byte cp.async copies in,
+// 16-byte stores out) through a ring of three tile buffers, so the compute warps
+// never stall on HBM back-pressure; mbarriers hand buffers over: full[b] when a
+// tile's copies have landed, done[b] when the compute warps have finished it.
 template <bool TWO>
-__global__ void __launch_bounds__(TWO ? 256 : 512, 1) qx_kernel(XArgs args) {
+__global__ void __launch_bounds__(TWO ? 288 : 544, 1) qx_kernel(const __grid_constant__ XArgs args) {
   constexpr uint32_t ES = TWO ? 16 : 8;  // bytes per shared-memory element
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ XPass P;
-  __shared__ uint64_t s_gk[16], s_dep[5][64];
-  __shared__ uint32_t s_pk[16];
-  __shared__ int s_lin[2][16];  // per tile parity: w_i of local bit i (i < 13), g at [15]
-  __shared__ double s_red[16];
+  __shared__ uint64_t s_dep[5][64];
+  __shared__ int s_lin[kXNB][16];  // per tile buffer: w_i of local bit i (i < 13), g at [15]
+  __shared__ double s_red[17];
   __shared__ int s_bad;
+  __shared__ __align__(8) uint64_t s_full[kXNB], s_done[kXNB];
+  const int tid = threadIdx.x, NT = blockDim.x, T = NT - 32, lane = tid & 31, warp = tid >> 5;
+  const bool producer = tid >= T;
   {
     const int* src = reinterpret_cast<const int*>(args.pass);
     int* dst = reinterpret_cast<int*>(&P);
-    for (int i = threadIdx.x; i < (int)(sizeof(XPass) / 4); i += blockDim.x) dst[i] = src[i];
-    if (threadIdx.x == 0) s_bad = 0;
+    for (int i = tid; i < (int)(sizeof(XPass) / 4); i += NT) dst[i] = src[i];
+    if (tid == 0) {
+      s_bad = 0;
+      for (int b = 0; b < kXNB; ++b) {
+        mbar_init(xsh(&s_full[b]), 1);
+        mbar_init(xsh(&s_done[b]), (uint32_t)T);
+      }
+    }
   }
   __syncthreads();
-  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int m = P.m, n_ph = P.n_phases;
   const uint32_t flags = P.flags, tile_n = 1u << m, tile_bytes = tile_n * ES;
   const int E1 = args.n_edges + 1;
   bool has_diag = false;
   for (int i = 0; i < n_ph; ++i) has_diag |= P.ph[i].diag != XD_NONE;
 
-  // ---- shared memory: LUT | in-tile edge counts | phase bases | tiles (aligned to their size)
+  // ---- shared memory: LUT | in-tile edge counts | phase bases | tile buffers
   float2* s_lut = reinterpret_cast<float2*>(smem);
   size_t off = ((size_t)E1 * 8 + 127) & ~(size_t)127;
   uint8_t* s_fs = smem + off;
   off += ((size_t)tile_n + 127) & ~(size_t)127;
   uint32_t* s_pl = reinterpret_cast<uint32_t*>(smem + off);
   off += (size_t)kXMaxPhases * T * 4;
-  const uint32_t sh0 = xsh(smem);
-  const uint32_t tile0 = (sh0 + (uint32_t)off + tile_bytes - 1) & ~(tile_bytes - 1);
-  const uint32_t tsh[kXNB] = {tile0, tile0 + tile_bytes};
+  // tiled tensor copies need 128-byte aligned shared addresses; the dynamic
+  // shared block follows the static variables and is only 16-byte aligned
+  const uint32_t tile0 = (xsh(smem) + (uint32_t)off + 127u) & ~127u;
+  // shared address of tile buffer b (arithmetic: an indexed array would live in local memory)
+  auto tsh = [&](int b) { return tile0 + (uint32_t)b * tile_bytes; };
 
   if (P.cd >= 0)
-    for (int i = tid; i < E1; i += T) s_lut[i] = args.coef[P.cd + i];
+    for (int i = tid; i < E1; i += NT) s_lut[i] = args.coef[P.cd + i];
   if (has_diag && P.fs_off >= 0) {
     const uint4* src = reinterpret_cast<const uint4*>(args.fs + P.fs_off);
-    for (uint32_t i = tid; i < (tile_n >> 4); i += T) reinterpret_cast<uint4*>(s_fs)[i] = src[i];
+    for (uint32_t i = tid; i < (tile_n >> 4); i += NT) reinterpret_cast<uint4*>(s_fs)[i] = src[i];
   }
   const float2 cs1 = P.c1 >= 0 ? args.coef[P.c1] : make_float2(1.f, 0.f);
   const float2 cs3 = P.c3 >= 0 ? args.coef[P.c3] : make_float2(1.f, 0.f);
-  // phase bases of this thread: (local index << 16) | swizzled position
-  for (int ph = 0; ph < n_ph; ++ph) {
+  // phase bases of each compute thread: (local index << 8) | relabel mask.
+  // Tiles are unswizzled copies of the HBM runs, so an element's bank column is
+  // its low local bits; where some of those are register bits, lanes kq..kq+kn-1
+  // XOR the thread's register index with a mask kappa: register j then holds
+  // element l0 | L(j ^ kappa) = (l0 | L(kappa)) ^ L(j).  The RX butterflies and
+  // the gradient sums are symmetric in the two elements of a pair, so they are
+  // unchanged; addresses, cut indices and weights take the relabel into account.
+  for (int i = tid; i < n_ph * T; i += NT) {
+    const int ph = i / T, t = i % T;
     const XPhase& PH = P.ph[ph];
-    uint32_t l0 = 0;
-    for (int i = 0; i < PH.nq; ++i) l0 |= ((uint32_t)(tid >> i) & 1u) << PH.q[i];
-    s_pl[ph * T + tid] = (l0 << 16) | qaoa_swizzle(!TWO, l0);
+    uint32_t l0 = 0, kap = 0;
+    for (int q = 0; q < PH.nq; ++q) l0 |= ((uint32_t)(t >> q) & 1u) << PH.q[q];
+    for (int k = 0; k < PH.kn; ++k) kap |= ((uint32_t)(t >> (PH.kq + k)) & 1u) << PH.kidx[k];
+    for (int r = 0; r < 4; ++r)
+      if ((kap >> r) & 1u) l0 |= PH.lbit[r];
+    s_pl[ph * T + t] = (l0 << 8) | kap;
   }
-  // global index of the last phase's sub-cube base (its stores go straight to HBM)
-  const uint64_t g_last = x_l2g(P, s_pl[(n_ph - 1) * T + tid] >> 16);
   // tile index -> complement bits, 6 bits per table
-  for (int i = tid; i < 5 * 64; i += T) {
+  for (int i = tid; i < 5 * 64; i += NT) {
     const int tb = i >> 6, v = i & 63;
     uint64_t o = 0;
     for (int k = 0; k < 6; ++k)
       if (((v >> k) & 1) && 6 * tb + k < P.ncomp) o |= 1ull << P.comp[6 * tb + k];
     s_dep[tb][v] = o;
   }
-  // copy addressing: thread tid copies chunks ch = tid + k T of 16 bytes (two
-  // amplitudes of psi, or one interleaved element; the turnaround reads psi
-  // pairs into the slot of the pair's first element).  Global offsets are byte
-  // offsets: the tile offset, the thread's part and the chunk's part cover
-  // disjoint qubits, so they add.
-  const bool rd_il = TWO && !(flags & XF_LOAD_PSI);
-  const uint32_t EPC = rd_il ? 1u : 2u;
-  const uint64_t GE = rd_il ? 16u : 8u;  // bytes per amplitude in HBM of the loaded array
-  const uint32_t nk = tile_n / EPC / T;
-  for (uint32_t k = tid; k < nk; k += T) {
-    s_gk[k] = x_l2g(P, k * T * EPC) * GE;
-    s_pk[k] = qaoa_swizzle(!TWO, k * T * EPC) * ES;
-  }
-  const uint64_t gt = x_l2g(P, tid * EPC) * GE;
-  const uint32_t pt = qaoa_swizzle(!TWO, tid * EPC) * ES;
-  const char* src_base = rd_il ? reinterpret_cast<const char*>(args.il) : reinterpret_cast<const char*>(args.psi);
-  char* dst_base = TWO ? reinterpret_cast<char*>(args.il) : reinterpret_cast<char*>(args.psi);
+  constexpr uint64_t GST = TWO ? 16u : 8u;  // HBM bytes per amplitude of the stored array
+  const bool ld_psi8 = TWO && (flags & XF_LOAD_PSI);
+  const uint64_t GLD = (TWO && !ld_psi8) ? 16u : 8u;
   __syncthreads();
 
   const uint64_t n_tiles = 1ull << (args.n - m);
@@ -395,122 +438,156 @@ __global__ void __launch_bounds__(TWO ? 256 : 512, 1) qx_kernel(XArgs args) {
     return s_dep[0][t & 63] | s_dep[1][(t >> 6) & 63] | s_dep[2][(t >> 12) & 63] | s_dep[3][(t >> 18) & 63] |
            s_dep[4][(t >> 24) & 63];
   };
-  // linear terms of C for tile t (warp 0): w_i = deg_out(i) - 2 #(outside neighbours set), g
-  auto lin_terms = [&](uint64_t t, int par) {
-    const uint64_t toff = toff_of(t);
-    int g = 0;
-    if (lane < m) {
-      const uint64_t wm = P.wmask[lane];
-      const int set = __popcll(toff & wm);
-      s_lin[par][lane] = __popcll(wm) - 2 * set;
-      g += set;  // crossing edges (i, b): [x_i != x_b] = x_b + x_i (1 - 2 x_b)
-    }
-    for (int k = lane; k < P.n_cc; k += 32) {
-      const int a = P.ccnode[k];
-      const uint64_t cm = P.ccmask[k];
-      const int cnt = __popcll(toff & cm);
-      g += ((toff >> a) & 1ull) ? __popcll(cm) - cnt : cnt;
-    }
-    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-    if (lane == 0) s_lin[par][15] = g;
-  };
-  auto issue = [&](uint64_t t, uint32_t tb) {
-    if (!(flags & XF_GEN_PLUS)) {
-      const char* gb = src_base + toff_of(t) * GE + gt;
-      const uint32_t db = tb ^ pt;
-      for (uint32_t k = 0; k < nk; ++k) xcp16(db ^ s_pk[k], gb + s_gk[k]);
-    }
-    xcommit();
-  };
-
   float acc_hi[3] = {0.f, 0.f, 0.f}, acc_lo[3] = {0.f, 0.f, 0.f};
 
-  uint64_t tile = blockIdx.x;
-  if (tile < n_tiles) {
-    issue(tile, tsh[0]);
-    if (has_diag && warp == 0) lin_terms(tile, 0);
-  } else {
-    xcommit();
-  }
-  for (int it = 0; tile < n_tiles; ++it, tile += gridDim.x) {
-    const int cur = it & 1;
-    const uint64_t next = tile + gridDim.x;
-    if (next < n_tiles) {
-      issue(next, tsh[cur ^ 1]);
-      if (has_diag && warp == 0) lin_terms(next, cur ^ 1);
-    } else {
-      xcommit();
-    }
-    xwait1();
-    const uint32_t tb = tsh[cur];
-    if (TWO && (flags & XF_LOAD_PSI)) {
-      // turnaround: the pair (psi_l, psi_l+1) landed in the slot of l; spread it
-      // into two elements (psi, lam = 0); slot(l + 1) = slot(l) ^ 1
-      for (uint32_t k = 0; k < nk; ++k) {
-        const uint32_t a = tb ^ pt ^ s_pk[k];
-        const float4 v = lds128(a);
-        sts128(a, v.x, 0.f, v.y, 0.f);
-        sts128(a ^ 16u, v.z, 0.f, v.w, 0.f);
-      }
-    }
-    __syncthreads();
-    const uint64_t toff = toff_of(tile);
-    const int* lin = s_lin[cur];
-    float acc[3] = {0.f, 0.f, 0.f};
-
-    for (int ph = 0; ph < n_ph; ++ph) {
-      const XPhase& PH = P.ph[ph];
-      const uint32_t pl = s_pl[ph * T + tid];
-      XPh h;
-      h.l0 = pl >> 16;
-      h.pb = tb ^ ((pl & 0xffffu) * ES);
-      h.sp0 = PH.spos[0] * ES;
-      h.sp1 = PH.spos[1] * ES;
-      h.sp2 = PH.spos[2] * ES;
-      h.sp3 = PH.spos[3] * ES;
-      h.lb0 = PH.lbit[0];
-      h.lb1 = PH.lbit[1];
-      h.lb2 = PH.lbit[2];
-      h.lb3 = PH.lbit[3];
-      h.fs = s_fs;
-      h.lut = s_lut;
-      h.ne = args.n_edges;
-      h.cs1 = cs1;
-      h.cs3 = cs3;
-      h.plus = args.plus_amp;
-      h.last = ph == n_ph - 1;
-      h.store = (flags & XF_STORE) != 0;
-      h.cutb = h.w0 = h.w1 = h.w2 = h.w3 = 0;
-      const int diag = PH.diag;
-      if (diag) {  // cut values: fs[l] + g + sum of w over the set local bits
-        int cb = lin[15];
-        for (uint32_t x = h.l0; x; x &= x - 1) cb += lin[__ffs(x) - 1];
-        h.cutb = cb;
-        h.w0 = lin[__ffs(h.lb0) - 1];
-        h.w1 = lin[__ffs(h.lb1) - 1];
-        h.w2 = lin[__ffs(h.lb2) - 1];
-        h.w3 = lin[__ffs(h.lb3) - 1];
-      }
-      if (h.last) {
-        h.gbase = dst_base + (toff + g_last) * ES;
-        h.gb0 = PH.gbit[0] * ES;
-        h.gb1 = PH.gbit[1] * ES;
-        h.gb2 = PH.gbit[2] * ES;
-        h.gb3 = PH.gbit[3] * ES;
-      } else {
-        h.gbase = nullptr;
-        h.gb0 = h.gb1 = h.gb2 = h.gb3 = 0;
-      }
-      const int code = xcode(__popc(PH.m1), diag, __popc(PH.m3)) + ((flags & XF_GEN_PLUS) && ph == 0 ? 125 : 0);
-      const bool ok = TWO ? xdispatch2(code, h, acc) : xdispatch1(code, h, acc);
-      if (!ok && tid == 0) s_bad = 1;
-      if (!h.last) __syncthreads();
-    }
+  if (producer) {
+    // ------------------------------------------------------------ producer warp
+    // a tile is 2^(m - mlb) boxes of one tensor map; lane j copies box j, whose
+    // tile-local offset j 2^mlb sets the local bits above the box
+    const bool gen = (flags & XF_GEN_PLUS) != 0, do_store = (flags & XF_STORE) != 0;
+    auto coords = [&](int k, uint64_t amp, int (&x)[5]) {  // word index -> five coordinates
+      const uint64_t wi = amp << P.me[k];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) xacc(acc_hi[k], acc_lo[k], acc[k]);
-    __syncthreads();  // this buffer is refilled by the copies issued in the next iteration
+      for (int d = 0; d < 5; ++d) x[d] = (int)((wi >> P.ma[k][d]) & ((1ull << P.mw[k][d]) - 1ull));
+    };
+    auto load = [&](uint64_t t, int b) {  // tile t into buffer b, completing full[b]
+      if (t >= n_tiles) return;
+      const uint32_t fb = xsh(&s_full[b]);
+      if (gen) {
+        if (lane == 0) mbar_arrive(fb);
+        return;
+      }
+      if (lane == 0) mbar_arrive_expect(fb, tile_n * (uint32_t)GLD);
+      __syncwarp();
+      const uint64_t toff = toff_of(t);
+      const uint32_t nb = 1u << (m - P.mlb[0]), bb = (1u << P.mlb[0]) * (uint32_t)GLD;
+      for (uint32_t j = lane; j < nb; j += 32) {
+        int x[5];
+        coords(0, toff + x_l2g(P, j << P.mlb[0]), x);
+        tma_load5(tsh(b) + j * bb, &args.tm[0], x, fb);
+      }
+    };
+    auto store = [&](uint64_t t, int b) {  // tile t from buffer b to HBM
+      const uint64_t toff = toff_of(t);
+      const uint32_t nb = 1u << (m - P.mlb[1]), bb = (1u << P.mlb[1]) * (uint32_t)GST;
+      for (uint32_t j = lane; j < nb; j += 32) {
+        int x[5];
+        coords(1, toff + x_l2g(P, j << P.mlb[1]), x);
+        tma_store5(&args.tm[1], x, tsh(b) + j * bb);
+      }
+      bulk_commit();
+      bulk_wait_read0();  // the buffer may be refilled once the stores have read it
+    };
+    uint64_t tile = blockIdx.x;
+    load(tile, 0);
+    load(tile + gridDim.x, 1);
+    int i = 0;
+    for (; tile < n_tiles; tile += gridDim.x, ++i) {
+      const int b2 = (i + 2) % kXNB;  // the previous tile's buffer, refilled with the tile two ahead
+      if (i >= 1) {
+        if (!mbar_wait(xsh(&s_done[b2]), (uint32_t)(((i - 1) / kXNB) & 1))) s_bad = 2;
+        if (do_store) store(tile - gridDim.x, b2);
+      }
+      load(tile + 2ull * gridDim.x, b2);
+    }
+    if (i >= 1) {  // the last tile
+      const int bl = (i - 1) % kXNB;
+      if (!mbar_wait(xsh(&s_done[bl]), (uint32_t)(((i - 1) / kXNB) & 1))) s_bad = 2;
+      if (do_store) store(tile - gridDim.x, bl);
+    }
+    bulk_wait0();
+  } else {
+    // ------------------------------------------------------------ compute warps
+    // linear terms of C for tile t (warp 0): w_i = deg_out(i) - 2 #(outside neighbours set), g
+    auto lin_terms = [&](uint64_t t, int par) {
+      const uint64_t toff = toff_of(t);
+      int g = 0;
+      if (lane < m) {
+        const uint64_t wm = P.wmask[lane];
+        const int set = __popcll(toff & wm);
+        s_lin[par][lane] = __popcll(wm) - 2 * set;
+        g += set;  // crossing edges (i, b): [x_i != x_b] = x_b + x_i (1 - 2 x_b)
+      }
+      for (int k = lane; k < P.n_cc; k += 32) {
+        const int a = P.ccnode[k];
+        const uint64_t cm = P.ccmask[k];
+        const int cnt = __popcll(toff & cm);
+        g += ((toff >> a) & 1ull) ? __popcll(cm) - cnt : cnt;
+      }
+      for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+      if (lane == 0) s_lin[par][15] = g;
+    };
+    uint64_t tile = blockIdx.x;
+    if (has_diag && warp == 0) {
+      if (tile < n_tiles) lin_terms(tile, 0);
+      if (tile + gridDim.x < n_tiles) lin_terms(tile + gridDim.x, 1);
+    }
+    xbar_compute(T);
+    int i = 0;
+    for (; tile < n_tiles; tile += gridDim.x, ++i) {
+      const int cur = i % kXNB;
+      const uint64_t t2 = tile + 2ull * gridDim.x;
+      if (has_diag && warp == 0 && t2 < n_tiles) lin_terms(t2, (i + 2) % kXNB);
+      if (!mbar_wait(xsh(&s_full[cur]), (uint32_t)((i / kXNB) & 1))) s_bad = 2;
+      const uint32_t tb = tsh(cur);
+      if (ld_psi8) {  // turnaround: the tile came in as 8-byte psi amplitudes; expand them in place to
+                      // (psi.re, 0, psi.im, 0) elements (all threads read, then all write)
+        float2 v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = lds64(tb + 8u * ((uint32_t)tid + (uint32_t)T * k));
+        xbar_compute(T);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) sts128(tb + 16u * ((uint32_t)tid + (uint32_t)T * k), v[k].x, 0.f, v[k].y, 0.f);
+        xbar_compute(T);
+      }
+      const int* lin = s_lin[cur];
+      float acc[3] = {0.f, 0.f, 0.f};
+      for (int ph = 0; ph < n_ph; ++ph) {
+        const XPhase& PH = P.ph[ph];
+        const uint32_t pl = s_pl[ph * T + tid];
+        XPh h;
+        h.l0 = pl >> 8;  // local index of register index 0, relabel bits included
+        const uint32_t kap = pl & 0xffu;
+        h.tb = tb;
+        h.pb = h.l0 * ES;
+        h.lb0 = PH.lbit[0];
+        h.lb1 = PH.lbit[1];
+        h.lb2 = PH.lbit[2];
+        h.lb3 = PH.lbit[3];
+        h.sp0 = h.lb0 * ES;
+        h.sp1 = h.lb1 * ES;
+        h.sp2 = h.lb2 * ES;
+        h.sp3 = h.lb3 * ES;
+        h.fs = xsh(s_fs);
+        h.lut = xsh(s_lut);
+        h.ne = args.n_edges;
+        h.cs1 = cs1;
+        h.cs3 = cs3;
+        h.plus = args.plus_amp;
+        h.cutb = h.w0 = h.w1 = h.w2 = h.w3 = 0;
+        const int diag = PH.diag;
+        if (diag) {  // cut values: fs[l] + g + sum of w over the set local bits
+          int cb = lin[15];
+          for (uint32_t x = h.l0; x; x &= x - 1) cb += lin[__ffs(x) - 1];
+          h.cutb = cb;  // includes the weights of the relabel bits set in l0
+          // a register bit set in kappa is set in l0 and flips in j: its weight enters with -1
+          h.w0 = ((kap & 1u) ? -1 : 1) * lin[__ffs(h.lb0) - 1];
+          h.w1 = ((kap & 2u) ? -1 : 1) * lin[__ffs(h.lb1) - 1];
+          h.w2 = ((kap & 4u) ? -1 : 1) * lin[__ffs(h.lb2) - 1];
+          h.w3 = h.lb3 ? ((kap & 8u) ? -1 : 1) * lin[__ffs(h.lb3) - 1] : 0;
+        }
+        const int code = xcode(__popc(PH.m1), diag, __popc(PH.m3)) + ((flags & XF_GEN_PLUS) && ph == 0 ? 125 : 0);
+        const bool ok = TWO ? xdispatch2(code, h, acc) : xdispatch1(code, h, acc);
+        if (!ok && tid == 0) s_bad = 1;
+        xbar_compute(T);
+      }
+      fence_async_smem();              // this thread's shared writes, before the bulk stores read them
+      mbar_arrive(xsh(&s_done[cur]));  // the producer may now store this buffer and refill it
+#pragma unroll
+      for (int k = 0; k < 3; ++k) xacc(acc_hi[k], acc_lo[k], acc[k]);
+    }
   }
-  xwait0();
+  __syncthreads();
 
   // ---- per-CTA sums of the accumulators, fixed order; a phase code without a
   // kernel body (a planner fault) poisons the results with NaN
@@ -523,7 +600,7 @@ __global__ void __launch_bounds__(TWO ? 256 : 512, 1) qx_kernel(XArgs args) {
     __syncthreads();
     if (tid == 0) {
       double s = 0;
-      for (int w = 0; w < (T + 31) / 32; ++w) s += s_red[w];
+      for (int w = 0; w < NT / 32; ++w) s += s_red[w];
       args.partials[(size_t)P.slot[k] * args.stride + blockIdx.x] = s_bad ? __longlong_as_double(0x7ff8000000000000ll) : s;
     }
     __syncthreads();
@@ -533,32 +610,32 @@ __global__ void __launch_bounds__(TWO ? 256 : 512, 1) qx_kernel(XArgs args) {
 #undef XL
 #undef XS
 #undef XW
-#undef XG
 #undef XCUT
 
-// Dynamic shared memory: LUT, edge counts and phase bases, then the tile
-// buffers at the next multiple of their size (at most one tile of padding).
+// Dynamic shared memory: LUT, edge counts and phase bases, then the tile buffers.
 size_t qx_smem(int two_state, int m, int n_edges) {
-  const size_t T = (size_t)1 << (m - 4);
+  const size_t T = (size_t)1 << (m - qx_reg_bits(two_state));
   const size_t tile = ((size_t)1 << m) * (two_state ? 16 : 8);
   size_t off = ((size_t)(n_edges + 1) * 8 + 127) & ~(size_t)127;
   off += (((size_t)1 << m) + 127) & ~(size_t)127;
-  off += (size_t)kXMaxPhases * T * 4;
-  return off + tile + (size_t)kXNB * tile;
+  off += ((size_t)kXMaxPhases * T * 4 + 127) & ~(size_t)127;
+  return off + 128 + (size_t)kXNB * tile;
 }
 
 }  // namespace
 
 int qx_occupancy(int two_state, int m, int n_edges, int /*n_phases*/) {
   static int last_key[2] = {-1, -1}, last_occ[2] = {0, 0};
-  if (m < 9 || m > (two_state ? 12 : kXMaxM)) return 0;
+  if (m < 5 + qx_reg_bits(two_state) || m > (two_state ? 12 : kXMaxM)) return 0;
   const size_t smem = qx_smem(two_state, m, n_edges);
   const int key = m * 1024 + n_edges;
   if (last_key[two_state] == key) return last_occ[two_state];
   const void* fn = two_state ? (const void*)qx_kernel<true> : (const void*)qx_kernel<false>;
   int blocks = 0;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, 1 << (m - 4), smem) != cudaSuccess || blocks < 1) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, (1 << (m - qx_reg_bits(two_state))) + 32, smem) !=
+          cudaSuccess ||
+      blocks < 1) {
     (void)cudaGetLastError();
     blocks = 0;
   }
@@ -578,8 +655,59 @@ int qx_grid(int two_state, int m, int n_edges, int n_phases, uint64_t n_tiles) {
   return (int)(g < 1 ? 1 : g);
 }
 
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+    else
+      (void)cudaGetLastError();
+  }
+  return fn;
+}
+
+// Tensor map k of pass h over `base` (8-byte words, n + me qubit bits of word index).
+qs_status encode_map(const XPass& h, int k, int n, void* base, CUtensorMap* out) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    set_error("qaoa: cuTensorMapEncodeTiled is unavailable");
+    return QS_ERR_CUDA;
+  }
+  cuuint64_t dim[5], stride[4];
+  cuuint32_t box[5], estr[5];
+  for (int d = 0; d < 5; ++d) {
+    dim[d] = 1ull << h.mw[k][d];
+    box[d] = 1u << h.mbx[k][d];
+    estr[d] = 1;
+    if (d > 0) stride[d - 1] = 8ull << h.ma[k][d];
+  }
+  (void)n;
+  const CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, base, dim, stride, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("qaoa: tensor map of a tile rejected (internal error)");
+    return QS_ERR_CUDA;
+  }
+  return QS_OK;
+}
+
+}  // namespace
+
 qs_status launch_qx_pass(int two_state, const XPass* d_pass, const XPass& h, const XLaunch& L, cudaStream_t st) {
-  if (h.m < 9 || h.m > (two_state ? 12 : kXMaxM) || h.m > L.n || L.grid < 1) {
+  if (h.m < 5 + qx_reg_bits(two_state) || h.m > (two_state ? 12 : kXMaxM) || h.m > L.n || L.grid < 1) {
     set_error("qaoa: invalid pass shape (internal error)");
     return QS_ERR_UNSUPPORTED;
   }
@@ -588,6 +716,10 @@ qs_status launch_qx_pass(int two_state, const XPass* d_pass, const XPass& h, con
     return QS_ERR_UNSUPPORTED;
   }
   XArgs a;
+  void* ld_base = two_state && !(h.flags & XF_LOAD_PSI) ? (void*)L.il : (void*)L.psi;
+  void* st_base = two_state ? (void*)L.il : (void*)L.psi;
+  QS_TRY(encode_map(h, 0, L.n, ld_base, &a.tm[0]));
+  QS_TRY(encode_map(h, 1, L.n, st_base, &a.tm[1]));
   a.pass = d_pass;
   a.psi = L.psi;
   a.il = L.il;
@@ -599,7 +731,7 @@ qs_status launch_qx_pass(int two_state, const XPass* d_pass, const XPass& h, con
   a.n = L.n;
   a.n_edges = L.n_edges;
   const size_t smem = qx_smem(two_state, h.m, L.n_edges);
-  const int threads = 1 << (h.m - 4);
+  const int threads = (1 << (h.m - qx_reg_bits(two_state))) + 32;  // compute threads + the producer warp
   if (two_state)
     qx_kernel<true><<<L.grid, threads, smem, st>>>(a);
   else

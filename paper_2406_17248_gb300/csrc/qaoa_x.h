@@ -38,13 +38,14 @@ enum XFlags : uint32_t {
 
 struct XPhase {
   uint64_t gbit[4];  // global (qubit) bit of each register bit
-  uint16_t spos[4];  // swizzled shared-memory position of each register bit
   uint16_t lbit[4];  // local-index bit of each register bit
   int8_t q[kXMaxM];  // sub-cube local bits, lane order
   uint8_t nq;
   uint8_t m1, m3;    // register-bit masks of steps 1 and 3
   uint8_t diag;      // XDiag (at most one phase of a pass has one)
-  uint8_t pad[2];
+  uint8_t kq;        // sub-cube bits that are bank-column bits (lanes 0..kq-1)
+  uint8_t kn;        // register bits that are bank-column bits, relabelled by lanes kq..kq+kn-1
+  uint8_t kidx[4];   // their register-bit indices
 };
 
 struct XPass {
@@ -61,8 +62,20 @@ struct XPass {
   uint64_t ccmask[kXMaxComp];  // complement neighbours (above) of ccnode[k]
   uint64_t wmask[kXMaxM];      // complement neighbours of tile (local) bit i
   uint64_t hiA[64], hiB[64];   // global bits of local bits c..c+5 and c+6..c+11
+  // TMA tensor maps of the tile, [0] load, [1] store.  The array is viewed as
+  // 8-byte words (a 16-byte element is two words: me = 1); its word-index bits
+  // are cut into five dimensions, dim i spanning bits [ma[i], ma[i] + mw[i]),
+  // of which the box holds the low mbx[i].  The boxes cover the low mlb local
+  // bits of the tile; the 2^(m - mlb) boxes of a tile differ in the higher ones.
+  uint8_t ma[2][5], mw[2][5], mbx[2][5], me[2], mlb[2];
+  uint8_t mpad[6];
   XPhase ph[kXMaxPhases];
 };
+
+// Splits the word-index bits of a tile (bit set S of an n-qubit array, words
+// per amplitude 2^e) into the five dimensions of a tensor map; false when the
+// tile needs more than 32 boxes or a dimension is wider than 31 bits.
+bool qx_map_dims(uint64_t S, int n, int e, int m, uint8_t a[5], uint8_t w[5], uint8_t bx[5], uint8_t* lb);
 
 struct XLaunch {
   float2* psi;                 // plain complex64 state
@@ -72,6 +85,9 @@ struct XLaunch {
   double* partials;
   int stride, grid, n, n_edges;
 };
+
+// Register bits per phase: 4 (16 amplitudes per thread) in both kernels.
+constexpr int qx_reg_bits(bool /*two_state*/) { return 4; }
 
 // two_state = 0: forward kernel (psi alone, 8-byte elements); 1: psi and lam
 // interleaved (16-byte elements).  Returns the resident CTAs per SM (0: does

@@ -147,66 +147,39 @@ std::vector<XSched> qx_reverse_schedule(int n, int p, int m, int c, uint64_t rem
 
 namespace {
 
-// Shared-memory column (bank group) bits of local bit b: the swizzle of
-// qaoa_swizzle is linear, so a local bit moves a fixed set of position bits.
-uint32_t col_bits(bool el8, int b) { return qaoa_swizzle(el8, 1u << b) & (el8 ? 15u : 7u); }
-
-// Order the sub-cube bits: the low local bits first (lanes of a warp then touch
-// contiguous addresses), then, for any column bit not yet covered by the first
-// lanes, a bit that moves it (bank-conflict-free loads and stores).
-std::vector<int> lane_order(const std::vector<int>& rest, bool el8) {
-  const int need = el8 ? 4 : 3;  // lanes that must hit distinct columns: 16 (8-byte) or 8 (16-byte elements)
+// Tiles sit in shared memory unswizzled (a copy of the gathered HBM runs), so
+// the bank column of an element is its low local bits: 3 bits for 16-byte
+// elements (8 per 128-byte row, the lanes of a quarter-warp), 4 for 8-byte ones
+// (a half-warp).  Lane order: the column bits among the sub-cube bits first
+// (lanes then also touch contiguous addresses), then the rest.  Column bits
+// held in registers are covered by the next lanes, which XOR-relabel the
+// thread's register index (see the kernel).
+std::vector<int> lane_order(const std::vector<int>& rest, int ncol) {
   std::vector<int> q;
-  std::vector<char> used(rest.size(), 0);
-  std::vector<uint32_t> basis;  // reduced column vectors of the chosen lane bits
-  auto independent = [&](uint32_t v) {
-    for (uint32_t b : basis)
-      if ((v ^ b) < v) v ^= b;
-    return v;
-  };
-  // pass 1: low local bits in order, while independent
-  for (size_t i = 0; i < rest.size() && (int)q.size() < need; ++i) {
-    const uint32_t v = independent(col_bits(el8, rest[i]));
-    if (rest[i] < need && v) {
-      q.push_back(rest[i]);
-      used[i] = 1;
-      basis.push_back(v);
-      std::sort(basis.begin(), basis.end(), std::greater<uint32_t>());
-    }
-  }
-  // pass 2: any bits that add a new column direction
-  for (size_t i = 0; i < rest.size() && (int)q.size() < need; ++i) {
-    if (used[i]) continue;
-    const uint32_t v = independent(col_bits(el8, rest[i]));
-    if (v) {
-      q.push_back(rest[i]);
-      used[i] = 1;
-      basis.push_back(v);
-      std::sort(basis.begin(), basis.end(), std::greater<uint32_t>());
-    }
-  }
-  for (size_t i = 0; i < rest.size(); ++i)
-    if (!used[i]) q.push_back(rest[i]);
+  for (int b : rest)
+    if (b < ncol) q.push_back(b);
+  for (int b : rest)
+    if (b >= ncol) q.push_back(b);
   return q;
 }
 
 struct PhasePlan {
-  std::vector<int> reg;  // 4 local bits
+  std::vector<int> reg;  // R local bits
   uint8_t m1 = 0, m3 = 0;
   uint8_t diag = XD_NONE;
 };
 
-// Register bits for a group of op bits, padded to 4 with bits that carry no op
+// Register bits for a group of op bits, padded to R with bits that carry no op
 // (non-low bits first, so the low bits stay lane bits).
-std::vector<int> pad_reg(std::vector<int> bits, int m, int c) {
-  for (int b = m - 1; b >= c && bits.size() < 4; --b)
+std::vector<int> pad_reg(std::vector<int> bits, int m, int c, size_t R) {
+  for (int b = m - 1; b >= c && bits.size() < R; --b)
     if (std::find(bits.begin(), bits.end(), b) == bits.end()) bits.push_back(b);
-  for (int b = 0; b < c && bits.size() < 4; ++b)
+  for (int b = 0; b < c && bits.size() < R; ++b)
     if (std::find(bits.begin(), bits.end(), b) == bits.end()) bits.push_back(b);
   return bits;
 }
 
-std::vector<PhasePlan> plan_phases(int m, int c, uint32_t A, int diag, uint32_t B) {
+std::vector<PhasePlan> plan_phases(int m, int c, uint32_t A, int diag, uint32_t B, size_t R) {
   auto bits_of = [&](uint32_t mask, bool low_first) {
     std::vector<int> v, lo;
     for (int b = 0; b < m; ++b)
@@ -221,7 +194,7 @@ std::vector<PhasePlan> plan_phases(int m, int c, uint32_t A, int diag, uint32_t 
   std::vector<PhasePlan> out;
   auto add = [&](const std::vector<int>& ops_bits, bool step1, bool step3, const std::vector<int>& ops3) {
     PhasePlan pp;
-    pp.reg = pad_reg(ops_bits, m, c);
+    pp.reg = pad_reg(ops_bits, m, c, R);
     for (size_t r = 0; r < pp.reg.size(); ++r) {
       if (step1 && std::find(ops_bits.begin(), ops_bits.end(), pp.reg[r]) != ops_bits.end()) pp.m1 |= 1u << r;
       if (step3 && std::find(ops3.begin(), ops3.end(), pp.reg[r]) != ops3.end()) pp.m3 |= 1u << r;
@@ -231,8 +204,8 @@ std::vector<PhasePlan> plan_phases(int m, int c, uint32_t A, int diag, uint32_t 
   if (diag == XD_NONE) {
     // step 1 only; low bits first so the last phase keeps them as lane bits
     const std::vector<int> a = bits_of(A, true);
-    for (size_t i = 0; i < a.size(); i += 4) {
-      std::vector<int> g(a.begin() + i, a.begin() + std::min(a.size(), i + 4));
+    for (size_t i = 0; i < a.size(); i += R) {
+      std::vector<int> g(a.begin() + i, a.begin() + std::min(a.size(), i + R));
       add(g, true, false, {});
     }
     if (out.empty()) add({}, false, false, {});
@@ -240,17 +213,17 @@ std::vector<PhasePlan> plan_phases(int m, int c, uint32_t A, int diag, uint32_t 
   }
   // before the diagonal: step-1 bits in groups of 4, the remainder goes to the diagonal phase
   const std::vector<int> a = bits_of(A, true);
-  const size_t kA = std::max<size_t>(1, (a.size() + 3) / 4);
-  for (size_t i = 0; i + 1 < kA; ++i) add(std::vector<int>(a.begin() + 4 * i, a.begin() + 4 * i + 4), true, false, {});
-  std::vector<int> d(a.begin() + std::min(a.size(), 4 * (kA - 1)), a.end());
+  const size_t kA = std::max<size_t>(1, (a.size() + R - 1) / R);
+  for (size_t i = 0; i + 1 < kA; ++i) add(std::vector<int>(a.begin() + R * i, a.begin() + R * i + R), true, false, {});
+  std::vector<int> d(a.begin() + std::min(a.size(), R * (kA - 1)), a.end());
   const std::vector<int> d1 = d;  // bits that still take step 1 in the diagonal phase
   // fill the diagonal phase with step-3 bits: the low ones first (they then take
   // their step 3 here and stay lane bits in the last phase)
   for (int b : bits_of(B, true))
-    if (d.size() < 4 && std::find(d.begin(), d.end(), b) == d.end()) d.push_back(b);
+    if (d.size() < R && std::find(d.begin(), d.end(), b) == d.end()) d.push_back(b);
   {
     PhasePlan pp;
-    pp.reg = pad_reg(d, m, c);
+    pp.reg = pad_reg(d, m, c, R);
     pp.diag = (uint8_t)diag;
     for (size_t r = 0; r < pp.reg.size(); ++r) {
       if (std::find(d1.begin(), d1.end(), pp.reg[r]) != d1.end()) pp.m1 |= 1u << r;
@@ -262,8 +235,8 @@ std::vector<PhasePlan> plan_phases(int m, int c, uint32_t A, int diag, uint32_t 
   uint32_t rest = B;
   for (int b : out.back().reg) rest &= ~(1u << b);
   const std::vector<int> r3 = bits_of(rest, true);
-  for (size_t i = 0; i < r3.size(); i += 4) {
-    std::vector<int> g(r3.begin() + i, r3.begin() + std::min(r3.size(), i + 4));
+  for (size_t i = 0; i < r3.size(); i += R) {
+    std::vector<int> g(r3.begin() + i, r3.begin() + std::min(r3.size(), i + R));
     add(g, false, true, g);
   }
   return out;
@@ -282,6 +255,46 @@ void edge_table(int m, const std::vector<std::pair<int, int>>& loc_edges, std::v
 }
 
 }  // namespace
+
+bool qx_map_dims(uint64_t S, int n, int e, int m, uint8_t a[5], uint8_t w[5], uint8_t bx[5], uint8_t* lb) {
+  const int N = n + e;  // word-index bits
+  const uint64_t Sw = (S << e) | ((1ull << e) - 1);
+  // runs of tile bits in the word index, cut into chunks of at most 8 bits (a box edge holds <= 256 words)
+  int st[64], ln[64], k = 0;
+  for (int q = 0; q < N;) {
+    if (!((Sw >> q) & 1)) {
+      ++q;
+      continue;
+    }
+    int r = q;
+    while (r < N && ((Sw >> r) & 1) && r - q < 8) ++r;
+    st[k] = q;
+    ln[k++] = r - q;
+    q = r;
+  }
+  if (k == 0 || st[0] != 0) return false;
+  const int d = std::min(k, 5);
+  int box_bits = 0;
+  for (int i = 0; i < d; ++i) box_bits += ln[i];
+  // the boxes cover the low (box_bits - e) local bits; the rest are enumerated
+  const int lb_amp = box_bits - e;
+  if (m - lb_amp > 5 || box_bits + 3 < 7) return false;  // <= 32 boxes of >= 128 bytes
+  for (int i = 0; i < 5; ++i) {
+    if (i < d) {
+      const int hi = i + 1 < d ? st[i + 1] : N;
+      a[i] = (uint8_t)st[i];
+      w[i] = (uint8_t)(hi - st[i]);
+      bx[i] = (uint8_t)ln[i];
+      if (w[i] > 31) return false;
+    } else {  // unused dimension: one word above the array
+      a[i] = (uint8_t)N;
+      w[i] = 0;
+      bx[i] = 0;
+    }
+  }
+  *lb = (uint8_t)lb_amp;
+  return true;
+}
 
 qs_status qx_build_pass(const XBuild& B, const XSched& s, bool two_state, uint32_t flags, int out_slots[3],
                         XPass* out, std::vector<uint8_t>* fs) {
@@ -328,7 +341,8 @@ qs_status qx_build_pass(const XBuild& B, const XSched& s, bool two_state, uint32
     set_error("qaoa planner: mixer bits outside the tile (internal error)");
     return QS_ERR_UNSUPPORTED;
   }
-  const std::vector<PhasePlan> phs = plan_phases(m, c, A, s.diag, Bm);
+  const int R = qx_reg_bits(two_state);
+  const std::vector<PhasePlan> phs = plan_phases(m, c, A, s.diag, Bm, (size_t)R);
   if ((int)phs.size() > kXMaxPhases) {
     set_error("qaoa planner: too many phases (internal error)");
     return QS_ERR_UNSUPPORTED;
@@ -340,33 +354,61 @@ qs_status qx_build_pass(const XBuild& B, const XSched& s, bool two_state, uint32
     const bool prefix = phs[i].m1 == (1u << k1) - 1 && phs[i].m3 == (1u << k3) - 1;
     bool ok;
     if (dg == XD_NONE) ok = (k1 > 0) != (k3 > 0);
-    else if (!two_state) ok = (dg == XD_COST && k3 == 4) || (dg == XD_ENERGY && k3 == 0);
-    else ok = (dg == XD_COST_GRAD && (k3 == 4 || k3 == 0)) || (dg == XD_ENERGY && k3 == 4);
+    else if (!two_state) ok = (dg == XD_COST && k3 == R) || (dg == XD_ENERGY && k3 == 0);
+    else ok = (dg == XD_COST_GRAD && (k3 == R || k3 == 0)) || (dg == XD_ENERGY && k3 == R);
     if (!prefix || !ok) {
       set_error("qaoa planner: a phase without a kernel body (internal error)");
       return QS_ERR_UNSUPPORTED;
     }
   }
-  const bool el8 = !two_state;
+  const bool el8 = !two_state;  // 8-byte elements (psi alone) or 16-byte (psi/lam)
   P.n_phases = (int)phs.size();
   for (int i = 0; i < P.n_phases; ++i) {
     XPhase& X = P.ph[i];
-    uint32_t R = 0;
-    for (int r = 0; r < 4; ++r) {
+    uint32_t regmask = 0;
+    for (int r = 0; r < 4; ++r) {  // unused register slots (R = 3): no bit
+      if (r >= R) {
+        X.lbit[r] = 0;
+        X.gbit[r] = 0;
+        continue;
+      }
       X.lbit[r] = (uint16_t)(1u << phs[i].reg[r]);
       X.gbit[r] = 1ull << global_of[phs[i].reg[r]];
-      X.spos[r] = (uint16_t)qaoa_swizzle(el8, 1u << phs[i].reg[r]);
-      R |= 1u << phs[i].reg[r];
+      regmask |= 1u << phs[i].reg[r];
     }
     std::vector<int> rest;
     for (int b = 0; b < m; ++b)
-      if (!((R >> b) & 1)) rest.push_back(b);
-    const std::vector<int> q = lane_order(rest, el8);
+      if (!((regmask >> b) & 1)) rest.push_back(b);
+    const int ncol = el8 ? 4 : 3;
+    const std::vector<int> q = lane_order(rest, ncol);
     X.nq = (uint8_t)q.size();
     for (size_t t = 0; t < q.size(); ++t) X.q[t] = (int8_t)q[t];
+    // register bits that are column bits: relabelled by the lanes after the
+    // column lanes, so the first 2^ncol lanes still hit 2^ncol columns
+    X.kq = 0;
+    while (X.kq < X.nq && X.q[X.kq] < ncol) ++X.kq;
+    X.kn = 0;
+    for (int r = 0; r < R; ++r)
+      if (phs[i].reg[r] < ncol) X.kidx[X.kn++] = (uint8_t)r;
+    if (X.kq + X.kn != ncol || X.kq + X.kn > X.nq) {
+      set_error("qaoa planner: bank-column lanes do not cover the columns (internal error)");
+      return QS_ERR_UNSUPPORTED;
+    }
     X.m1 = phs[i].m1;
     X.m3 = phs[i].m3;
     X.diag = phs[i].diag;
+  }
+  // tensor maps: loads of psi (8-byte words) or of the interleaved pair (two
+  // words per amplitude), stores to the interleaved pair in the two-state kernel
+  {
+    const int e_ld = two_state && !(flags & XF_LOAD_PSI) ? 1 : 0, e_st = two_state ? 1 : 0;
+    if (!qx_map_dims(s.S, B.n, e_ld, m, P.ma[0], P.mw[0], P.mbx[0], &P.mlb[0]) ||
+        !qx_map_dims(s.S, B.n, e_st, m, P.ma[1], P.mw[1], P.mbx[1], &P.mlb[1])) {
+      set_error("qaoa planner: the tile does not map onto a five-dimensional copy");
+      return QS_ERR_UNSUPPORTED;
+    }
+    P.me[0] = (uint8_t)e_ld;
+    P.me[1] = (uint8_t)e_st;
   }
   // coefficients: per layer lut[E+1], lut_dag[E+1], rx (c, s), rx_dag (c, -s)
   const int E1 = B.n_edges + 1, per_layer = 2 * E1 + 2;
@@ -549,7 +591,17 @@ extern "C" qs_status qs_qaoa_xplan(int n_qubits, const int* edges, int n_edges, 
       q[0] = X2.m1;
       q[1] = X2.m3;
       q[2] = X2.diag;
-      for (int k = 0; k < 4; ++k) q[3 + k] = gl[__builtin_ctz(X2.lbit[k])];
+      for (int k = 0; k < 4; ++k) q[3 + k] = X2.lbit[k] ? gl[__builtin_ctz(X2.lbit[k])] : -1;
+    }
+    for (int k = 0; k < 2; ++k) {
+      long long* t = r + 12 + 7 * kXMaxPhases + 17 * k;
+      t[0] = P.me[k];
+      t[1] = P.mlb[k];
+      for (int d = 0; d < 5; ++d) {
+        t[2 + d] = P.ma[k][d];
+        t[7 + d] = P.mw[k][d];
+        t[12 + d] = P.mbx[k][d];
+      }
     }
   }
   return QS_OK;

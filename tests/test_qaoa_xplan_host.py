@@ -66,9 +66,11 @@ def replay(plan, slots, n, edges, gamma, beta, gs, p):
         c1 = tab[P["c1"]] if P["c1"] >= 0 else 1.0
         c3 = tab[P["c3"]] if P["c3"] >= 0 else 1.0
         seen1, seen3 = set(), set()
+        R = 4  # register bits per phase
         for ph in P["phases"]:
-            assert len(set(ph["reg"])) == 4
-            assert all((P["S"] >> q) & 1 for q in ph["reg"])
+            reg = ph["reg"][:R]
+            assert len(set(reg)) == R and all(q >= 0 for q in reg) and all(q == -1 for q in ph["reg"][R:])
+            assert all((P["S"] >> q) & 1 for q in reg)
             for step, mask, cf, grad_flag, seen in ((0, ph["m1"], c1, 8, seen1), (2, ph["m3"], c3, 16, seen3)):
                 if step == 2:  # the diagonal step sits between the two mixer steps
                     d = ph["diag"]
@@ -82,7 +84,7 @@ def replay(plan, slots, n, edges, gamma, beta, gs, p):
                         acc[1] += float(np.sum(C * np.abs(psi) ** 2))
                         if two:
                             lam = C * psi
-                for r in range(4):
+                for r in range(R):
                     if not (mask >> r) & 1:
                         continue
                     q = ph["reg"][r]
@@ -145,3 +147,56 @@ def test_benchmark_plan_shape(Q):
         elem = 16 if P["two"] else 8
         hi = [q for q in range(P["c"], n) if (P["S"] >> q) & 1]
         assert any((1 << q) * elem <= 16384 for q in hi), (P["S"], P["two"])
+
+
+def _box_words(mp, n, S, toff):
+    """Word indices that the tile's boxes deliver, in shared-memory order: a
+    tiled tensor copy walks its box with dimension 0 fastest, box j of a tile
+    starts at the word index of local offset j 2^lb (local bits ascend with the
+    global ones)."""
+    e, lb = mp["e"], mp["lb"]
+    glob = [q for q in range(n) if (S >> q) & 1]
+    m = len(glob)
+
+    def l2g(l):
+        return sum(1 << glob[i] for i in range(m) if (l >> i) & 1)
+
+    out = []
+    for j in range(1 << (m - lb)):
+        wi = (toff + l2g(j << lb)) << e
+        x = [(wi >> mp["a"][d]) & ((1 << mp["w"][d]) - 1) for d in range(5)]
+        boxes = [1 << b for b in mp["box"]]
+        idx = np.indices(boxes[::-1]).reshape(5, -1)[::-1]  # dimension 0 fastest
+        addr = np.zeros(idx.shape[1], dtype=np.int64)
+        for d in range(5):
+            assert x[d] + boxes[d] <= (1 << mp["w"][d]), "box leaves its dimension"
+            addr += (x[d] + idx[d]) << mp["a"][d]
+        out.append(addr)
+    return np.concatenate(out), e
+
+
+@pytest.mark.parametrize("n,p,tb,lb", [(30, 8, 0, 0), (21, 3, 12, 3), (16, 2, 10, 3), (14, 2, 9, 2)])
+def test_tile_tensor_maps_land_the_tile_in_local_order(Q, n, p, tb, lb):
+    """Every pass's load and store maps move exactly the tile's words, each to
+    the shared position of its local index, for the zero tile offset and for a
+    random one (the complement bits set at random)."""
+    edges = I.random_regular_graph(n, 3 if n % 2 == 0 else 4, seed=5)
+    plan, _ = Q.qaoa_xplan(n, edges, p, 0.5, tb, lb)
+    rng = np.random.default_rng(n)
+    for P in plan:
+        S = P["S"]
+        glob = [q for q in range(n) if (S >> q) & 1]
+        comp = [q for q in range(n) if not (S >> q) & 1]
+        offs = [0, sum(1 << q for q in comp if rng.random() < 0.5)]
+        for k, mp in enumerate(P["maps"]):
+            assert mp["e"] == (1 if P["two"] and (k == 1 or not P["flags"] & 2) else 0)
+            for toff in offs:
+                got, e = _box_words(mp, n, S, toff)
+                loc = np.arange(len(got)) >> e
+                sub = np.arange(len(got)) & ((1 << e) - 1)
+                want = np.zeros(len(got), dtype=np.int64)
+                for i, q in enumerate(glob):
+                    want += ((loc >> i) & 1) << q
+                want = ((want + toff) << e) | sub
+                assert len(got) == (1 << len(glob)) << e
+                assert np.array_equal(got, want)

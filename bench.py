@@ -141,82 +141,108 @@ def measured_peak_hbm():
 
 
 def kernel_source_hash():
-    """Hash of the sources of the QAOA pass kernels (the counters in the committed
-    ncu summary are valid only for this exact source)."""
+    """Hash of the sources of the complex64 QAOA pass kernels (the counters in the
+    committed ncu summary are valid only for this exact source)."""
     h = hashlib.sha256()
-    for f in ("k_qaoa.cu", "qaoa_pass.h", "qsim_internal.h"):
+    for f in ("k_qaoa_x.cu", "qaoa_x.h", "qaoa_x_plan.cu"):
         with open(os.path.join(ROOT, "paper_2406_17248_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_launch():
-    """DRAM bytes per reverse-pass launch from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+def ncu_traffic_per_launch(kind):
+    """DRAM bytes per launch of a QAOA pass kernel kind from the committed ncu
+    summary (a smaller capture scaled to 30 qubits), if it was taken on the
+    current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "qaoa_passes_qaoa30.md")
     try:
         text = open(path).read()
     except OSError:
         return None
     m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    m_tr = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    m_tr = re.search(r"traffic_bytes_per_full_launch\[%s\]:\s*([0-9.eE+]+)" % re.escape(kind), text)
     if not (m_hash and m_tr) or m_hash.group(1) != kernel_source_hash():
         return None
     return float(m_tr.group(1))
 
 
-# --------------------------------------------------------------------------- CPU oracle sample
+# --------------------------------------------------------------------------- CPU oracle
 
-def oracle_sample(n_small=18, p=8, evals=1):
-    """Time the FP64 oracle on the same recipe at n_small qubits in a child process
-    pinned to one BLAS thread; return (evals/s at n_small, seconds, cores)."""
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:  # Arm: /proc/cpuinfo has part numbers only; lscpu names the core
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=30).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample(n_small, p, evals, threads, warmup=0):
+    """Time the C FP64 oracle (one loop per gate, OpenMP over amplitudes) on the
+    same recipe at n_small qubits in a child process without the GPU: (evals/s,
+    seconds, threads used)."""
     code = (
         "import sys,time; sys.path.insert(0, %r)\n"
-        "from oracle import qsim_oracle as O\n"
+        "from oracle import qaoa_c\n"
         "from bench import workload\n"
         "e,g,b = workload(%d,%d)\n"
+        "th = %d or qaoa_c.max_threads()\n"
+        "for _ in range(%d): qaoa_c.evaluate(%d, e, g, b, 0.5, th)\n"
         "t=time.perf_counter()\n"
-        "for _ in range(%d): O.qaoa_expectation_with_grad(%d, e, g, b, 0.5)\n"
-        "print(time.perf_counter()-t)\n" % (ROOT, n_small, p, evals, n_small))
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+        "for _ in range(%d): qaoa_c.evaluate(%d, e, g, b, 0.5, th)\n"
+        "print(time.perf_counter()-t, th)\n" % (ROOT, n_small, p, threads, warmup, n_small, evals, n_small))
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    env.pop("OMP_NUM_THREADS", None)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3600)
     if out.returncode != 0:
         raise RuntimeError(out.stderr)
-    sec = float(out.stdout.strip().splitlines()[-1])
-    return evals / sec, sec, 1
+    sec, th = out.stdout.strip().splitlines()[-1].split()
+    return evals / float(sec), float(sec), int(th)
 
 
-def cpu_baseline_block(n, n_small, p, evals):
-    rate_small, sec, cores = oracle_sample(n_small, p, evals)
-    scale = 2.0 ** (n_small - n)
-    return {"value": rate_small * scale, "unit": "evals/s", "cores": cores, "kind": "oracle",
-            "sample": f"{evals} FP64 oracle eval(s) of the same recipe at {n_small} qubits "
-                      f"({sec:.1f} s, {rate_small:.4g} evals/s), scaled by 2^({n_small}-{n}) to the "
-                      f"{n}-qubit state size (the oracle's cost is linear in 2^n)"}
+def cpu_baseline_block(n, n_cpu, p):
+    """The oracle measured at n_cpu qubits (not scaled to n): one evaluation on
+    one thread, two on every host core."""
+    r1, s1, _ = oracle_sample(n_cpu, p, 1, 1)
+    ra, sa, tha = oracle_sample(n_cpu, p, 2, 0)
+    return {"value": ra, "unit": "evals/s", "cores": tha, "kind": "oracle", "n_qubits": n_cpu,
+            "sample": f"FP64 C oracle, the same recipe at {n_cpu} qubits (seeded 3-regular graph, p={p}), "
+                      f"2 evaluations on {tha} threads ({sa:.1f} s); measured at {n_cpu} qubits, not scaled "
+                      f"to the {n}-qubit workload",
+            "single_thread": {"value": r1, "unit": "evals/s", "cores": 1, "seconds": s1},
+            "nproc": os.cpu_count(), "cpu_model": cpu_model()}
 
 
 # --------------------------------------------------------------------------- arms
 
 def run_reference(args, ws, rank):
-    """The oracle as it stands on the host cores: each step a bounded sample."""
+    """The oracle as it stands on the host cores: each step one evaluation of the
+    recipe at --ref-qubits (24) qubits on every core, measured, not scaled."""
     if rank != 0:
         return
     n, p = args.n, args.p
     edges, _, _ = workload(n, p)
     ns = args.ref_qubits
-    if args.warmup:
-        oracle_sample(ns, p, args.warmup)  # untimed warm-up evaluations
-    rate, sec, cores = oracle_sample(ns, p, args.steps)
-    value = rate * 2.0 ** (ns - n)
-    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+    rate, sec, cores = oracle_sample(ns, p, args.steps, 0, warmup=args.warmup)
+    line = {"metric": METRIC, "value": rate, "unit": "evals/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 / rate, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(n, p, len(edges)),
             "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} oracle evals at {ns} qubits ({sec:.1f} s), scaled by "
-                                       f"2^({ns}-{n})"},
-            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": rate, "unit": "evals/s", "cores": cores, "kind": "oracle", "n_qubits": ns,
+                             "sample": f"{args.steps} FP64 C oracle evaluations of the recipe at {ns} qubits on "
+                                       f"{cores} threads ({sec:.1f} s), after {args.warmup} warm-up; measured at "
+                                       f"{ns} qubits, not scaled to the {n}-qubit workload",
+                             "nproc": os.cpu_count(), "cpu_model": cpu_model()},
+            "e2e": {"value": rate, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -296,7 +322,7 @@ def run_ours(args, ws, rank, local):
     achieved = per_kind[dom]["GBps"]
     all_ms = float(np.sum(k_ms))
     all_achieved = float(np.sum(k_bytes)) / (all_ms / 1000.0) / 1e9 if all_ms > 0 else None
-    traffic = ncu_traffic_per_launch()
+    traffic = ncu_traffic_per_launch(dom)
     launches_per_step = len(k_ms) / max(args.steps, 1) + 2  # + slot reduction and output gather
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
@@ -317,7 +343,7 @@ def run_ours(args, ws, rank, local):
         "energy": E,
     }
     if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_block(n, args.cpu_qubits, p, 1)
+        line["cpu_baseline"] = cpu_baseline_block(n, args.cpu_qubits, p)
     if ws == 1 and not args.no_extras:
         # the rest of the headline: the single-gate sweep against the HBM roofline
         # and batched vs one-launch-per-circuit (untimed by the step clock above)
@@ -1082,8 +1108,8 @@ def main():
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--low-bits", type=int, default=0)
-    ap.add_argument("--cpu-qubits", type=int, default=20)
-    ap.add_argument("--ref-qubits", type=int, default=18)
+    ap.add_argument("--cpu-qubits", type=int, default=24)
+    ap.add_argument("--ref-qubits", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="default workload: skip the gate sweep and batch lines")
     ap.add_argument("--block-k", type=int, default=5)

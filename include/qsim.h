@@ -555,7 +555,10 @@ typedef enum {
   QS_TRACE_QAOA_IL = 3,   /* QAOA reverse pass on interleaved psi/lam */
   QS_TRACE_BATCH = 4,     /* batched persistent launch */
   QS_TRACE_DENSE_TC = 5,  /* dense k-qubit block on the tensor cores */
-  QS_TRACE_DENSE_CC = 6   /* dense k-qubit block on the CUDA cores */
+  QS_TRACE_DENSE_CC = 6,  /* dense k-qubit block on the CUDA cores */
+  QS_TRACE_QX_FWD = 7,    /* complex64 two-shape QAOA pass on psi alone (forward sweep) */
+  QS_TRACE_QX_TURN = 8,   /* two-shape turnaround: psi in, interleaved (psi, lam) out */
+  QS_TRACE_QX_REV = 9     /* two-shape reverse pass on interleaved (psi, lam) */
 } qs_trace_kind;
 
 /* Tracing of the engine's launches: while enabled, every tile-pass or batch

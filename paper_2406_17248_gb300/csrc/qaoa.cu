@@ -779,13 +779,13 @@ qs_status run_xpasses(qs_qaoa* q, const std::vector<XPass>& passes, const std::v
       double b = 0;
       if (!two[i]) {
         b = ((f & XF_GEN_PLUS) ? 0 : S) + ((f & XF_STORE) ? S : 0);
-        rec->kind = QS_TRACE_QAOA_FWD;
+        rec->kind = QS_TRACE_QX_FWD;
       } else if (f & XF_LOAD_PSI) {
         b = S + ((f & XF_STORE) ? 2 * S : 0);
-        rec->kind = QS_TRACE_QAOA_TWO;
+        rec->kind = QS_TRACE_QX_TURN;
       } else {
         b = 2 * S + ((f & XF_STORE) ? 2 * S : 0);
-        rec->kind = QS_TRACE_QAOA_IL;
+        rec->kind = QS_TRACE_QX_REV;
       }
       rec->bytes = b;
       QS_CUDA(cudaEventRecord(rec->end, st));

@@ -85,7 +85,9 @@ typedef struct qs_qaoa qs_qaoa;
 
 /* Execution options for a circuit plan.  Zero means "library default". */
 typedef struct {
-  int fuse;       /* 1 (default): fused shared-memory tile passes; -1: one kernel per gate */
+  int fuse;       /* 1 (default): fused shared-memory tile passes (complex64 passes that qualify run
+                     as pre-decoded micro-ops on TMA-fed tiles, the others on the op interpreter);
+                     2: fused passes, all on the op interpreter; -1: one kernel per gate */
   int tile_bits;  /* log2 amplitudes per fused tile, 6..13 (default 12 for c64, 11 for c128) */
   int low_bits;   /* low (contiguous) qubits present in every tile, 1..tile_bits (default 4) */
   int checkpoint; /* adjoint state checkpoints, 0 (default): none.  Circuits: every `checkpoint`
@@ -558,7 +560,8 @@ typedef enum {
   QS_TRACE_DENSE_CC = 6,  /* dense k-qubit block on the CUDA cores */
   QS_TRACE_QX_FWD = 7,    /* complex64 two-shape QAOA pass on psi alone (forward sweep) */
   QS_TRACE_QX_TURN = 8,   /* two-shape turnaround: psi in, interleaved (psi, lam) out */
-  QS_TRACE_QX_REV = 9     /* two-shape reverse pass on interleaved (psi, lam) */
+  QS_TRACE_QX_REV = 9,    /* two-shape reverse pass on interleaved (psi, lam) */
+  QS_TRACE_TILE2 = 10     /* complex64 fused tile pass as micro-ops (TMA-fed) */
 } qs_trace_kind;
 
 /* Tracing of the engine's launches: while enabled, every tile-pass or batch

@@ -330,7 +330,18 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
     P.valid = true;
     return QS_OK;
   }
-  PlanParams pp{P.ne, P.m, P.c, dt};
+  // complex64 micro-op passes: without a tile option the forward sweep takes
+  // 2^13-amplitude tiles (16 compute warps per SM) and the reverse sweep, which
+  // carries psi and lam, 2^12 (three buffers of both fit in shared memory)
+  const bool micro = dt == QS_C64 && P.fuse != 2;
+  int m_fwd = P.m, m_rev = P.m;
+  if (micro && !c->opts.tile_bits) {
+    m_fwd = std::min(13, P.ne);
+    m_rev = std::min(12, P.ne);
+  }
+  PlanParams pp{P.ne, m_fwd, P.c, dt, micro};
+  PlanParams pp_rev{P.ne, m_rev, P.c, dt, micro};
+  if (pp.m - pp.c > 12) pp.c = pp.m - 12;
   auto make_item = [&](size_t i, bool reverse) {
     const HostGate& g = c->gates[i];
     PlanItem it;
@@ -341,19 +352,18 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
     it.touched = it.ctrl | (1ull << g.t[0]) | (g.nt == 2 ? (1ull << g.t[1]) : 0);
     const int cls = P.gclass[i];
     it.kind = cls == GC_DENSE1 ? IK_DENSE1 : cls == GC_DENSE2 ? IK_DENSE2 : IK_DIAG;
-    // X gates (CNOT, Toffoli) swap amplitudes in complex128 forward passes (FP64
-    // bound there: 397 -> 467 gates/s on the random 28-qubit circuit); complex64
-    // keeps them as 2x2 matrices (the extra op cost the issue-bound complex64
-    // interpreter more than it saved: 5541 -> 4625), and so does the two-state
-    // reverse kernel (its registers are at the limit)
-    // For the same reason complex128 forward passes apply real matrices (H, RY)
-    // with real arithmetic and diagonals of +-1, +-i (Z, S, CZ) as sign flips.
-    const bool c128f = !reverse && dt == QS_C128;
-    const bool rx = g.kind == QS_GATE_RX, x = g.kind == QS_GATE_X && c128f;
-    const bool real = c128f && real_kind(g.kind), unit = c128f && unit_diag_kind(g.kind);
+    // The op names what the gate is: X gates (CNOT, Toffoli) as swaps, real
+    // matrices (H, RY) with real arithmetic, Z (CZ) as a sign flip, other
+    // diagonals of +-1, +-i as unit diagonals.  Each kernel lowers them to what
+    // it implements (the complex64 interpreter kernel runs all of them as
+    // general matrices: there an extra op type cost more issue slots than it
+    // saved, 5541 -> 4625 gates/s; complex128 one-state passes are FP64-bound
+    // and gain, 397 -> 467).
+    const bool rx = g.kind == QS_GATE_RX, x = g.kind == QS_GATE_X;
+    const bool real = real_kind(g.kind), unit = unit_diag_kind(g.kind), zf = g.kind == QS_GATE_Z && g.nt == 1;
     const uint8_t apply_type = cls == GC_DENSE1   ? (rx ? OP_RX : x ? OP_X : real ? OP_REAL1 : OP_DENSE1)
                                : cls == GC_DENSE2 ? OP_DENSE2
-                                                  : (unit ? OP_UDIAG : OP_DIAG);
+                                                  : (zf ? OP_ZFLIP : unit ? OP_UDIAG : OP_DIAG);
     if (!reverse) {
       it.ops.push_back(ItemOp{apply_type, 0, P.off_u[i], -1, 0.0});
     } else {
@@ -376,7 +386,7 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
       it.kind = P.run_diag[r] ? IK_DIAG : IK_DENSE1;
       // products of real matrices are real, products of i^k are i^k: exactly,
       // in complex arithmetic (the other parts stay exact zeros)
-      bool real = dt == QS_C128, unit = dt == QS_C128;
+      bool real = true, unit = true;
       for (int j : P.runs[r]) {
         real = real && real_kind(c->gates[j].kind);
         unit = unit && unit_diag_kind(c->gates[j].kind);
@@ -396,15 +406,16 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
   }
   for (int sg = n_seg - 1; sg >= 0; --sg) {
     if (!rev[sg].empty())
-      QS_TRY(plan_items(rev[sg], pp, PF_LOAD_PSI | PF_LOAD_LAM | PF_STORE_PSI | PF_STORE_LAM, &P.rev, &P.rev_slots));
+      QS_TRY(plan_items(rev[sg], pp_rev, PF_LOAD_PSI | PF_LOAD_LAM | PF_STORE_PSI | PF_STORE_LAM, &P.rev,
+                        &P.rev_slots));
     P.rev_seg_end.push_back((int)P.rev.passes.size());
   }
   QS_TRY(P.fwd.upload(st));
   QS_TRY(P.rev.upload(st));
   QS_TRY(build_csr(P.rev_slots, std::max(P.n_params, 1), &P.d_row, &P.d_sidx, &P.d_w, st));
-  const uint64_t n_tiles = 1ull << (P.ne - P.m);
-  P.grid1 = tile_grid_size(dt, P.m, 1, (int)std::min<uint64_t>(n_tiles, 1u << 30));
-  P.grid2 = tile_grid_size(dt, P.m, 2, (int)std::min<uint64_t>(n_tiles, 1u << 30));
+  const uint64_t n_tiles = 1ull << (P.ne - m_fwd), n_tiles_rev = 1ull << (P.ne - m_rev);
+  P.grid1 = tile_grid_size(dt, m_fwd, 1, (int)std::min<uint64_t>(n_tiles, 1u << 30));
+  P.grid2 = tile_grid_size(dt, m_rev, 2, (int)std::min<uint64_t>(n_tiles_rev, 1u << 30));
   P.valid = true;
   return QS_OK;
 }
@@ -500,7 +511,7 @@ qs_status run_passes(const TilePlan& plan, int begin, int end, qs_dtype dt, void
       rec->bytes = S * (((f & PF_LOAD_PSI) ? 1 : 0) + ((f & PF_LOAD_LAM) ? 1 : 0) + ((f & PF_STORE_PSI) ? 1 : 0) +
                         ((f & PF_STORE_LAM) ? 1 : 0)) +
                    ((f & PF_NEED_CUT) ? (double)(1ull << n) : 0.0);
-      rec->kind = QS_TRACE_TILE;
+      rec->kind = plan.passes[i].t2 ? QS_TRACE_TILE2 : QS_TRACE_TILE;
       QS_CUDA(cudaEventRecord(rec->end, st));
     }
   }
@@ -782,7 +793,7 @@ qs_status qs_circuit_finalize(qs_circuit* c, qs_dtype dtype, const qs_options* o
     QS_CHECK(opts->tile_bits == 0 || (opts->tile_bits >= kMinTileBits && opts->tile_bits <= kMaxTileBits),
              "tile_bits must be 0 or 6..13");
     QS_CHECK(opts->low_bits >= 0 && opts->low_bits <= kMaxTileBits, "low_bits must be 0..13");
-    QS_CHECK(opts->fuse == 0 || opts->fuse == 1 || opts->fuse == -1, "fuse must be -1, 0 or 1");
+    QS_CHECK(opts->fuse >= -1 && opts->fuse <= 2, "fuse must be -1, 0, 1 or 2");
     QS_CHECK(opts->checkpoint >= 0, "checkpoint must be >= 0");
     c->opts = *opts;
   }

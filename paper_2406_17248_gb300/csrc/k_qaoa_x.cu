@@ -21,13 +21,12 @@
 // still hit distinct banks.  C(x) is assembled per amplitude from a per-pass
 // table of in-tile edge counts and per-tile linear terms (computed by warp 0
 // two tiles ahead), so no cut-value array is read.
-#include <cuda.h>
-
 #include <cmath>
 #include <type_traits>
 
 #include "qaoa_pass.h"
 #include "qaoa_x.h"
+#include "tma.h"
 
 namespace qs {
 
@@ -36,7 +35,7 @@ namespace {
 constexpr int kXN = 16;  // amplitudes per thread per phase
 constexpr int kXNB = 3;  // tile buffers: the current tile, the next one landing, the one after issued
 
-__device__ __forceinline__ uint32_t xsh(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t xsh(const void* p) { return tma_sh(p); }
 __device__ __forceinline__ float2 lds64(uint32_t a) {
   float2 v;
   asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a));
@@ -297,54 +296,7 @@ __device__ __forceinline__ bool xdispatch2(int code, const XPh& h, float (&acc)[
   }
 }
 
-// Bulk (TMA engine) copies of contiguous runs: HBM -> shared memory completing
-// on an mbarrier's transaction count, and shared memory -> HBM in bulk groups.
-// five-dimensional tiled tensor copies (TMA); the tensor map lives in kernel parameter space
-__device__ __forceinline__ void tma_load5(uint32_t dst, const CUtensorMap* map, const int (&x)[5], uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
-      "%6}], [%7];\n" ::"r"(dst),
-      "l"(map), "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(mbar)
-      : "memory");
-}
-__device__ __forceinline__ void tma_store5(const CUtensorMap* map, const int (&x)[5], uint32_t src) {
-  asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];\n" ::"l"(
-                   map),
-               "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(src)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-// mbarrier helpers (shared::cta addresses).  Waits are bounded: on timeout
-// they return false and the kernel records a fault instead of hanging.
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared.b64 st, [%0];\n}\n" ::"r"(a) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect(uint32_t a, uint32_t bytes) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(a), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
-  for (long long it = 0; it < (1ll << 26); ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-__device__ __forceinline__ void xbar_compute(int nthreads) {  // named barrier of the compute warps
-  asm volatile("bar.sync 1, %0;\n" ::"r"(nthreads) : "memory");
-}
 
 // Block: T = 2^(m-R) compute threads plus one producer warp.  The producer
 // moves every tile between HBM and shared memory (16-byte cp.async copies in,
@@ -445,11 +397,7 @@ __global__ void __launch_bounds__(TWO ? 288 : 544, 1) qx_kernel(const __grid_con
     // a tile is 2^(m - mlb) boxes of one tensor map; lane j copies box j, whose
     // tile-local offset j 2^mlb sets the local bits above the box
     const bool gen = (flags & XF_GEN_PLUS) != 0, do_store = (flags & XF_STORE) != 0;
-    auto coords = [&](int k, uint64_t amp, int (&x)[5]) {  // word index -> five coordinates
-      const uint64_t wi = amp << P.me[k];
-#pragma unroll
-      for (int d = 0; d < 5; ++d) x[d] = (int)((wi >> P.ma[k][d]) & ((1ull << P.mw[k][d]) - 1ull));
-    };
+    auto coords = [&](int k, uint64_t amp, int (&x)[5]) { tile_coords(P.ma[k], P.mw[k], amp << P.me[k], x); };
     auto load = [&](uint64_t t, int b) {  // tile t into buffer b, completing full[b]
       if (t >= n_tiles) return;
       const uint32_t fb = xsh(&s_full[b]);
@@ -522,7 +470,7 @@ __global__ void __launch_bounds__(TWO ? 288 : 544, 1) qx_kernel(const __grid_con
       if (tile < n_tiles) lin_terms(tile, 0);
       if (tile + gridDim.x < n_tiles) lin_terms(tile + gridDim.x, 1);
     }
-    xbar_compute(T);
+    bar_compute(T);
     int i = 0;
     for (; tile < n_tiles; tile += gridDim.x, ++i) {
       const int cur = i % kXNB;
@@ -535,10 +483,10 @@ __global__ void __launch_bounds__(TWO ? 288 : 544, 1) qx_kernel(const __grid_con
         float2 v[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = lds64(tb + 8u * ((uint32_t)tid + (uint32_t)T * k));
-        xbar_compute(T);
+        bar_compute(T);
 #pragma unroll
         for (int k = 0; k < 16; ++k) sts128(tb + 16u * ((uint32_t)tid + (uint32_t)T * k), v[k].x, 0.f, v[k].y, 0.f);
-        xbar_compute(T);
+        bar_compute(T);
       }
       const int* lin = s_lin[cur];
       float acc[3] = {0.f, 0.f, 0.f};
@@ -579,7 +527,7 @@ __global__ void __launch_bounds__(TWO ? 288 : 544, 1) qx_kernel(const __grid_con
         const int code = xcode(__popc(PH.m1), diag, __popc(PH.m3)) + ((flags & XF_GEN_PLUS) && ph == 0 ? 125 : 0);
         const bool ok = TWO ? xdispatch2(code, h, acc) : xdispatch1(code, h, acc);
         if (!ok && tid == 0) s_bad = 1;
-        xbar_compute(T);
+        bar_compute(T);
       }
       fence_async_smem();              // this thread's shared writes, before the bulk stores read them
       mbar_arrive(xsh(&s_done[cur]));  // the producer may now store this buffer and refill it
@@ -657,51 +605,16 @@ int qx_grid(int two_state, int m, int n_edges, int n_phases, uint64_t n_tiles) {
 
 namespace {
 
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(f);
-    else
-      (void)cudaGetLastError();
+qs_status encode_map(const XPass& h, int k, void* base, CUtensorMap* out) {
+  TileMapDims d;
+  for (int i = 0; i < 5; ++i) {
+    d.a[i] = h.ma[k][i];
+    d.w[i] = h.mw[k][i];
+    d.bx[i] = h.mbx[k][i];
   }
-  return fn;
-}
-
-// Tensor map k of pass h over `base` (8-byte words, n + me qubit bits of word index).
-qs_status encode_map(const XPass& h, int k, int n, void* base, CUtensorMap* out) {
-  EncodeTiledFn fn = encode_fn();
-  if (!fn) {
-    set_error("qaoa: cuTensorMapEncodeTiled is unavailable");
-    return QS_ERR_CUDA;
-  }
-  cuuint64_t dim[5], stride[4];
-  cuuint32_t box[5], estr[5];
-  for (int d = 0; d < 5; ++d) {
-    dim[d] = 1ull << h.mw[k][d];
-    box[d] = 1u << h.mbx[k][d];
-    estr[d] = 1;
-    if (d > 0) stride[d - 1] = 8ull << h.ma[k][d];
-  }
-  (void)n;
-  const CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, base, dim, stride, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    set_error("qaoa: tensor map of a tile rejected (internal error)");
-    return QS_ERR_CUDA;
-  }
-  return QS_OK;
+  d.e = h.me[k];
+  d.lb = h.mlb[k];
+  return encode_tile_map(d, base, false, out);
 }
 
 }  // namespace
@@ -718,8 +631,8 @@ qs_status launch_qx_pass(int two_state, const XPass* d_pass, const XPass& h, con
   XArgs a;
   void* ld_base = two_state && !(h.flags & XF_LOAD_PSI) ? (void*)L.il : (void*)L.psi;
   void* st_base = two_state ? (void*)L.il : (void*)L.psi;
-  QS_TRY(encode_map(h, 0, L.n, ld_base, &a.tm[0]));
-  QS_TRY(encode_map(h, 1, L.n, st_base, &a.tm[1]));
+  QS_TRY(encode_map(h, 0, ld_base, &a.tm[0]));
+  QS_TRY(encode_map(h, 1, st_base, &a.tm[1]));
   a.pass = d_pass;
   a.psi = L.psi;
   a.il = L.il;

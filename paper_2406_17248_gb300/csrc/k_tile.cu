@@ -773,6 +773,7 @@ int tile_grid_size(qs_dtype dt, int m, int ns, int n_tiles) {
 
 qs_status launch_tile_pass(qs_dtype dt, const TilePlan& plan, int pi, const TileLaunch& L, cudaStream_t st) {
   const PlannedPass& pp = plan.passes[pi];
+  if (pp.t2 && dt == QS_C64) return launch_tile2_pass(plan, pi, L, st);
   const uint32_t fl = pp.hdr.flags;
   const int ns = (fl & (PF_LOAD_LAM | PF_STORE_LAM)) ? 2 : 1;
   TileKArgs a;

@@ -31,6 +31,7 @@ struct PlanParams {
   int m;       // tile bits
   int c;       // low contiguous bits
   qs_dtype dt;
+  bool micro = true;  // also lower qualifying passes to micro-ops (k_tile2.cu)
 };
 
 // Slots: every accumulating op of a pass gets a launch-local slot; the plan's

@@ -27,6 +27,7 @@
 #include "qaoa_pass.h"
 #include "qaoa_x.h"
 #include "qaoa_x_plan.h"
+#include "tma.h"
 
 namespace qs {
 
@@ -257,42 +258,14 @@ void edge_table(int m, const std::vector<std::pair<int, int>>& loc_edges, std::v
 }  // namespace
 
 bool qx_map_dims(uint64_t S, int n, int e, int m, uint8_t a[5], uint8_t w[5], uint8_t bx[5], uint8_t* lb) {
-  const int N = n + e;  // word-index bits
-  const uint64_t Sw = (S << e) | ((1ull << e) - 1);
-  // runs of tile bits in the word index, cut into chunks of at most 8 bits (a box edge holds <= 256 words)
-  int st[64], ln[64], k = 0;
-  for (int q = 0; q < N;) {
-    if (!((Sw >> q) & 1)) {
-      ++q;
-      continue;
-    }
-    int r = q;
-    while (r < N && ((Sw >> r) & 1) && r - q < 8) ++r;
-    st[k] = q;
-    ln[k++] = r - q;
-    q = r;
-  }
-  if (k == 0 || st[0] != 0) return false;
-  const int d = std::min(k, 5);
-  int box_bits = 0;
-  for (int i = 0; i < d; ++i) box_bits += ln[i];
-  // the boxes cover the low (box_bits - e) local bits; the rest are enumerated
-  const int lb_amp = box_bits - e;
-  if (m - lb_amp > 5 || box_bits + 3 < 7) return false;  // <= 32 boxes of >= 128 bytes
+  TileMapDims d;
+  if (!tile_map_dims(S, n, e, m, 1, 8, 128, &d)) return false;
   for (int i = 0; i < 5; ++i) {
-    if (i < d) {
-      const int hi = i + 1 < d ? st[i + 1] : N;
-      a[i] = (uint8_t)st[i];
-      w[i] = (uint8_t)(hi - st[i]);
-      bx[i] = (uint8_t)ln[i];
-      if (w[i] > 31) return false;
-    } else {  // unused dimension: one word above the array
-      a[i] = (uint8_t)N;
-      w[i] = 0;
-      bx[i] = 0;
-    }
+    a[i] = d.a[i];
+    w[i] = d.w[i];
+    bx[i] = d.bx[i];
   }
-  *lb = (uint8_t)lb_amp;
+  *lb = d.lb;
   return true;
 }
 

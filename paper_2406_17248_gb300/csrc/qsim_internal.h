@@ -41,7 +41,9 @@ enum OpType : uint8_t {
   OP_ENERGY = 11,   // acc += C(x) |psi_x|^2 and lam_x = C(x) psi_x
   OP_X = 12,        // X on rb0, complex128 one-state passes: a swap of the amplitude pairs (controls as OP_DENSE1)
   OP_REAL1 = 13,    // as OP_DENSE1 with real entries (H, RY; complex128 one-state passes): half the FP64 work
-  OP_UDIAG = 14     // as OP_DIAG with entries in {1, i, -1, -i} (Z, S, CZ; complex128 one-state passes): no FP64 work
+  OP_UDIAG = 14,    // as OP_DIAG with entries in {1, i, -1, -i} (Z, S, CZ; complex128 one-state passes): no FP64 work
+  OP_ZFLIP = 15     // diag(1, -1) on one target (Z, CZ): a sign flip (lowered to OP_UDIAG / OP_DIAG for the
+                    // interpreter kernel)
 };
 
 enum OpFlags : uint8_t { OPF_LAM = 1 };  // apply to lam as well as psi
@@ -106,10 +108,74 @@ struct HostGate {
 // Class of a gate for the engines: which tile-pass op realises it.
 enum GateClass { GC_DENSE1, GC_DENSE2, GC_DIAG1, GC_DIAG2 };
 
+// ---- the complex64 micro-op tile kernel (k_tile2.cu): every op lowered on the
+// host to a code naming its compiled body (register bits as template
+// arguments), its shared-memory coefficients and its predicates.
+enum T2Kind : uint8_t {
+  T2_U1 = 1,     // 2x2 complex on register bit r0
+  T2_R1 = 2,     // 2x2 real (the real parts of the entries) on r0
+  T2_RX = 3,     // RX: coefficient (c, s) on r0
+  T2_X = 4,      // X on r0 (a swap)
+  T2_Z = 5,      // sign flip where the diagonal bit is 1: on register bit r0
+  T2_ZC = 6,     // ... on a constant bit (d0)
+  T2_D1R = 7,    // diagonal (D0, D1) on register bit r0
+  T2_D1C = 8,    // ... on a constant bit d0: one factor per sub-cube
+  T2_D2RR = 9,   // diagonal D[b0 + 2 b1] with b0 on r0, b1 on r1
+  T2_D2RC = 10,  // b0 on r0, b1 constant (d1)
+  T2_D2CR = 11,  // b0 constant (d0), b1 on r1
+  T2_D2CC = 12,  // both constant
+  T2_U2 = 13,    // 4x4 complex on (r0, r1)
+  T2_G1 = 14,    // acc += 2 Re <lam|A|psi>, A 2x2 on r0
+  T2_G2 = 15,    // ... A 4x4 on (r0, r1)
+  T2_GD = 16     // ... A diagonal: (d0, d1) as register bits (bit 7 clear) or constant bits
+};
+// code = kind | r0 << 5 | r1 << 7 | (register controls ? 1 << 9 : 0); bit 10 (T2_OUTSIDE) of an op's
+// code marks controls outside the registers (lc, gc), checked before the body runs
+constexpr int t2_code(int kind, int r0, int r1, bool jc) { return kind | (r0 << 5) | (r1 << 7) | (jc ? 512 : 0); }
+constexpr int T2_OUTSIDE = 1024;
+
+struct T2Op {
+  uint16_t code;
+  uint16_t cs;      // first coefficient in the pass's shared coefficient stage
+  uint16_t slot;    // accumulator slot (gradient ops)
+  uint8_t jc;       // controls among the register bits (mask over the register index)
+  uint8_t d0, d1;   // constant diagonal bits: local bit l, 64 + global qubit q; GD: 128 + register bit
+  uint8_t pad0[3];
+  uint32_t lc;      // controls on local bits outside the registers
+  uint64_t gc;      // controls outside the tile (checked on the tile offset)
+  uint32_t coef;    // source of the coefficients in the call's table
+  uint32_t ncoef;   // ... and their count
+};
+
+struct T2Phase {
+  uint8_t R[4];          // local bits of register bits 0..3, ascending
+  uint8_t pair;          // R[0] is local bit 0: register elements (2k, 2k+1) are one 16-byte access
+  uint8_t pad0[3];
+  uint16_t op_begin, op_end;  // ops of the phase (pass-relative)
+  uint32_t sp[4];        // swizzled element offset of each register bit
+  uint32_t l0tab[48];    // sub-cube index u -> local base: tab[u & 15] | tab[16 + (u >> 4)]
+};
+
+struct T2Pass {
+  int m, ns, n_phases, n_ops, n_coef, n_slots, slot_base, ncomp;
+  uint32_t flags;
+  uint32_t smem;          // dynamic shared bytes
+  int8_t comp[40];
+  uint8_t ma[5], mw[5], mbx[5], mlb;  // tensor map of the tile (8-byte words, 128-byte swizzle)
+  uint8_t pad0[4];
+  uint64_t hiA[64], hiB[128];  // deposit of local bits c..c+5 / c+6..c+12 (c = 4)
+};
+
 struct PlannedPass {
   DevPass hdr;
   std::vector<DevPhase> phases;
   std::vector<DevOp> ops;
+  // the micro-op form, when the pass qualifies (complex64, 4 low bits, a
+  // five-dimensional tile map, shared-memory budget)
+  bool t2 = false;
+  T2Pass t2hdr;
+  std::vector<T2Phase> t2ph;
+  std::vector<T2Op> t2ops;
 };
 
 // A compiled sequence of tile passes plus the coefficient recipe to fill per call.
@@ -124,6 +190,10 @@ struct TilePlan {
   DevPass* d_pass = nullptr;
   DevPhase* d_phase = nullptr;
   DevOp* d_ops = nullptr;
+  T2Pass* d_t2pass = nullptr;   // per pass (unused entries for passes without the micro-op form)
+  T2Phase* d_t2ph = nullptr;
+  T2Op* d_t2ops = nullptr;
+  std::vector<int> t2_phase_off, t2_op_off;  // per pass: first phase / op in the device arrays
   void free_device();
   qs_status upload(cudaStream_t st);
 };
@@ -141,6 +211,7 @@ struct TileLaunch {
   int stride;  // stride of the partials array (the plan's 2-state grid)
 };
 
+qs_status launch_tile2_pass(const TilePlan& plan, int pass_index, const TileLaunch& L, cudaStream_t st);
 qs_status launch_tile_pass(qs_dtype dt, const TilePlan& plan, int pass_index, const TileLaunch& L,
                            cudaStream_t st);
 int tile_grid_size(qs_dtype dt, int m, int ns, int n_tiles);

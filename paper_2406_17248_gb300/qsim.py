@@ -685,7 +685,7 @@ def trace_enable(on: bool = True):
 TRACE_KINDS = {0: "tile_pass_kernel", 1: "qaoa_pass_kernel (psi)", 2: "qaoa_pass_kernel (psi, lam)",
                3: "qaoa_il_kernel (interleaved reverse)", 4: "batch_kernel", 5: "dense_tc_kernel (tcgen05)",
                6: "dense_cc_kernel", 7: "qx_kernel<false> (psi, forward)", 8: "qx_kernel<true> (turnaround)",
-               9: "qx_kernel<true> (psi/lam interleaved, reverse)"}
+               9: "qx_kernel<true> (psi/lam interleaved, reverse)", 10: "tile2_kernel (micro-op tile pass)"}
 
 
 def trace_read(max_records: int = 65536):

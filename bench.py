@@ -352,6 +352,7 @@ def run_ours(args, ws, rank, local):
         sw = measure_gate_sweep(Q, n, Q.C64, 3)
         line["gate_sweep"] = {k: sw[k] for k in ("n_qubits", "dtype", "GBps", "frac", "gates_per_s", "launches")}
         line["gate_sweep"]["per_kind_frac_median"] = {k: v["frac_median"] for k, v in sw["per_kind"].items()}
+        line["random28"] = measure_random_c64(Q)
         line["batched_vs_plain"] = measure_batched_vs_plain(Q, args.instances, 3, args.plain_instances)
     print(json.dumps(line), flush=True)
 
@@ -416,6 +417,9 @@ def run_batch_workload(args):
     from paper_2406_17248_gb300 import build
     build.build()
     from paper_2406_17248_gb300 import qsim as Q
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        return run_batch_partitioned(Q, args, ws, rank, local)
     r = measure_batched_vs_plain(Q, args.instances, args.steps, args.plain_instances, args.warmup)
     line = {"metric": "batched VQE energy+adjoint-grad instances/s (persistent launch vs one launch sequence per circuit)",
             "value": r["batched"], "unit": "instances/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -426,6 +430,88 @@ def run_batch_workload(args):
                       "seconds": r["plain_seconds"]},
             "speedup_vs_plain": r["speedup_vs_plain"], "energy_check": r["energy_check"], "batch_info": r["batch_info"]}
     print(json.dumps(line), flush=True)
+
+
+def run_batch_partitioned(Q, args, ws, rank, local):
+    """The batch over N ranks (strong scaling: the instance set is fixed): each
+    rank evaluates its cost-balanced share (2^n x gates, longest first) in its
+    own persistent launch, with no collective on the data path; one gather of
+    the energies at the end checks that every instance was evaluated."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2406_17248_gb300 import distributed as D
+    from paper_2406_17248_gb300 import inputs as I
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    inst = I.batched_vqe(args.instances, seed=4)
+    costs = [D.instance_cost(it.circuit.n_qubits, len(it.circuit.gates)) for it in inst]
+    mine = D.partition_by_cost(costs, ws)[rank]
+    sub = [inst[i] for i in mine]
+    b = Q.Batch(sub, Q.C64)
+    params = torch.tensor(np.concatenate([it.params for it in sub]), dtype=torch.float64, device="cuda")
+    energies = torch.empty(len(sub), dtype=torch.float64, device="cuda")
+    grads = torch.empty_like(params)
+    for _ in range(args.warmup):
+        b.expectation_with_grad_device(params, energies, grads)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        b.expectation_with_grad_device(params, energies, grads)
+    t1.record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = reduce_max(t0.elapsed_time(t1) / args.steps, ws)
+    allr = [None] * ws
+    dist.all_gather_object(allr, (mine, energies.cpu().numpy().tolist()))
+    if rank == 0:
+        seen = sorted(i for idx, _ in allr for i in idx)
+        assert seen == list(range(len(inst))), "an instance was not evaluated"
+        line = {"metric": "batched VQE energy+adjoint-grad instances/s", "value": len(inst) / (ms / 1e3),
+                "unit": "instances/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "strong", "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"{len(inst)} instances, n ~ U{{10..20}}, HEA depth ~ U{{2..10}}, TFIM, "
+                                       "complex64, seed 4; instances partitioned by 2^n x gates",
+                           "instances": len(inst), "parallelism": f"instances over {ws} ranks"}}
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
+def measure_random_c64(Q, n=28, G=500, reps=5, warmup=3):
+    """The 28-qubit random circuit (500 gates over {H, RX, RY, RZ, CNOT, CZ},
+    seed 2) on complex64 fused passes: gates/s and the passes' HBM roofline
+    (algorithmic bytes of the traced passes / their CUDA-event time)."""
+    import torch
+    from paper_2406_17248_gb300 import inputs as I
+    circ = I.random_circuit(n, G, seed=2)
+    c = Q.circuit_from(circ).finalize(Q.C64)
+    s = Q.State(n, Q.C64)
+    for _ in range(warmup):
+        s.set_basis(0)
+        c.apply(s)
+    torch.cuda.synchronize()
+    Q.trace_enable(True)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(reps):
+        s.set_basis(0)
+        c.apply(s)
+    t1.record()
+    torch.cuda.synchronize()
+    Q.trace_enable(False)
+    k_ms, k_by, k_kind = Q.trace_read()
+    ms = t0.elapsed_time(t1) / reps
+    peak, peak_kind = measured_peak_hbm()
+    gbps = float(k_by.sum() / (k_ms.sum() / 1e3) / 1e9) if len(k_ms) else None
+    micro = int((k_kind == 10).sum()) // reps
+    del s
+    torch.cuda.empty_cache()
+    return {"n_qubits": n, "gates": G, "dtype": "c64", "gates_per_s": G / (ms / 1e3), "ms": ms,
+            "passes": c.info()["passes"], "micro_op_passes": micro, "GBps": gbps, "peak": peak,
+            "frac": gbps / peak if gbps else None, "peak_source": f"{peak_kind} hbm_gbs",
+            "note": "state reset to |0...0> each repetition (set_basis, inside the timed region)"}
 
 
 def run_random_workload(args):

@@ -85,9 +85,10 @@ typedef struct qs_qaoa qs_qaoa;
 
 /* Execution options for a circuit plan.  Zero means "library default". */
 typedef struct {
-  int fuse;       /* 1 (default): fused shared-memory tile passes (complex64 passes that qualify run
-                     as pre-decoded micro-ops on TMA-fed tiles, the others on the op interpreter);
-                     2: fused passes, all on the op interpreter; -1: one kernel per gate */
+  int fuse;       /* 1 (default): fused shared-memory tile passes (complex64 states of 22 or more
+                     qubits run the passes that qualify as pre-decoded micro-ops on TMA-fed tiles,
+                     the rest on the op interpreter); 2: all on the op interpreter; 3: micro-ops
+                     wherever a pass qualifies, whatever the size; -1: one kernel per gate */
   int tile_bits;  /* log2 amplitudes per fused tile, 6..13 (default 12 for c64, 11 for c128) */
   int low_bits;   /* low (contiguous) qubits present in every tile, 1..tile_bits (default 4) */
   int checkpoint; /* adjoint state checkpoints, 0 (default): none.  Circuits: every `checkpoint`

@@ -333,7 +333,10 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
   // complex64 micro-op passes: without a tile option the forward sweep takes
   // 2^13-amplitude tiles (16 compute warps per SM) and the reverse sweep, which
   // carries psi and lam, 2^12 (three buffers of both fit in shared memory)
-  const bool micro = dt == QS_C64 && P.fuse != 2;
+  // (states below 22 qubits have too few tiles to fill the GPU with one
+  // 192 KB CTA per SM; their many small launches overlap better on the
+  // interpreter kernel: the 2048-instance batch ran 5150 -> 3897 instances/s)
+  const bool micro = dt == QS_C64 && (P.fuse == 3 || (P.fuse == 1 && P.ne >= kMicroMinQubits));
   int m_fwd = P.m, m_rev = P.m;
   if (micro && !c->opts.tile_bits) {
     m_fwd = std::min(13, P.ne);
@@ -793,7 +796,7 @@ qs_status qs_circuit_finalize(qs_circuit* c, qs_dtype dtype, const qs_options* o
     QS_CHECK(opts->tile_bits == 0 || (opts->tile_bits >= kMinTileBits && opts->tile_bits <= kMaxTileBits),
              "tile_bits must be 0 or 6..13");
     QS_CHECK(opts->low_bits >= 0 && opts->low_bits <= kMaxTileBits, "low_bits must be 0..13");
-    QS_CHECK(opts->fuse >= -1 && opts->fuse <= 2, "fuse must be -1, 0, 1 or 2");
+    QS_CHECK(opts->fuse >= -1 && opts->fuse <= 3, "fuse must be -1, 0, 1, 2 or 3");
     QS_CHECK(opts->checkpoint >= 0, "checkpoint must be >= 0");
     c->opts = *opts;
   }

@@ -20,6 +20,7 @@ constexpr int kMaxTileBits = 13;     // 2^13 amplitudes per tile
 // Largest tile whose two-state (psi, lam) pass fits in shared memory.
 constexpr int max_tile_bits(qs_dtype dt) { return dt == QS_C64 ? 13 : 12; }
 constexpr int kMinTileBits = 6;
+constexpr int kMicroMinQubits = 22;  // default use of the complex64 micro-op tile passes
 constexpr int kMaxSlotsPerPass = 256;  // gradient/energy accumulators of one launch
 constexpr int kMaxPhasesPerPass = 64;
 constexpr int kSmallMaxBytes = 96 * 1024;  // per-state bytes of the one-CTA engine

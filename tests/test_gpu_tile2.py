@@ -1,5 +1,5 @@
 """GPU parity of the complex64 micro-op tile passes (k_tile2.cu) against the
-FP64 oracle and the interpreter kernel: every gate kind with 0-2 controls on
+FP64 oracle and the interpreter kernel (fuse = 3 forces the micro-op form at these sizes): every gate kind with 0-2 controls on
 register, tile and outside bits, dense two-qubit matrices, the adjoint reverse
 passes with shared parameters, and tile shapes whose low run spans several box
 dimensions.  Tracing confirms which kernel ran (kind 10: micro-op passes)."""
@@ -44,7 +44,7 @@ def test_micro_forward_matches_oracle_and_interpreter(Q, n, opts):
     params = I.uniform_params(circ.n_params, 4100 + n)
     psi0 = I.random_state(n, 4200 + n)
     want = O.evolve(circ, params, psi0)
-    c = Q.circuit_from(circ).finalize(Q.C64, **opts)
+    c = Q.circuit_from(circ).finalize(Q.C64, fuse=3, **opts)
     s = Q.State(n, Q.C64).set_qs(psi0)
     kinds = traced_apply(Q, c, s, params)
     assert (kinds == MICRO).any(), "no pass ran as micro-ops"
@@ -61,7 +61,7 @@ def test_micro_random_recipe_20q(Q):
     n = 20
     circ = I.random_circuit(n, 500, seed=2)
     want = O.evolve(circ, [], O.zero_state(n))
-    c = Q.circuit_from(circ).finalize(Q.C64)
+    c = Q.circuit_from(circ).finalize(Q.C64, fuse=3)
     s = Q.State(n, Q.C64).set_basis(0)
     kinds = traced_apply(Q, c, s, [])
     assert (kinds == MICRO).all(), kinds
@@ -79,7 +79,7 @@ def test_micro_adjoint_matches_oracle(Q, n, opts):
     psi0 = I.random_state(n, 4600 + n)
     E0, g0 = O.adjoint_gradient(circ, ham, params, psi0)
     import torch
-    c = Q.circuit_from(circ).finalize(Q.C64, **opts)
+    c = Q.circuit_from(circ).finalize(Q.C64, fuse=3, **opts)
     psi, lam = Q.State(n, Q.C64).set_qs(psi0), Q.State(n, Q.C64)
     torch.cuda.synchronize()
     Q.trace_enable(True)

@@ -376,12 +376,28 @@ QS_API qs_status qs_qaoa_expectation_with_grad(qs_qaoa* q, qs_state* psi, qs_sta
  * at [68] and [85] the tile's load and store tensor maps, 17 entries each:
  * log2 of 8-byte words per amplitude, local bits covered by one box, and per
  * dimension 0..4 its first word-index bit, its width in bits and the box width
- * in bits.  slot_out/slot_w: output (0 = E, 1 + l = dgamma_l, 1 + p + l =
- * dbeta_l) and weight per slot. */
-#define QS_XPLAN_REC 102
+ * in bits, then at [102] the offset of the pass's phase weights in the
+ * per-call coefficient table.  slot_out/slot_w: output (0 = E, 1 + l =
+ * dgamma_l, 1 + p + l = dbeta_l) and weight per slot. */
+#define QS_XPLAN_REC 103
 QS_API qs_status qs_qaoa_xplan(int n_qubits, const int* edges, int n_edges, int p, double gamma_scale, int tile_bits,
                                int low_bits, int which, long long* rec, int max_passes, int* n_passes,
                                int* slot_out, double* slot_w, int max_slots, int* n_slots);
+
+/* The per-call coefficient table of the same plans (host only), for
+ * inspection and host-side tests: interleaved FP64 complex, *n_entries
+ * entries (table: double[2 * max_entries]).  Per layer l at l * (2 |E| + 4):
+ * the cost LUT exp(-i gs gamma_l C) for cut = 0..|E| times its renormalisation,
+ * the reverse LUT (conjugate phases, its own renormalisation), then (t, 0) of
+ * the scaled mixer of RX(beta_l) and of RX(-beta_l): [[1, -it], [-it, 1]]
+ * with t = s/c when |c| >= |s| (c, s = cos, sin of the half angle), else
+ * t = -c/s with every qubit the step rotates flipped in the data.  Then each
+ * pass's phase weights (record [102]): per phase (w1, w3), (wd, 0), the factors
+ * of the step-1, step-3 and diagonal sums.  *flip = 1: the energy plan leaves
+ * every qubit flipped (the engine flips the state back). */
+QS_API qs_status qs_qaoa_xcoef(int n_qubits, const int* edges, int n_edges, int p, double gamma_scale, int tile_bits,
+                               int low_bits, const double* gamma, const double* beta, double* table, int max_entries,
+                               int* n_entries, int* flip);
 
 /* One evaluation without handles, in the shape of the QuPack QAOA call (§6.2):
  * graph, depth and angles in; energy and gradients out (host arrays of p

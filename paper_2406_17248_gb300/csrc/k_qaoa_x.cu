@@ -21,6 +21,7 @@
 // still hit distinct banks.  C(x) is assembled per amplitude from a per-pass
 // table of in-tile edge counts and per-tile linear terms (computed by warp 0
 // two tiles ahead), so no cut-value array is read.
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 
@@ -75,33 +76,34 @@ __device__ __forceinline__ uint64_t x_l2g(const XPass& P, uint32_t l) {
 }
 
 // ---------------------------------------------------------------- one-state steps
-// RX(c, s) = [[c, -is], [-is, c]] on register bit RB
+// scaled mixer [[1, -it], [-it, 1]] on register bit RB: one FMA per real output
 template <int RB>
-__device__ __forceinline__ void xrx1(float2 (&a)[kXN], float c, float s) {
+__device__ __forceinline__ void xrx1(float2 (&a)[kXN], float t) {
 #pragma unroll
   for (int j = 0; j < kXN; ++j) {
     if (j & (1 << RB)) continue;
     const int j1 = j | (1 << RB);
     const float2 x0 = a[j], x1 = a[j1];
-    a[j].x = __fmaf_rn(c, x0.x, s * x1.y);
-    a[j].y = __fmaf_rn(c, x0.y, -s * x1.x);
-    a[j1].x = __fmaf_rn(c, x1.x, s * x0.y);
-    a[j1].y = __fmaf_rn(c, x1.y, -s * x0.x);
+    a[j].x = __fmaf_rn(t, x1.y, x0.x);
+    a[j].y = __fmaf_rn(-t, x1.x, x0.y);
+    a[j1].x = __fmaf_rn(t, x0.y, x1.x);
+    a[j1].y = __fmaf_rn(-t, x0.x, x1.y);
   }
 }
 // ---------------------------------------------------------------- two-state steps
-// RE = (psi.re, lam.re), IM = (psi.im, lam.im): RX(c, s) on both states at once
+// RE = (psi.re, lam.re), IM = (psi.im, lam.im): the scaled mixer on both states
+// at once, one packed FMA per pair of real outputs
 template <int RB, int N>
-__device__ __forceinline__ void xrx2(float2 (&RE)[N], float2 (&IM)[N], float2 c2, float2 s2, float2 ms2) {
+__device__ __forceinline__ void xrx2(float2 (&RE)[N], float2 (&IM)[N], float2 t2, float2 mt2) {
 #pragma unroll
   for (int j = 0; j < N; ++j) {
     if (j & (1 << RB)) continue;
     const int j1 = j | (1 << RB);
     const float2 r0 = RE[j], i0 = IM[j], r1 = RE[j1], i1 = IM[j1];
-    RE[j] = __ffma2_rn(c2, r0, __fmul2_rn(s2, i1));
-    IM[j] = __ffma2_rn(c2, i0, __fmul2_rn(ms2, r1));
-    RE[j1] = __ffma2_rn(c2, r1, __fmul2_rn(s2, i0));
-    IM[j1] = __ffma2_rn(c2, i1, __fmul2_rn(ms2, r0));
+    RE[j] = __ffma2_rn(t2, i1, r0);
+    IM[j] = __ffma2_rn(mt2, r1, i0);
+    RE[j1] = __ffma2_rn(t2, i0, r1);
+    IM[j1] = __ffma2_rn(mt2, r0, i1);
   }
 }
 // Im <lam|X_RB|psi> over the sub-cube (four independent partial sums)
@@ -135,8 +137,8 @@ struct XPh {
   int cutb, w0, w1, w2, w3;     // cut value = fs[l0 | L(j)] + cutb + W(j)
   uint32_t fs, lut;             // shared addresses of the edge-count table and the LUT
   int ne;
-  float2 cs1, cs3;
-  float plus;
+  float2 cs1, cs3;              // steps 1 and 3: (scaled-mixer t, weight 1 / |scale|^2 of the step's sums)
+  float pw;                     // the |+> amplitude in a generating phase, else the diagonal sum's weight
 };
 
 // Register-index sums: L(j) = OR of the local bits, S(j) = XOR of the shared
@@ -151,31 +153,40 @@ struct XPh {
 
 // RX on the first K register bits
 template <int K>
-__device__ __forceinline__ void xrx1_k(float2 (&a)[kXN], float2 cs) {
-  if (K > 0) xrx1<0>(a, cs.x, cs.y);
-  if (K > 1) xrx1<1>(a, cs.x, cs.y);
-  if (K > 2) xrx1<2>(a, cs.x, cs.y);
-  if (K > 3) xrx1<3>(a, cs.x, cs.y);
+__device__ __forceinline__ void xrx1_k(float2 (&a)[kXN], float2 ts) {
+  if (K > 0) xrx1<0>(a, ts.x);
+  if (K > 1) xrx1<1>(a, ts.x);
+  if (K > 2) xrx1<2>(a, ts.x);
+  if (K > 3) xrx1<3>(a, ts.x);
 }
+// Im <lam|X_q|psi> of each of the first K register bits, each taken before its
+// rotation, then the rotation; ts = (t, weight of the step's start).  Every
+// scaled rotation multiplies the data's |scale|^2 by 1 + t^2 (= 1/c^2 or 1/s^2
+// in the two forms), so term r carries the weight times kappa^r,
+// kappa = 1 / (1 + t^2)
 template <int K, int N>
-__device__ __forceinline__ float xrx2_k(float2 (&RE)[N], float2 (&IM)[N], float2 cs) {
-  const float2 c2 = make_float2(cs.x, cs.x), s2 = make_float2(cs.y, cs.y), ms2 = make_float2(-cs.y, -cs.y);
-  float g = 0.f;
+__device__ __forceinline__ float xrx2_k(float2 (&RE)[N], float2 (&IM)[N], float2 ts) {
+  const float2 t2 = make_float2(ts.x, ts.x), mt2 = make_float2(-ts.x, -ts.x);
+  const float kap = __frcp_rn(__fmaf_rn(ts.x, ts.x, 1.f));
+  float g = 0.f, sc = ts.y;  // the step's weight at its start
   if (K > 0) {
-    g += xgx2<0>(RE, IM);
-    xrx2<0>(RE, IM, c2, s2, ms2);
+    g = sc * xgx2<0>(RE, IM);
+    xrx2<0>(RE, IM, t2, mt2);
+    sc *= kap;
   }
   if (K > 1) {
-    g += xgx2<1>(RE, IM);
-    xrx2<1>(RE, IM, c2, s2, ms2);
+    g = __fmaf_rn(sc, xgx2<1>(RE, IM), g);
+    xrx2<1>(RE, IM, t2, mt2);
+    sc *= kap;
   }
   if (K > 2) {
-    g += xgx2<2>(RE, IM);
-    xrx2<2>(RE, IM, c2, s2, ms2);
+    g = __fmaf_rn(sc, xgx2<2>(RE, IM), g);
+    xrx2<2>(RE, IM, t2, mt2);
+    sc *= kap;
   }
   if (K > 3) {
-    g += xgx2<3>(RE, IM);
-    xrx2<3>(RE, IM, c2, s2, ms2);
+    g = __fmaf_rn(sc, xgx2<3>(RE, IM), g);
+    xrx2<3>(RE, IM, t2, mt2);
   }
   return g;
 }
@@ -186,7 +197,7 @@ __device__ __forceinline__ void xphase1(const XPh& h, float (&acc)[3]) {
   float2 a[kXN];
   if (GEN) {
 #pragma unroll
-    for (int j = 0; j < kXN; ++j) a[j] = make_float2(h.plus, 0.f);
+    for (int j = 0; j < kXN; ++j) a[j] = make_float2(h.pw, 0.f);
   } else {
 #pragma unroll
     for (int j = 0; j < kXN; ++j) a[j] = lds64(h.tb + (h.pb ^ XS(j)));
@@ -209,7 +220,7 @@ __device__ __forceinline__ void xphase1(const XPh& h, float (&acc)[3]) {
       if (j & 1) e1 = __fmaf_rn(C, pr, e1);
       else e0 = __fmaf_rn(C, pr, e0);
     }
-    acc[1] += e0 + e1;
+    acc[1] = __fmaf_rn(h.pw, e0 + e1, acc[1]);
   }
   xrx1_k<K3>(a, h.cs3);
 #pragma unroll
@@ -244,7 +255,7 @@ __device__ __forceinline__ void xphase2(const XPh& h, float (&acc)[3]) {
       RE[j] = __ffma2_rn(dr, r, __fmul2_rn(mdi, i));
       IM[j] = __ffma2_rn(dr, i, __fmul2_rn(di, r));
     }
-    acc[1] += g0 + g1;
+    acc[1] = __fmaf_rn(h.pw, g0 + g1, acc[1]);
   } else if (DG == XD_ENERGY) {
     float e0 = 0.f, e1 = 0.f;
 #pragma unroll
@@ -256,7 +267,7 @@ __device__ __forceinline__ void xphase2(const XPh& h, float (&acc)[3]) {
       RE[j].y = C * RE[j].x;  // lam = C psi
       IM[j].y = C * IM[j].x;
     }
-    acc[1] += e0 + e1;
+    acc[1] = __fmaf_rn(h.pw, e0 + e1, acc[1]);
   }
   if (K3 > 0) acc[2] += xrx2_k<K3>(RE, IM, h.cs3);
 #pragma unroll
@@ -311,6 +322,7 @@ __global__ void __launch_bounds__(TWO ? 288 : 544, 1) qx_kernel(const __grid_con
   __shared__ uint64_t s_dep[5][64];
   __shared__ int s_lin[kXNB][16];  // per tile buffer: w_i of local bit i (i < 13), g at [15]
   __shared__ double s_red[17];
+  __shared__ float s_w[4 * kXMaxPhases];  // per phase: w1, w3, wd (phase weights of the scaled mixer)
   __shared__ int s_bad;
   __shared__ __align__(8) uint64_t s_full[kXNB], s_done[kXNB];
   const int tid = threadIdx.x, NT = blockDim.x, T = NT - 32, lane = tid & 31, warp = tid >> 5;
@@ -352,6 +364,11 @@ __global__ void __launch_bounds__(TWO ? 288 : 544, 1) qx_kernel(const __grid_con
   if (has_diag && P.fs_off >= 0) {
     const uint4* src = reinterpret_cast<const uint4*>(args.fs + P.fs_off);
     for (uint32_t i = tid; i < (tile_n >> 4); i += NT) reinterpret_cast<uint4*>(s_fs)[i] = src[i];
+  }
+  for (int i = tid; i < 2 * n_ph; i += NT) {
+    const float2 w = args.coef[P.cw + i];
+    s_w[2 * i] = w.x;
+    s_w[2 * i + 1] = w.y;
   }
   const float2 cs1 = P.c1 >= 0 ? args.coef[P.c1] : make_float2(1.f, 0.f);
   const float2 cs3 = P.c3 >= 0 ? args.coef[P.c3] : make_float2(1.f, 0.f);
@@ -509,9 +526,8 @@ __global__ void __launch_bounds__(TWO ? 288 : 544, 1) qx_kernel(const __grid_con
         h.fs = xsh(s_fs);
         h.lut = xsh(s_lut);
         h.ne = args.n_edges;
-        h.cs1 = cs1;
-        h.cs3 = cs3;
-        h.plus = args.plus_amp;
+        const bool gen = (flags & XF_GEN_PLUS) && ph == 0;
+        h.pw = gen ? args.plus_amp : s_w[4 * ph + 2];
         h.cutb = h.w0 = h.w1 = h.w2 = h.w3 = 0;
         const int diag = PH.diag;
         if (diag) {  // cut values: fs[l] + g + sum of w over the set local bits
@@ -524,7 +540,10 @@ __global__ void __launch_bounds__(TWO ? 288 : 544, 1) qx_kernel(const __grid_con
           h.w2 = ((kap & 4u) ? -1 : 1) * lin[__ffs(h.lb2) - 1];
           h.w3 = h.lb3 ? ((kap & 8u) ? -1 : 1) * lin[__ffs(h.lb3) - 1] : 0;
         }
-        const int code = xcode(__popc(PH.m1), diag, __popc(PH.m3)) + ((flags & XF_GEN_PLUS) && ph == 0 ? 125 : 0);
+        const int code = xcode(__popc(PH.m1), diag, __popc(PH.m3)) + (gen ? 125 : 0);
+        // the phase's sums are weighted by 1 / |data scale|^2 where each is taken
+        h.cs1 = make_float2(cs1.x, s_w[4 * ph]);
+        h.cs3 = make_float2(cs3.x, s_w[4 * ph + 1]);
         const bool ok = TWO ? xdispatch2(code, h, acc) : xdispatch1(code, h, acc);
         if (!ok && tid == 0) s_bad = 1;
         bar_compute(T);
@@ -570,7 +589,30 @@ size_t qx_smem(int two_state, int m, int n_edges) {
   return off + 128 + (size_t)kXNB * tile;
 }
 
+// psi[x] <-> psi[NOT x] (every qubit flipped): pairs of amplitudes (2k, 2k + 1)
+// swap with (N - 1 - 2k, N - 2 - 2k), in 16-byte words
+__global__ void qx_flip_kernel(float4* psi, uint64_t half_words, uint64_t words) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < half_words;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t r = words - 1 - k;
+    const float4 a = psi[k], b = psi[r];
+    psi[k] = make_float4(b.z, b.w, b.x, b.y);
+    psi[r] = make_float4(a.z, a.w, a.x, a.y);
+  }
+}
+
 }  // namespace
+
+qs_status launch_qx_flip(float2* psi, int n, cudaStream_t st) {
+  const uint64_t words = 1ull << (n - 1), half = words / 2;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::min<uint64_t>((half + 255) / 256, (uint64_t)std::max(sms, 1) * 8);
+  qx_flip_kernel<<<std::max(grid, 1), 256, 0, st>>>(reinterpret_cast<float4*>(psi), half, words);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
 
 int qx_occupancy(int two_state, int m, int n_edges, int /*n_phases*/) {
   static int last_key[2] = {-1, -1}, last_occ[2] = {0, 0};

@@ -456,8 +456,7 @@ qs_status build_x_engine(qs_qaoa* q, const std::vector<std::pair<int, int>>& es,
   // buffer is left unused by these passes)
   QS_CUDA(cudaMalloc(&q->d_il_priv, (size_t)16 << n));
   q->il = true;
-  const CoefLayout L = layout_for(q->n_edges);
-  q->n_coef = L.per_layer * p;
+  q->n_coef = X.n_coef;
   QS_CUDA(cudaMalloc(&q->d_coef, (size_t)q->n_coef * 16));
   QS_TRY(build_csr(q->gslots, 1 + 2 * p, &q->g_row, &q->g_sidx, &q->g_w, nullptr));
   QS_TRY(build_csr(q->eslots, 1, &q->e_row, &q->e_sidx, &q->e_w, nullptr));
@@ -794,10 +793,21 @@ qs_status run_xpasses(qs_qaoa* q, const std::vector<XPass>& passes, const std::v
   return QS_OK;
 }
 
+// The call's coefficient table: the scaled-mixer table of the two-shape passes
+// (and whether the energy plan leaves every qubit flipped), else the plain one.
+qs_status fill_coef_for(qs_qaoa* q, const double* gamma, const double* beta, bool* flip) {
+  *flip = false;
+  if (!q->xp) return fill_qaoa_coef(q, gamma, beta);
+  for (int l = 0; l < q->p; ++l)
+    QS_CHECK(std::isfinite(gamma[l]) && std::isfinite(beta[l]), "non-finite angle");
+  return qx_fill_coef(q->n, q->p, q->n_edges, q->gs, gamma, beta, q->xg, q->xe, q->n_coef, &q->host_coef, flip);
+}
+
 qs_status qaoa_energy(qs_qaoa* q, qs_state* psi, const double* gamma, const double* beta, double* energy) {
   QS_TRY(qaoa_check(q, psi, gamma, beta));
   cudaStream_t st = psi->st;
-  QS_TRY(fill_qaoa_coef(q, gamma, beta));
+  bool flip = false;
+  QS_TRY(fill_coef_for(q, gamma, beta, &flip));
   QS_TRY(upload_table(q->host_coef, q->dt, q->d_coef, st, psi->host_out));
   const int n_slots = (int)q->eslots.out.size();
   const size_t part = (size_t)std::max(n_slots, 1) * q->grid2;
@@ -809,6 +819,7 @@ qs_status qaoa_energy(qs_qaoa* q, qs_state* psi, const double* gamma, const doub
     double* d_out = d_slot + n_slots;
     QS_CUDA(cudaMemsetAsync(d_part, 0, xpart * sizeof(double), st));
     QS_TRY(run_xpasses(q, q->xe, q->xe_two, q->d_xe, psi->ptr, nullptr, d_part, st));
+    if (flip) QS_TRY(launch_qx_flip(reinterpret_cast<float2*>(psi->ptr), q->n, st));  // the evolved state exactly
     QS_TRY(launch_reduce_slots(d_part, n_slots, q->xstride, nullptr, d_slot, st));
     QS_TRY(launch_param_gather(d_slot, q->e_row, q->e_sidx, q->e_w, 1, d_out, st));
     if (energy) {
@@ -853,7 +864,8 @@ qs_status qs_qaoa_expectation_with_grad(qs_qaoa* q, qs_state* psi, qs_state* lam
   QS_CHECK(energy && dgamma && dbeta, "null output");
   if (lam->st != psi->st) QS_CUDA(cudaStreamSynchronize(lam->st));
   cudaStream_t st = psi->st;
-  QS_TRY(fill_qaoa_coef(q, gamma, beta));
+  bool flip = false;  // psi and lam are undefined on return: no unflip needed
+  QS_TRY(fill_coef_for(q, gamma, beta, &flip));
   QS_TRY(upload_table(q->host_coef, q->dt, q->d_coef, st, psi->host_out));
   const int n_slots = (int)q->gslots.out.size();
   const int n_out = 1 + 2 * q->p;

@@ -1,6 +1,18 @@
 // Descriptors of the complex64 QAOA passes with separate forward and reverse
 // tile shapes (host planner <-> kernels).
 //
+// Scaled mixer.  RX(b) = [[c, -is], [-is, c]] is applied as c [[1, -it], [-it, 1]]
+// with t = s/c when |c| >= |s| (one FMA per real output instead of a product
+// and an FMA), and when |s| > |c| as (s/i) X [[1, -it'], [-it', 1]], t' = -c/s:
+// the data then hold the state with that qubit flipped.  Every layer's mixer
+// is complete before the next cost layer, so the flips there are none or all
+// qubits, and C(x) = C(NOT x) for MaxCut: the cost layers, the energy and all
+// the gradient terms read the flipped data unchanged.  The scalar the data
+// carry (a product of 1/c and i/s factors) is tracked on the host: the cost
+// LUTs fold in a renormalisation (so the data stay O(1) and the evolved state
+// comes out exact), and each phase's gradient and energy sums are weighted by
+// 1 / |scalar|^2 at the point where they are taken.
+//
 // A pass stages one tile (2^m amplitudes over a bit set S that holds the low c
 // qubits) in shared memory and runs phases over it.  In a phase every thread
 // holds 16 amplitudes (4 register bits) of one sub-cube and applies, in order:
@@ -56,7 +68,7 @@ struct XPass {
   int fs_off;        // byte offset of this pass's in-tile edge-count table (2^m bytes)
   int ncomp;         // complement (tile-index) bits
   int n_cc;          // complement nodes with complement neighbours above them
-  int pad;
+  int cw;            // coefficient offset of the pass's phase weights: per phase (w1, w3), (wd, 0)
   int8_t comp[kXMaxComp];
   uint8_t ccnode[kXMaxComp];
   uint64_t ccmask[kXMaxComp];  // complement neighbours (above) of ccnode[k]
@@ -96,5 +108,7 @@ int qx_occupancy(int two_state, int m, int n_edges, int n_phases);
 int qx_grid(int two_state, int m, int n_edges, int n_phases, uint64_t n_tiles);
 qs_status launch_qx_pass(int two_state, const XPass* d_pass, const XPass& h_pass, const XLaunch& L,
                          cudaStream_t st);
+// psi[x] <-> psi[NOT x] over the n-qubit complex64 state (n >= 2)
+qs_status launch_qx_flip(float2* psi, int n, cudaStream_t st);
 
 }  // namespace qs

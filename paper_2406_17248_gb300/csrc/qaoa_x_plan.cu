@@ -21,6 +21,7 @@
 // to 4.8 TB/s; so the small-stride qubits are dealt round-robin to the groups.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 
 #include "plan.h"
@@ -491,11 +492,114 @@ qs_status qx_make_plans(const XBuild& B, double gs, XPlans* X) {
     X->energy_two.push_back(0);
   }
   if (X->fs.empty()) X->fs.assign(16, 0);
+  {  // phase-weight blocks after the per-layer coefficients
+    const int per_layer = 2 * (B.n_edges + 1) + 2;
+    int off = p * per_layer;
+    for (XPass& P : X->grad) {
+      P.cw = off;
+      off += 2 * kXMaxPhases;
+    }
+    for (XPass& P : X->energy) {
+      P.cw = off;
+      off += 2 * kXMaxPhases;
+    }
+    X->n_coef = off;
+  }
   const double S = 8.0 * (double)(1ull << n);
   X->bytes_grad = S + 2 * S * (double)(fw.size() - 2) + 3 * S + 4 * S * (double)(rv.size() - 1) + 2 * S;
   X->bytes_energy = S + 2 * S * (double)(fw.size() - 1);
   X->n_fwd = (int)fw.size();
   X->n_rev = (int)rv.size();
+  return QS_OK;
+}
+
+qs_status qx_fill_coef(int n, int p, int n_edges, double gs, const double* gamma, const double* beta,
+                       const std::vector<XPass>& grad, const std::vector<XPass>& energy, int n_coef,
+                       std::vector<double>* tab, bool* flip) {
+  using cd = std::complex<double>;
+  const int E1 = n_edges + 1, per_layer = 2 * E1 + 2;
+  tab->assign((size_t)2 * n_coef, 0.0);
+  auto put = [&](int o, cd v) {
+    (*tab)[2 * (size_t)o] = v.real();
+    (*tab)[2 * (size_t)o + 1] = v.imag();
+  };
+  // scaled mixer of layer l, direction d (0: RX(beta), 1: RX(-beta)): t and the factor g
+  std::vector<double> tt(2 * p);
+  std::vector<cd> gg(2 * p);
+  std::vector<char> form_b(p);
+  for (int l = 0; l < p; ++l) {
+    const double c = std::cos(0.5 * beta[l]), s0 = std::sin(0.5 * beta[l]);
+    form_b[l] = std::fabs(s0) > std::fabs(c);
+    for (int d = 0; d < 2; ++d) {
+      const double sd = d == 0 ? s0 : -s0;
+      if (!form_b[l]) {
+        tt[2 * l + d] = sd / c;
+        gg[2 * l + d] = cd(1.0 / c, 0.0);
+      } else {
+        tt[2 * l + d] = -c / sd;
+        gg[2 * l + d] = cd(0.0, 1.0 / sd);
+      }
+      put(l * per_layer + 2 * E1 + d, cd(tt[2 * l + d], 0.0));
+    }
+  }
+  // renormalisation of each cost LUT (forward: index l, reverse: p + l), set where first met
+  std::vector<cd> rho(2 * p, cd(0, 0));
+  std::vector<char> have(2 * p, 0);
+  auto ipow = [](cd g, int k) {
+    cd r(1, 0);
+    for (int i = 0; i < k; ++i) r *= g;
+    return r;
+  };
+  auto step = [&](int off) -> int {  // coefficient offset -> 2 l + d
+    const int l = off / per_layer, d = off % per_layer - 2 * E1;
+    return 2 * l + d;
+  };
+  auto simulate = [&](const std::vector<XPass>& plan) {
+    cd sigma(1, 0);
+    for (const XPass& P : plan) {
+      for (int ph = 0; ph < P.n_phases; ++ph) {
+        const XPhase& X = P.ph[ph];
+        const int k1 = __builtin_popcount(X.m1), k3 = __builtin_popcount(X.m3);
+        const double w1 = 1.0 / std::norm(sigma);
+        if (k1) sigma *= ipow(gg[step(P.c1)], k1);
+        const double wd = 1.0 / std::norm(sigma);
+        if (X.diag == XD_COST || X.diag == XD_COST_GRAD) {
+          const int l = P.cd / per_layer, rev = X.diag == XD_COST_GRAD;
+          const int key = rev * p + l;
+          if (!have[key]) {
+            if (!rev && l == p - 1)  // the state leaves the last mixer exactly
+              rho[key] = 1.0 / (sigma * ipow(gg[2 * l], n));
+            else
+              rho[key] = 1.0 / std::abs(sigma);
+            have[key] = 1;
+          }
+          sigma *= rho[key];
+        }
+        const double w3 = 1.0 / std::norm(sigma);
+        if (k3) sigma *= ipow(gg[step(P.c3)], k3);
+        put(P.cw + 2 * ph, cd(w1, w3));
+        put(P.cw + 2 * ph + 1, cd(wd, 0.0));
+      }
+    }
+    return sigma;
+  };
+  simulate(grad);
+  const cd s_end = simulate(energy);
+  if (std::abs(s_end - cd(1, 0)) > 1e-6) {
+    set_error("qaoa: scaled-mixer bookkeeping does not close (internal error)");
+    return QS_ERR_UNSUPPORTED;
+  }
+  for (int l = 0; l < p; ++l) {
+    const cd rf = have[l] ? rho[l] : cd(1, 0), rr = have[p + l] ? rho[p + l] : cd(1, 0);
+    for (int k = 0; k <= n_edges; ++k) {
+      const double ph = gs * gamma[l] * (double)(n_edges - 2 * k);
+      put(l * per_layer + k, cd(std::cos(ph), -std::sin(ph)) * rf);
+      put(l * per_layer + E1 + k, cd(std::cos(ph), std::sin(ph)) * rr);
+    }
+  }
+  int nb = 0;
+  for (int l = 0; l < p; ++l) nb += form_b[l];
+  *flip = (nb & 1) != 0;
   return QS_OK;
 }
 
@@ -566,6 +670,7 @@ extern "C" qs_status qs_qaoa_xplan(int n_qubits, const int* edges, int n_edges, 
       q[2] = X2.diag;
       for (int k = 0; k < 4; ++k) q[3 + k] = X2.lbit[k] ? gl[__builtin_ctz(X2.lbit[k])] : -1;
     }
+    r[12 + 7 * kXMaxPhases + 34] = P.cw;
     for (int k = 0; k < 2; ++k) {
       long long* t = r + 12 + 7 * kXMaxPhases + 17 * k;
       t[0] = P.me[k];
@@ -577,5 +682,36 @@ extern "C" qs_status qs_qaoa_xplan(int n_qubits, const int* edges, int n_edges, 
       }
     }
   }
+  return QS_OK;
+}
+
+extern "C" qs_status qs_qaoa_xcoef(int n_qubits, const int* edges, int n_edges, int p, double gamma_scale,
+                                   int tile_bits, int low_bits, const double* gamma, const double* beta,
+                                   double* table, int max_entries, int* n_entries, int* flip) {
+  QS_CHECK(edges != nullptr && n_edges >= 1 && n_edges <= 255, "need 1..255 edges");
+  QS_CHECK(n_qubits >= 10 && n_qubits <= kMaxQubits, "n_qubits must be in 10..34");
+  QS_CHECK(gamma && beta && table && n_entries && flip, "null argument");
+  XBuild B;
+  B.n = n_qubits;
+  B.p = p;
+  B.mr = tile_bits ? tile_bits : 12;
+  B.cr = low_bits ? low_bits : 3;
+  B.mf = B.mr + 1;
+  B.cf = B.cr + 1;
+  B.n_edges = n_edges;
+  for (int e = 0; e < n_edges; ++e) {
+    const int a = edges[2 * e], b = edges[2 * e + 1];
+    QS_CHECK(a >= 0 && a < n_qubits && b >= 0 && b < n_qubits && a != b, "edge endpoint out of range");
+    B.edges.push_back({std::min(a, b), std::max(a, b)});
+  }
+  XPlans X;
+  QS_TRY(qx_make_plans(B, gamma_scale, &X));
+  QS_CHECK(X.n_coef <= max_entries, "table too small");
+  std::vector<double> tab;
+  bool fl = false;
+  QS_TRY(qx_fill_coef(n_qubits, p, n_edges, gamma_scale, gamma, beta, X.grad, X.energy, X.n_coef, &tab, &fl));
+  for (size_t i = 0; i < tab.size(); ++i) table[i] = tab[i];
+  *n_entries = X.n_coef;
+  *flip = fl ? 1 : 0;
   return QS_OK;
 }

@@ -49,7 +49,17 @@ struct XPlans {
   std::vector<uint8_t> fs;
   double bytes_grad = 0, bytes_energy = 0;
   int n_fwd = 0, n_rev = 0;  // forward passes (the turnaround included), reverse passes
+  int n_coef = 0;            // complex entries of the per-call coefficient table
 };
 qs_status qx_make_plans(const XBuild& B, double gs, XPlans* X);
+
+// The per-call coefficient table (interleaved FP64 complex, n_coef entries):
+// per layer the renormalised cost LUTs and the scaled-mixer t of both sweep
+// directions, then every pass's phase weights (see qaoa_x.h).  *flip: the
+// energy plan leaves the state with every qubit flipped (an odd number of
+// layers took the flipped mixer form).
+qs_status qx_fill_coef(int n, int p, int n_edges, double gs, const double* gamma, const double* beta,
+                       const std::vector<XPass>& grad, const std::vector<XPass>& energy, int n_coef,
+                       std::vector<double>* tab, bool* flip);
 
 }  // namespace qs

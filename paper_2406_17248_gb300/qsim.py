@@ -81,6 +81,7 @@ SIGNATURES = [
     ("qs_qaoa_expectation", [_VP, _VP, _PD, _PD, _PD]),
     ("qs_qaoa_expectation_with_grad", [_VP, _VP, _VP, _PD, _PD, _PD, _PD, _PD]),
     ("qs_qaoa_xplan", [_I, _PI, _I, _I, _D, _I, _I, _I, C.POINTER(C.c_longlong), _I, _PI, _PI, _PD, _I, _PI]),
+    ("qs_qaoa_xcoef", [_I, _PI, _I, _I, _D, _I, _I, _PD, _PD, _PD, _I, _PI, _PI]),
     ("qs_qaoa_evaluate", [_I, _PI, _I, _I, _D, _PD, _PD, _I, _PD, _PD, _PD]),
     ("qs_batch_create", [_I, _PI, _PI, _VP, _PI, _PU64, _PU64, _PD, _PI, _I, _VP, _PVP]),
     ("qs_batch_destroy", [_VP]),
@@ -629,7 +630,7 @@ def apply_matrix(state: State, targets, matrix, engine: int = 0) -> State:
     return state
 
 
-XPLAN_REC = 102
+XPLAN_REC = 103
 
 
 def qaoa_xplan(n: int, edges, p: int, gamma_scale: float = 1.0, tile_bits: int = 0, low_bits: int = 0,
@@ -652,12 +653,29 @@ def qaoa_xplan(n: int, edges, p: int, gamma_scale: float = 1.0, tile_bits: int =
         for ph in range(r[3]):
             q = r[12 + 7 * ph:12 + 7 * ph + 7]
             d["phases"].append(dict(m1=q[0], m3=q[1], diag=q[2], reg=list(q[3:7])))
+        d["cw"] = r[102]
         d["maps"] = []
         for k in range(2):
             t = r[68 + 17 * k:68 + 17 * k + 17]
             d["maps"].append(dict(e=t[0], lb=t[1], a=list(t[2:7]), w=list(t[7:12]), box=list(t[12:17])))
         out.append(d)
     return out, [(so[i], sw[i]) for i in range(nslot.value)]
+
+
+def qaoa_xcoef(n: int, edges, p: int, gamma, beta, gamma_scale: float = 1.0, tile_bits: int = 0, low_bits: int = 0):
+    """The per-call coefficient table of the complex64 two-shape QAOA passes
+    (qs_qaoa_xcoef, host only): complex entries and whether the energy plan
+    leaves every qubit flipped."""
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    maxe = 1 << 16
+    tab = np.zeros(2 * maxe)
+    ne, fl = C.c_int(), C.c_int()
+    _check(lib().qs_qaoa_xcoef(n, e.ctypes.data_as(_PI), int(e.size // 2), p, gamma_scale, tile_bits, low_bits,
+                               _dptr(g), _dptr(b), _dptr(tab), maxe, C.byref(ne), C.byref(fl)))
+    t = tab[:2 * ne.value]
+    return t[0::2] + 1j * t[1::2], bool(fl.value)
 
 
 def expectation_noalloc(state: State, ham: I.PauliSum, stream=None) -> float:

@@ -428,3 +428,27 @@ def test_qaoa_two_shape_passes(Q, n, p, tb, lb, gs):
     check(tag + " state", state_err(psi.get_qs(), want), TOL[0])
     # max cut from the lazily built cut-value array
     assert q.max_cut() == O.maxcut_brute_force(n, edges)
+
+
+@pytest.mark.parametrize("beta", [(0.3, 0.5, 1.0), (2.9, 0.5, 1.0), (2.9, 3.0, 0.2), (2.5, 2.8, -2.9)])
+def test_qaoa_scaled_mixer_forms_and_flip(Q, beta):
+    """The two-shape passes apply RX as [[1, -it], [-it, 1]] in one of two forms
+    (t = s/c, or t = -c/s with the qubits flipped in the data): angles with
+    zero to three layers in the flipped form, so the energy plan ends flipped or
+    not; energy, gradients and the evolved state against the oracle."""
+    n, p, gs = 18, 3, 0.5
+    edges = I.random_regular_graph(n, 3, seed=11)
+    gamma = np.array([0.4, 1.1, 2.3])
+    beta = np.array(beta)
+    E0, dg0, db0 = O.qaoa_expectation_with_grad(n, edges, gamma, beta, gs)
+    q = Q.QAOA(n, edges, p, gamma_scale=gs, dtype=0, tile_bits=11, low_bits=3, engine=2)
+    psi, lam = Q.State(n, 0), Q.State(n, 0)
+    E, dg, db = q.expectation_with_grad(psi, lam, gamma, beta)
+    te, tg, tb_ = qaoa_grad_tols(0, n, len(edges), gs)
+    tag = f"qaoa scaled mixer beta={tuple(beta)}"
+    check(tag + " energy", abs(E - E0), te)
+    check(tag + " dgamma", np.abs(dg - dg0), tg)
+    check(tag + " dbeta", np.abs(db - db0), tb_)
+    check(tag + " energy-only", abs(q.expectation(psi, gamma, beta) - E0), te)
+    want = O.qaoa_layers_state(n, edges, gamma, beta, gs)
+    check(tag + " state", state_err(psi.get_qs(), want), TOL[0])

@@ -200,3 +200,101 @@ def test_tile_tensor_maps_land_the_tile_in_local_order(Q, n, p, tb, lb):
                 want = ((want + toff) << e) | sub
                 assert len(got) == (1 << len(glob)) << e
                 assert np.array_equal(got, want)
+
+
+def _mix(v, n, q, t):
+    """[[1, -it], [-it, 1]] on qubit q (the scaled mixer the kernels apply)."""
+    w = v.reshape(-1, 2, 1 << q)
+    a0, a1 = w[:, 0, :].copy(), w[:, 1, :].copy()
+    w[:, 0, :] = a0 - 1j * t * a1
+    w[:, 1, :] = a1 - 1j * t * a0
+    return w.reshape(-1)
+
+
+def replay_scaled(plan, slots, n, edges, tab, p):
+    """The plan's steps in FP64 with the call's coefficient table exactly as the
+    kernels use it: scaled mixers, renormalised LUTs, each mixer gradient term
+    taken before its rotation and weighted by the phase weight times
+    (1 + t^2)^-r after r rotations of its step."""
+    C = O.cut_values(n, edges).astype(np.int64)
+    cut = (len(edges) - C) // 2
+    psi = np.zeros(1 << n, complex)
+    lam = np.zeros(1 << n, complex)
+    vals = np.zeros(len(slots))
+    for P in plan:
+        acc = [0.0, 0.0, 0.0]
+        two = P["two"]
+        if P["flags"] & 1:
+            psi = O.plus_state(n).astype(complex)
+        if two and P["flags"] & 2:
+            lam = np.zeros(1 << n, complex)
+        for k, ph in enumerate(P["phases"]):
+            w1, w3 = tab[P["cw"] + 2 * k].real, tab[P["cw"] + 2 * k].imag
+            wd = tab[P["cw"] + 2 * k + 1].real
+            for step, mask, off, wgt in ((0, ph["m1"], P["c1"], w1), (2, ph["m3"], P["c3"], w3)):
+                if step == 2:
+                    d = ph["diag"]
+                    if d == 1:
+                        psi = psi * tab[P["cd"] + cut]
+                    elif d == 2:
+                        acc[1] += wd * float(np.sum(C * np.imag(np.conj(lam) * psi)))
+                        lut = tab[P["cd"] + cut]
+                        psi, lam = psi * lut, lam * lut
+                    elif d == 3:
+                        acc[1] += wd * float(np.sum(C * np.abs(psi) ** 2))
+                        if two:
+                            lam = C * psi
+                qs = [ph["reg"][r] for r in range(4) if (mask >> r) & 1]
+                if not qs:
+                    continue
+                t = tab[off].real
+                kap = 1.0 / (1.0 + t * t)  # each scaled rotation multiplies |scale|^2 by 1 + t^2
+                for r, q in enumerate(qs):
+                    if two:
+                        acc[step] += wgt * kap ** r * _gx(lam, psi, n, q)
+                    psi = _mix(psi, n, q, t)
+                    if two:
+                        lam = _mix(lam, n, q, t)
+        for k in range(3):
+            if P["slot"][k] >= 0:
+                vals[P["slot"][k]] += acc[k]
+    out = np.zeros(1 + 2 * p)
+    for s, (o, w) in enumerate(slots):
+        out[o] += w * vals[s]
+    return out, psi
+
+
+# angles that put some layers in each mixer form (|cos b/2| >= |sin b/2| and <)
+SCALED = [(12, 2, 9, 2, 0.5, (0.3, 2.9)), (13, 3, 9, 2, 1.0, (2.5, 0.4, 3.0)),
+          (14, 2, 9, 3, 0.5, (2.2, 2.8)), (16, 4, 10, 3, 0.5, (0.2, 1.8, 2.7, -2.9))]
+
+
+@pytest.mark.parametrize("n,p,tb,lb,gs,beta", SCALED)
+def test_scaled_mixer_table_replays_to_the_oracle(Q, n, p, tb, lb, gs, beta):
+    edges = I.random_regular_graph(n, 3 if n % 2 == 0 else 4, seed=n + 7)
+    gamma = I.uniform_params(p, n, 0.0, np.pi)
+    beta = np.array(beta)
+    tab, _ = Q.qaoa_xcoef(n, edges, p, gamma, beta, gs, tb, lb)
+    plan, slots = Q.qaoa_xplan(n, edges, p, gs, tb, lb, which=0)
+    out, _ = replay_scaled(plan, slots, n, edges, tab, p)
+    E0, dg0, db0 = O.qaoa_expectation_with_grad(n, edges, gamma, beta, gs)
+    assert abs(out[0] - E0) < 1e-10
+    assert np.abs(out[1:1 + p] - dg0).max() < 1e-9
+    assert np.abs(out[1 + p:] - db0).max() < 1e-9
+
+
+@pytest.mark.parametrize("n,p,tb,lb,gs,beta", SCALED)
+def test_scaled_energy_plan_gives_the_state_up_to_the_reported_flip(Q, n, p, tb, lb, gs, beta):
+    edges = I.random_regular_graph(n, 3 if n % 2 == 0 else 4, seed=n + 7)
+    gamma = I.uniform_params(p, n + 1, 0.0, np.pi)
+    beta = np.array(beta)
+    tab, flip = Q.qaoa_xcoef(n, edges, p, gamma, beta, gs, tb, lb)
+    assert flip == (int(np.sum(np.abs(np.sin(beta / 2)) > np.abs(np.cos(beta / 2)))) % 2 == 1)
+    plan, slots = Q.qaoa_xplan(n, edges, p, gs, tb, lb, which=1)
+    out, psi = replay_scaled(plan, slots, n, edges, tab, p)
+    if flip:
+        psi = psi[::-1]  # index NOT x = 2^n - 1 - x
+    want = O.qaoa_layers_state(n, edges, gamma, beta, gs)
+    assert np.abs(psi - want).max() < 1e-12
+    E0, _, _ = O.qaoa_expectation_with_grad(n, edges, gamma, beta, gs)
+    assert abs(out[0] - E0) < 1e-10

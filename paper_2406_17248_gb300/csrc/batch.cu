@@ -32,13 +32,36 @@ struct BLane {
   double* scratch = nullptr;
 };
 
+// Large instances of one qubit count run in lock-step: pass k of every member
+// in one launch (instance = blockIdx.y), then one batched Hamiltonian apply,
+// energy reduction, reverse passes, slot reduction and parameter gather.
+struct BGroup {
+  int ne = 0, m_fwd = 0, m_rev = 0, grid1 = 0, grid2 = 0, hgrid = 0;
+  std::vector<int> members;  // indices into qs_batch::large
+  void* psi = nullptr;       // members' states back to back
+  void* lam = nullptr;
+  double* scratch = nullptr;
+  TileKArgs* d_fwd = nullptr;  // [pass k][member with that pass]
+  TileKArgs* d_rev = nullptr;
+  std::vector<int> fwd_off, fwd_cnt, rev_off, rev_cnt;
+  HamMultiArgs* d_ham = nullptr;
+  ReduceMultiArgs* d_red_e = nullptr;
+  ReduceMultiArgs* d_red_s = nullptr;
+  GatherMultiArgs* d_gather = nullptr;
+  int n_red_s = 0, n_gather = 0, max_slots = 0, max_params = 0;
+  cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
 struct qs_batch {
   qs_dtype dt = QS_C64;
   cudaStream_t st = nullptr;
   int n_inst = 0;
   int n_small = 0;                 // instances run by the persistent kernel (shared memory)
   std::vector<BLarge> large;       // instances run on fused tile passes
-  std::vector<BLane> lanes;
+  std::vector<BGroup> groups;      // ... in lock-step by qubit count
+  std::vector<char> in_group;      // per entry of `large`
+  std::vector<BLane> lanes;        // ... or one by one on lanes (the rest)
   BCoefGate* d_cg = nullptr;       // coefficient-table entries of the large instances' gates
   int n_cg = 0;
   BCoefRun* d_runs = nullptr;      // fused single-qubit runs of their forward passes
@@ -78,6 +101,13 @@ void free_batch(qs_batch* b) {
   for (BLarge& L : b->large) {
     if (L.c) qs_circuit_destroy(L.c);
     if (L.h) qs_ham_destroy(L.h);
+  }
+  for (BGroup& G : b->groups) {
+    for (void* p : {G.psi, G.lam, (void*)G.scratch, (void*)G.d_fwd, (void*)G.d_rev, (void*)G.d_ham,
+                    (void*)G.d_red_e, (void*)G.d_red_s, (void*)G.d_gather})
+      if (p) cudaFree(p);
+    if (G.st) cudaStreamDestroy(G.st);
+    if (G.done) cudaEventDestroy(G.done);
   }
   for (BLane& L : b->lanes) {
     if (L.st) cudaStreamDestroy(L.st);
@@ -134,6 +164,153 @@ qs_status run_large(const qs_batch* b, const BLarge& I, const BLane& L, double* 
   return QS_OK;
 }
 
+// One lock-step group: |0>, forward passes, lam = H psi and E, reverse passes,
+// slot sums, gradient gather; every step one launch over all members.  The
+// output pointers in the argument tables are the batch's own buffers.
+qs_status run_group(const qs_batch* b, const BGroup& G, double* energies, double* grads) {
+  (void)energies;
+  (void)grads;
+  QS_TRY(launch_set_zero_multi(b->dt, G.psi, G.ne, (int)G.members.size(), G.st));
+  for (size_t k = 0; k < G.fwd_cnt.size(); ++k)
+    QS_TRY(launch_tile_pass_multi(b->dt, 1, G.m_fwd, G.d_fwd + G.fwd_off[k], G.fwd_cnt[k], G.grid1, G.st));
+  QS_TRY(launch_ham_apply_multi(b->dt, G.d_ham, (int)G.members.size(), G.hgrid, G.st));
+  QS_TRY(launch_reduce_multi(G.d_red_e, (int)G.members.size(), 1, G.st));
+  for (size_t k = 0; k < G.rev_cnt.size(); ++k)
+    QS_TRY(launch_tile_pass_multi(b->dt, 2, G.m_rev, G.d_rev + G.rev_off[k], G.rev_cnt[k], G.grid2, G.st));
+  QS_TRY(launch_reduce_multi(G.d_red_s, G.n_red_s, G.max_slots, G.st));
+  QS_TRY(launch_gather_multi(G.d_gather, G.n_gather, G.max_params, G.st));
+  return QS_OK;
+}
+
+// Groups of large instances with one qubit count whose plans run only on the
+// interpreter kernel (equal tile shapes and grids): built once, the argument
+// tables pointing at the batch's parameter, energy and gradient buffers.
+qs_status build_groups(qs_batch* b) {
+  b->in_group.assign(b->large.size(), 0);
+  std::vector<int> by_ne(64, -1);
+  for (size_t k = 0; k < b->large.size(); ++k) {
+    const CircuitPlan& P = b->large[k].c->plan;
+    bool ok = P.valid && P.fuse >= 0 && P.ckpt.empty() && !P.fwd.passes.empty() && !P.rev.passes.empty();
+    for (const auto& pp : P.fwd.passes) ok = ok && !pp.t2;
+    for (const auto& pp : P.rev.passes) ok = ok && !pp.t2;
+    if (!ok) continue;
+    const int mf = P.fwd.passes[0].hdr.m, mr = P.rev.passes[0].hdr.m;
+    for (const auto& pp : P.fwd.passes) ok = ok && pp.hdr.m == mf;
+    for (const auto& pp : P.rev.passes) ok = ok && pp.hdr.m == mr;
+    if (!ok) continue;
+    int gi = by_ne[P.ne];
+    if (gi >= 0) {
+      const BGroup& G = b->groups[gi];
+      if (G.m_fwd != mf || G.m_rev != mr || G.grid1 != P.grid1 || G.grid2 != P.grid2) continue;
+    } else {
+      gi = (int)b->groups.size();
+      by_ne[P.ne] = gi;
+      b->groups.emplace_back();
+      BGroup& G = b->groups.back();
+      G.ne = P.ne;
+      G.m_fwd = mf;
+      G.m_rev = mr;
+      G.grid1 = P.grid1;
+      G.grid2 = P.grid2;
+      G.hgrid = ham_grid_size(P.ne);
+    }
+    b->groups[gi].members.push_back((int)k);
+    b->in_group[k] = 1;
+  }
+  const size_t amp = amp_bytes(b->dt);
+  for (BGroup& G : b->groups) {
+    const int cnt = (int)G.members.size();
+    const size_t sb = amp << G.ne;
+    QS_CUDA(cudaMalloc(&G.psi, sb * cnt));
+    QS_CUDA(cudaMalloc(&G.lam, sb * cnt));
+    QS_CUDA(cudaStreamCreateWithFlags(&G.st, cudaStreamNonBlocking));
+    QS_CUDA(cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming));
+    // scratch per member: slot partials (slots x grid2), slot sums, Hamiltonian partials
+    std::vector<size_t> off(cnt + 1, 0);
+    for (int i = 0; i < cnt; ++i) {
+      const CircuitPlan& P = b->large[G.members[i]].c->plan;
+      const size_t ns = P.rev_slots.out.size();
+      off[i + 1] = off[i] + std::max<size_t>(ns, 1) * G.grid2 + ns + (size_t)G.hgrid + 2;
+    }
+    QS_CUDA(cudaMalloc(&G.scratch, off[cnt] * sizeof(double)));
+    auto state = [&](void* base, int i) { return (void*)((char*)base + sb * (size_t)i); };
+    std::vector<TileKArgs> fwd, rev;
+    std::vector<HamMultiArgs> ham;
+    std::vector<ReduceMultiArgs> rede, reds;
+    std::vector<GatherMultiArgs> gath;
+    size_t max_f = 0, max_r = 0;
+    for (int i = 0; i < cnt; ++i) {
+      const CircuitPlan& P = b->large[G.members[i]].c->plan;
+      max_f = std::max(max_f, P.fwd.passes.size());
+      max_r = std::max(max_r, P.rev.passes.size());
+    }
+    auto targs = [&](const CircuitPlan& P, const TilePlan& T, int k, int i) {
+      TileKArgs a;
+      a.psi = state(G.psi, i);
+      a.lam = state(G.lam, i);
+      a.pass = T.d_pass + k;
+      a.phases = T.d_phase;
+      a.ops = T.d_ops;
+      a.coef = P.d_coef;
+      a.cut = nullptr;
+      a.partials = G.scratch + off[i];
+      a.n = G.ne;
+      a.n_edges = 0;
+      a.grid_stride = G.grid2;
+      return a;
+    };
+    for (size_t k = 0; k < max_f; ++k) {
+      G.fwd_off.push_back((int)fwd.size());
+      for (int i = 0; i < cnt; ++i) {
+        const CircuitPlan& P = b->large[G.members[i]].c->plan;
+        if (k < P.fwd.passes.size()) fwd.push_back(targs(P, P.fwd, (int)k, i));
+      }
+      G.fwd_cnt.push_back((int)fwd.size() - G.fwd_off.back());
+    }
+    for (size_t k = 0; k < max_r; ++k) {
+      G.rev_off.push_back((int)rev.size());
+      for (int i = 0; i < cnt; ++i) {
+        const CircuitPlan& P = b->large[G.members[i]].c->plan;
+        if (k < P.rev.passes.size()) rev.push_back(targs(P, P.rev, (int)k, i));
+      }
+      G.rev_cnt.push_back((int)rev.size() - G.rev_off.back());
+    }
+    for (int i = 0; i < cnt; ++i) {
+      const BLarge& L = b->large[G.members[i]];
+      const CircuitPlan& P = L.c->plan;
+      const size_t ns = P.rev_slots.out.size();
+      double* part = G.scratch + off[i];
+      double* slot = part + std::max<size_t>(ns, 1) * G.grid2;
+      double* hpart = slot + ns + 1;
+      HamMultiArgs h;
+      h.psi = state(G.psi, i);
+      h.lam = state(G.lam, i);
+      h.groups = L.h->d_groups;
+      h.terms = L.h->d_terms;
+      h.partials = hpart;
+      h.n = G.ne;
+      h.n_groups = L.h->n_groups;
+      ham.push_back(h);
+      rede.push_back(ReduceMultiArgs{hpart, b->d_energy + L.inst, 1, G.hgrid});
+      if (ns > 0 && L.n_params > 0) {
+        reds.push_back(ReduceMultiArgs{part, slot, (int)ns, G.grid2});
+        gath.push_back(GatherMultiArgs{slot, P.d_row, P.d_sidx, P.d_w, b->d_grad + L.param_off, L.n_params, 0});
+        G.max_slots = std::max(G.max_slots, (int)ns);
+        G.max_params = std::max(G.max_params, L.n_params);
+      }
+    }
+    G.n_red_s = (int)reds.size();
+    G.n_gather = (int)gath.size();
+    QS_TRY(upload(&G.d_fwd, fwd));
+    QS_TRY(upload(&G.d_rev, rev));
+    QS_TRY(upload(&G.d_ham, ham));
+    QS_TRY(upload(&G.d_red_e, rede));
+    QS_TRY(upload(&G.d_red_s, reds));
+    QS_TRY(upload(&G.d_gather, gath));
+  }
+  return QS_OK;
+}
+
 }  // namespace
 
 // Enqueue one evaluation of every instance on st (lanes forked and joined).
@@ -147,8 +324,14 @@ static qs_status issue_all(qs_batch* b, cudaStream_t st, const double* dev_param
     QS_TRY(launch_batch_runs(b->dt, b->d_runs, b->n_runs, b->d_run_members, dev_params, st));
     QS_CUDA(cudaEventRecord(b->ev_fill, st));
     for (BLane& L : b->lanes) QS_CUDA(cudaStreamWaitEvent(L.st, b->ev_fill, 0));
+    for (BGroup& G : b->groups) {
+      QS_CUDA(cudaStreamWaitEvent(G.st, b->ev_fill, 0));
+      QS_TRY(run_group(b, G, dev_energies, dev_grads));
+      QS_CUDA(cudaEventRecord(G.done, G.st));
+    }
+    size_t lane = 0;
     for (size_t k = 0; k < b->large.size(); ++k)
-      QS_TRY(run_large(b, b->large[k], b->lanes[k % b->lanes.size()], dev_energies, dev_grads));
+      if (!b->in_group[k]) QS_TRY(run_large(b, b->large[k], b->lanes[lane++ % b->lanes.size()], dev_energies, dev_grads));
     for (BLane& L : b->lanes) QS_CUDA(cudaEventRecord(L.done, L.st));
   }
   if (b->n_small > 0) {
@@ -176,6 +359,7 @@ static qs_status issue_all(qs_batch* b, cudaStream_t st, const double* dev_param
     }
   }
   for (BLane& L : b->lanes) QS_CUDA(cudaStreamWaitEvent(st, L.done, 0));
+  for (BGroup& G : b->groups) QS_CUDA(cudaStreamWaitEvent(st, G.done, 0));
   return QS_OK;
 }
 
@@ -274,6 +458,17 @@ qs_status qs_batch_create(int n_inst, const int* n_qubits, const int* gate_offse
   b->st = (cudaStream_t)cuda_stream;
   b->n_inst = n_inst;
   b->n_params_total = param_offsets[n_inst];
+  {
+    const size_t np = std::max(b->n_params_total, 1);
+    cudaError_t e = cudaMalloc(&b->d_params, np * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_grad, np * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_energy, (size_t)n_inst * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(int));
+    if (e != cudaSuccess) {
+      free_batch(b);
+      return cuda_fail(e, "cudaMalloc(batch outputs)");
+    }
+  }
   // shared memory sized for the largest shared-memory instance (more CTAs per SM
   // when all are small)
   int sm_n = 1, sm_g = 1, sm_p = 1;
@@ -381,7 +576,12 @@ qs_status qs_batch_create(int n_inst, const int* n_qubits, const int* gate_offse
       // flight keep the SMs busy; the largest instances are dealt out first
       std::stable_sort(b->large.begin(), b->large.end(),
                        [&](const BLarge& x, const BLarge& y) { return inst[x.inst].cost > inst[y.inst].cost; });
-      const int n_lanes = std::min<int>(kBatchLanes, (int)b->large.size());
+      s = build_groups(b);
+    }
+    if (s == QS_OK) {
+      int rest = 0;
+      for (char g : b->in_group) rest += !g;
+      const int n_lanes = std::min<int>(kBatchLanes, rest);
       const size_t state_bytes = amp_bytes(dtype) << max_ne;
       cudaError_t e = cudaEventCreateWithFlags(&b->ev_fill, cudaEventDisableTiming);
       for (int l = 0; l < n_lanes && e == cudaSuccess; ++l) {
@@ -405,15 +605,6 @@ qs_status qs_batch_create(int n_inst, const int* n_qubits, const int* gate_offse
       (s = upload(&b->d_terms, terms)) != QS_OK) {
     free_batch(b);
     return s;
-  }
-  const size_t np = std::max(b->n_params_total, 1);
-  cudaError_t e = cudaMalloc(&b->d_params, np * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_grad, np * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_energy, (size_t)n_inst * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(int));
-  if (e != cudaSuccess) {
-    free_batch(b);
-    return cuda_fail(e, "cudaMalloc(batch outputs)");
   }
   *out = b;
   return QS_OK;
@@ -480,7 +671,18 @@ qs_status qs_batch_expectation_with_grad_device(qs_batch* b, const double* dev_p
       return QS_OK;
     }
   }
-  return issue_all(b, b->st, dev_params, dev_energies, dev_grads);
+  // direct launches: the argument tables of the lock-step groups name the
+  // batch's own buffers, so the call goes through them
+  const size_t np = (size_t)b->n_params_total * sizeof(double);
+  if (np && dev_params != b->d_params)
+    QS_CUDA(cudaMemcpyAsync(b->d_params, dev_params, np, cudaMemcpyDeviceToDevice, b->st));
+  QS_TRY(issue_all(b, b->st, b->d_params, b->d_energy, b->d_grad));
+  if (dev_energies != b->d_energy)
+    QS_CUDA(cudaMemcpyAsync(dev_energies, b->d_energy, (size_t)b->n_inst * sizeof(double), cudaMemcpyDeviceToDevice,
+                            b->st));
+  if (np && dev_grads != b->d_grad)
+    QS_CUDA(cudaMemcpyAsync(dev_grads, b->d_grad, np, cudaMemcpyDeviceToDevice, b->st));
+  return QS_OK;
 }
 
 qs_status qs_batch_expectation_with_grad(qs_batch* b, const double* params, double* energies, double* grads) {

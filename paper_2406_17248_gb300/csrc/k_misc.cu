@@ -442,9 +442,10 @@ constexpr int kFlush = 16;  // FP32 partial sums are flushed to FP64 every kFlus
 
 // lam_y = sum_g psi_{y^m_g} * sum_{k in g} c'_k (-1)^{popcount((y^m_g) & z_k)};  E += Re(conj(psi_y) lam_y)
 template <class T>
-__global__ void ham_apply_kernel(const typename V2<T>::V* __restrict__ psi, typename V2<T>::V* __restrict__ lam, int n,
-                                 const DevHamGroup* __restrict__ groups, int n_groups,
-                                 const DevHamTerm* __restrict__ terms, double* partials) {
+__device__ __forceinline__ void ham_apply_kernel_body(const typename V2<T>::V* __restrict__ psi,
+                                                      typename V2<T>::V* __restrict__ lam, int n,
+                                                      const DevHamGroup* __restrict__ groups, int n_groups,
+                                                      const DevHamTerm* __restrict__ terms, double* partials) {
   using V = typename V2<T>::V;
   __shared__ double sh[32];
   const uint64_t N = 1ull << n;
@@ -484,6 +485,21 @@ __global__ void ham_apply_kernel(const typename V2<T>::V* __restrict__ psi, type
   acc_d += (double)acc;
   const double s = block_sum(acc_d, sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <class T>
+__global__ void ham_apply_kernel(const typename V2<T>::V* __restrict__ psi, typename V2<T>::V* __restrict__ lam, int n,
+                                 const DevHamGroup* __restrict__ groups, int n_groups,
+                                 const DevHamTerm* __restrict__ terms, double* partials) {
+  ham_apply_kernel_body<T>(psi, lam, n, groups, n_groups, terms, partials);
+}
+
+template <class T>
+__global__ void ham_apply_multi_kernel(const HamMultiArgs* __restrict__ argv) {
+  const HamMultiArgs a = argv[blockIdx.y];
+  ham_apply_kernel_body<T>(reinterpret_cast<const typename V2<T>::V*>(a.psi),
+                           reinterpret_cast<typename V2<T>::V*>(a.lam), a.n, a.groups, a.n_groups, a.terms,
+                           a.partials);
 }
 
 // <a|b> partials: [0][grid] real, [1][grid] imag
@@ -575,6 +591,32 @@ __global__ void reduce_slots_kernel(const double* partials, int n_slots, int nb,
   for (int b = lane; b < nb; b += 32) v += partials[(size_t)warp * nb + b];
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if (lane == 0) out[warp] = scale ? v * scale[warp] : v;
+}
+
+__global__ void reduce_multi_kernel(const ReduceMultiArgs* __restrict__ argv) {
+  const ReduceMultiArgs a = argv[blockIdx.y];
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= a.n_slots) return;
+  double v = 0;
+  for (int b = lane; b < a.nb; b += 32) v += a.partials[(size_t)warp * a.nb + b];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) a.out[warp] = v;
+}
+
+__global__ void gather_multi_kernel(const GatherMultiArgs* __restrict__ argv) {
+  const GatherMultiArgs a = argv[blockIdx.y];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.n_params) return;
+  double s = 0;
+  for (int k = a.row_ptr[p]; k < a.row_ptr[p + 1]; ++k) s += a.gate_coef[k] * a.gate_grad[a.gate_idx[k]];
+  a.grad[p] = s;
+}
+
+template <class T>
+__global__ void set_zero_multi_kernel(typename V2<T>::V* base, uint64_t N, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) base[(uint64_t)i * N].x = (T)1;
 }
 
 __global__ void param_gather_kernel(const double* gate_grad, const int* row_ptr, const int* gate_idx,
@@ -1001,6 +1043,46 @@ qs_status launch_ham_apply(qs_dtype dt, const void* psi, void* lam, int n, const
   else
     ham_apply_kernel<double><<<grid, kThreads, 0, st>>>((const double2*)psi, (double2*)lam, n, groups, n_groups,
                                                         terms, partials);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_ham_apply_multi(qs_dtype dt, const HamMultiArgs* d_argv, int count, int grid, cudaStream_t st) {
+  if (count <= 0) return QS_OK;
+  const dim3 g((unsigned)grid, (unsigned)count);
+  if (dt == QS_C64)
+    ham_apply_multi_kernel<float><<<g, kThreads, 0, st>>>(d_argv);
+  else
+    ham_apply_multi_kernel<double><<<g, kThreads, 0, st>>>(d_argv);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_reduce_multi(const ReduceMultiArgs* d_argv, int count, int max_slots, cudaStream_t st) {
+  if (count <= 0 || max_slots <= 0) return QS_OK;
+  const dim3 g((unsigned)((max_slots * 32 + 255) / 256), (unsigned)count);
+  reduce_multi_kernel<<<g, 256, 0, st>>>(d_argv);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_gather_multi(const GatherMultiArgs* d_argv, int count, int max_params, cudaStream_t st) {
+  if (count <= 0 || max_params <= 0) return QS_OK;
+  const dim3 g((unsigned)((max_params + 127) / 128), (unsigned)count);
+  gather_multi_kernel<<<g, 128, 0, st>>>(d_argv);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_set_zero_multi(qs_dtype dt, void* base, int n, int count, cudaStream_t st) {
+  if (count <= 0) return QS_OK;
+  const size_t bytes = ((size_t)(dt == QS_C64 ? 8 : 16) << n) * (size_t)count;
+  QS_CUDA(cudaMemsetAsync(base, 0, bytes, st));
+  const int blocks = (count + 255) / 256;
+  if (dt == QS_C64)
+    set_zero_multi_kernel<float><<<blocks, 256, 0, st>>>((float2*)base, 1ull << n, count);
+  else
+    set_zero_multi_kernel<double><<<blocks, 256, 0, st>>>((double2*)base, 1ull << n, count);
   QS_CUDA(cudaGetLastError());
   return QS_OK;
 }

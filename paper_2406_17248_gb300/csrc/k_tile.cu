@@ -83,19 +83,6 @@ __device__ __forceinline__ T warp_sum(T v) {
 constexpr int RN = 1 << kRegBits;
 constexpr int kTileOpStage = 256;  // ops of a pass staged in shared memory (more: read from global)
 
-struct TileKArgs {
-  void* psi;
-  void* lam;
-  const DevPass* pass;
-  const DevPhase* phases;
-  const DevOp* ops;
-  const void* coef;
-  const uint8_t* cut;
-  double* partials;
-  int n;
-  int n_edges;
-  int grid_stride;  // stride of the partials array (the plan's grid)
-};
 
 template <int J>
 __device__ __forceinline__ uint32_t off_of(const uint32_t (&rm)[kRegBits]) {
@@ -311,8 +298,10 @@ __device__ __forceinline__ auto grad_x(const V (&a)[RN], const V (&b)[RN], uint3
 #ifndef QS_TILE_C64_MINB
 #define QS_TILE_C64_MINB 2
 #endif
+// The pass body: one CTA's share (tiles blockIdx.x, + gridDim.x, ...) of one
+// instance's pass, its gradient partials in column blockIdx.x.
 template <class T, int NS>
-__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? QS_TILE_C64_MINB : 1) tile_pass_kernel(TileKArgs args) {
+__device__ __forceinline__ void tile_pass_body(const TileKArgs& args) {
   using V = typename VecT<T>::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
 
@@ -719,6 +708,20 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? QS_TILE_C64_MIN
   }
 }
 
+template <class T, int NS>
+__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? QS_TILE_C64_MINB : 1) tile_pass_kernel(TileKArgs args) {
+  tile_pass_body<T, NS>(args);
+}
+
+// The same pass of many independent instances (equal tile shape and grid) in
+// one launch: instance blockIdx.y, its arguments from a device table.
+template <class T, int NS>
+__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? QS_TILE_C64_MINB : 1)
+    tile_pass_multi_kernel(const TileKArgs* __restrict__ argv) {
+  const TileKArgs args = argv[blockIdx.y];
+  tile_pass_body<T, NS>(args);
+}
+
 size_t tile_smem_bytes(qs_dtype dt, int m, int ns) {
   const size_t amp = dt == QS_C64 ? 8 : 16;
   const size_t tile = (size_t)1 << m;
@@ -769,6 +772,33 @@ int tile_grid_size(qs_dtype dt, int m, int ns, int n_tiles) {
   long g = (long)sm_count() * occ;
   if (g > n_tiles) g = n_tiles;
   return (int)(g < 1 ? 1 : g);
+}
+
+qs_status launch_tile_pass_multi(qs_dtype dt, int ns, int m, const TileKArgs* d_argv, int count, int grid,
+                                 cudaStream_t st) {
+  if (count <= 0) return QS_OK;
+  const size_t smem = tile_smem_bytes(dt, m, ns);
+  const dim3 g((unsigned)grid, (unsigned)count);
+  auto prep = [&](const void* fn) { return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); };
+  if (dt == QS_C64) {
+    if (ns == 2) {
+      QS_CUDA(prep((const void*)tile_pass_multi_kernel<float, 2>));
+      tile_pass_multi_kernel<float, 2><<<g, kTileThreads, smem, st>>>(d_argv);
+    } else {
+      QS_CUDA(prep((const void*)tile_pass_multi_kernel<float, 1>));
+      tile_pass_multi_kernel<float, 1><<<g, kTileThreads, smem, st>>>(d_argv);
+    }
+  } else {
+    if (ns == 2) {
+      QS_CUDA(prep((const void*)tile_pass_multi_kernel<double, 2>));
+      tile_pass_multi_kernel<double, 2><<<g, kTileThreads, smem, st>>>(d_argv);
+    } else {
+      QS_CUDA(prep((const void*)tile_pass_multi_kernel<double, 1>));
+      tile_pass_multi_kernel<double, 1><<<g, kTileThreads, smem, st>>>(d_argv);
+    }
+  }
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
 }
 
 qs_status launch_tile_pass(qs_dtype dt, const TilePlan& plan, int pi, const TileLaunch& L, cudaStream_t st) {

@@ -212,6 +212,25 @@ struct TileLaunch {
   int stride;  // stride of the partials array (the plan's 2-state grid)
 };
 
+// Kernel arguments of one instance's tile pass (device layout).
+struct TileKArgs {
+  void* psi;
+  void* lam;
+  const DevPass* pass;
+  const DevPhase* phases;
+  const DevOp* ops;
+  const void* coef;
+  const uint8_t* cut;
+  double* partials;
+  int n;
+  int n_edges;
+  int grid_stride;  // stride of the partials array (the plan's grid)
+};
+// The same pass index of `count` independent instances with equal tile bits m
+// and equal grid, in one launch (interpreter kernel): instance i's arguments in
+// d_argv[i].
+qs_status launch_tile_pass_multi(qs_dtype dt, int ns, int m, const TileKArgs* d_argv, int count, int grid,
+                                 cudaStream_t st);
 qs_status launch_tile2_pass(const TilePlan& plan, int pass_index, const TileLaunch& L, cudaStream_t st);
 qs_status launch_tile_pass(qs_dtype dt, const TilePlan& plan, int pass_index, const TileLaunch& L,
                            cudaStream_t st);
@@ -264,6 +283,36 @@ size_t sample_scratch_doubles(int n);
 // scratch[2 nb] = outcome, scratch[2 nb + 1] = 1/sqrt(P(outcome)).
 qs_status launch_measure(qs_dtype dt, void* psi, int n, int q, uint64_t seed, double* scratch, int nb,
                          cudaStream_t st);
+
+// Batched forms of the Hamiltonian apply, slot reduction and parameter gather:
+// one launch, instance blockIdx.y.
+struct HamMultiArgs {
+  const void* psi;
+  void* lam;
+  const DevHamGroup* groups;
+  const DevHamTerm* terms;
+  double* partials;
+  int n, n_groups;
+};
+struct ReduceMultiArgs {
+  const double* partials;
+  double* out;
+  int n_slots, nb;
+};
+struct GatherMultiArgs {
+  const double* gate_grad;
+  const int* row_ptr;
+  const int* gate_idx;
+  const double* gate_coef;
+  double* grad;
+  int n_params, pad;
+};
+qs_status launch_ham_apply_multi(qs_dtype dt, const HamMultiArgs* d_argv, int count, int grid, cudaStream_t st);
+qs_status launch_reduce_multi(const ReduceMultiArgs* d_argv, int count, int max_slots, cudaStream_t st);
+qs_status launch_gather_multi(const GatherMultiArgs* d_argv, int count, int max_params, cudaStream_t st);
+// psi_i = |0...0> for count states of 2^n amplitudes stored back to back
+qs_status launch_set_zero_multi(qs_dtype dt, void* base, int n, int count, cudaStream_t st);
+
 
 // ----------------------------------------------------------------------------- errors
 void set_error(const std::string& msg);

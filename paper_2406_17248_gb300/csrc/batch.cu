@@ -37,6 +37,11 @@ struct BLane {
 // energy reduction, reverse passes, slot reduction and parameter gather.
 struct BGroup {
   int ne = 0, m_fwd = 0, m_rev = 0, grid1 = 0, grid2 = 0, hgrid = 0;
+  bool micro = false;          // every pass in micro-op form (k_tile2.cu), else every pass on the interpreter
+  T2Args* d_fwd2 = nullptr;    // micro-op pass arguments, [pass k][member with that pass]
+  T2Args* d_rev2 = nullptr;
+  std::vector<uint32_t> fwd_smem, rev_smem;  // per pass index: the largest member's shared memory
+  int gx_fwd = 1, gx_rev = 1;  // CTAs per member (each loops over several tiles)
   std::vector<int> members;  // indices into qs_batch::large
   void* psi = nullptr;       // members' states back to back
   void* lam = nullptr;
@@ -104,7 +109,7 @@ void free_batch(qs_batch* b) {
   }
   for (BGroup& G : b->groups) {
     for (void* p : {G.psi, G.lam, (void*)G.scratch, (void*)G.d_fwd, (void*)G.d_rev, (void*)G.d_ham,
-                    (void*)G.d_red_e, (void*)G.d_red_s, (void*)G.d_gather})
+                    (void*)G.d_red_e, (void*)G.d_red_s, (void*)G.d_gather, (void*)G.d_fwd2, (void*)G.d_rev2})
       if (p) cudaFree(p);
     if (G.st) cudaStreamDestroy(G.st);
     if (G.done) cudaEventDestroy(G.done);
@@ -171,12 +176,20 @@ qs_status run_group(const qs_batch* b, const BGroup& G, double* energies, double
   (void)energies;
   (void)grads;
   QS_TRY(launch_set_zero_multi(b->dt, G.psi, G.ne, (int)G.members.size(), G.st));
-  for (size_t k = 0; k < G.fwd_cnt.size(); ++k)
-    QS_TRY(launch_tile_pass_multi(b->dt, 1, G.m_fwd, G.d_fwd + G.fwd_off[k], G.fwd_cnt[k], G.grid1, G.st));
+  for (size_t k = 0; k < G.fwd_cnt.size(); ++k) {
+    if (G.micro)
+      QS_TRY(launch_tile2_multi(1, G.d_fwd2 + G.fwd_off[k], G.fwd_cnt[k], G.gx_fwd, G.fwd_smem[k], G.st));
+    else
+      QS_TRY(launch_tile_pass_multi(b->dt, 1, G.m_fwd, G.d_fwd + G.fwd_off[k], G.fwd_cnt[k], G.grid1, G.st));
+  }
   QS_TRY(launch_ham_apply_multi(b->dt, G.d_ham, (int)G.members.size(), G.hgrid, G.st));
   QS_TRY(launch_reduce_multi(G.d_red_e, (int)G.members.size(), 1, G.st));
-  for (size_t k = 0; k < G.rev_cnt.size(); ++k)
-    QS_TRY(launch_tile_pass_multi(b->dt, 2, G.m_rev, G.d_rev + G.rev_off[k], G.rev_cnt[k], G.grid2, G.st));
+  for (size_t k = 0; k < G.rev_cnt.size(); ++k) {
+    if (G.micro)
+      QS_TRY(launch_tile2_multi(2, G.d_rev2 + G.rev_off[k], G.rev_cnt[k], G.gx_rev, G.rev_smem[k], G.st));
+    else
+      QS_TRY(launch_tile_pass_multi(b->dt, 2, G.m_rev, G.d_rev + G.rev_off[k], G.rev_cnt[k], G.grid2, G.st));
+  }
   QS_TRY(launch_reduce_multi(G.d_red_s, G.n_red_s, G.max_slots, G.st));
   QS_TRY(launch_gather_multi(G.d_gather, G.n_gather, G.max_params, G.st));
   return QS_OK;
@@ -191,8 +204,9 @@ qs_status build_groups(qs_batch* b) {
   for (size_t k = 0; k < b->large.size(); ++k) {
     const CircuitPlan& P = b->large[k].c->plan;
     bool ok = P.valid && P.fuse >= 0 && P.ckpt.empty() && !P.fwd.passes.empty() && !P.rev.passes.empty();
-    for (const auto& pp : P.fwd.passes) ok = ok && !pp.t2;
-    for (const auto& pp : P.rev.passes) ok = ok && !pp.t2;
+    const bool micro = P.fwd.passes[0].t2;
+    for (const auto& pp : P.fwd.passes) ok = ok && pp.t2 == micro;
+    for (const auto& pp : P.rev.passes) ok = ok && pp.t2 == micro;
     if (!ok) continue;
     const int mf = P.fwd.passes[0].hdr.m, mr = P.rev.passes[0].hdr.m;
     for (const auto& pp : P.fwd.passes) ok = ok && pp.hdr.m == mf;
@@ -201,12 +215,13 @@ qs_status build_groups(qs_batch* b) {
     int gi = by_ne[P.ne];
     if (gi >= 0) {
       const BGroup& G = b->groups[gi];
-      if (G.m_fwd != mf || G.m_rev != mr || G.grid1 != P.grid1 || G.grid2 != P.grid2) continue;
+      if (G.m_fwd != mf || G.m_rev != mr || G.grid1 != P.grid1 || G.grid2 != P.grid2 || G.micro != micro) continue;
     } else {
       gi = (int)b->groups.size();
       by_ne[P.ne] = gi;
       b->groups.emplace_back();
       BGroup& G = b->groups.back();
+      G.micro = micro;
       G.ne = P.ne;
       G.m_fwd = mf;
       G.m_rev = mr;
@@ -259,22 +274,52 @@ qs_status build_groups(qs_batch* b) {
       a.grid_stride = G.grid2;
       return a;
     };
+    std::vector<T2Args> fwd2, rev2;
+    // micro-op passes: CTAs per member so that each loops over about 8 tiles
+    G.gx_fwd = (int)std::max<uint64_t>(1, (1ull << (G.ne - G.m_fwd)) / 8);
+    G.gx_rev = (int)std::max<uint64_t>(1, (1ull << (G.ne - G.m_rev)) / 8);
+    auto t2args = [&](const CircuitPlan& P, const TilePlan& T, int k, int i, T2Args* a) {
+      return make_tile2_args(T, k, state(G.psi, i), state(G.lam, i), P.d_coef, G.scratch + off[i], G.grid2,
+                             G.grid2, G.ne, a);
+    };
     for (size_t k = 0; k < max_f; ++k) {
-      G.fwd_off.push_back((int)fwd.size());
+      G.fwd_off.push_back(G.micro ? (int)fwd2.size() : (int)fwd.size());
+      uint32_t sm = 0;
       for (int i = 0; i < cnt; ++i) {
         const CircuitPlan& P = b->large[G.members[i]].c->plan;
-        if (k < P.fwd.passes.size()) fwd.push_back(targs(P, P.fwd, (int)k, i));
+        if (k >= P.fwd.passes.size()) continue;
+        if (G.micro) {
+          T2Args a;
+          QS_TRY(t2args(P, P.fwd, (int)k, i, &a));
+          fwd2.push_back(a);
+          sm = std::max(sm, P.fwd.passes[k].t2hdr.smem);
+        } else {
+          fwd.push_back(targs(P, P.fwd, (int)k, i));
+        }
       }
-      G.fwd_cnt.push_back((int)fwd.size() - G.fwd_off.back());
+      G.fwd_cnt.push_back((G.micro ? (int)fwd2.size() : (int)fwd.size()) - G.fwd_off.back());
+      G.fwd_smem.push_back(sm);
     }
     for (size_t k = 0; k < max_r; ++k) {
-      G.rev_off.push_back((int)rev.size());
+      G.rev_off.push_back(G.micro ? (int)rev2.size() : (int)rev.size());
+      uint32_t sm = 0;
       for (int i = 0; i < cnt; ++i) {
         const CircuitPlan& P = b->large[G.members[i]].c->plan;
-        if (k < P.rev.passes.size()) rev.push_back(targs(P, P.rev, (int)k, i));
+        if (k >= P.rev.passes.size()) continue;
+        if (G.micro) {
+          T2Args a;
+          QS_TRY(t2args(P, P.rev, (int)k, i, &a));
+          rev2.push_back(a);
+          sm = std::max(sm, P.rev.passes[k].t2hdr.smem);
+        } else {
+          rev.push_back(targs(P, P.rev, (int)k, i));
+        }
       }
-      G.rev_cnt.push_back((int)rev.size() - G.rev_off.back());
+      G.rev_cnt.push_back((G.micro ? (int)rev2.size() : (int)rev.size()) - G.rev_off.back());
+      G.rev_smem.push_back(sm);
     }
+    QS_TRY(upload(&G.d_fwd2, fwd2));
+    QS_TRY(upload(&G.d_rev2, rev2));
     for (int i = 0; i < cnt; ++i) {
       const BLarge& L = b->large[G.members[i]];
       const CircuitPlan& P = L.c->plan;
@@ -519,6 +564,9 @@ qs_status qs_batch_create(int n_inst, const int* n_qubits, const int* gate_offse
         s = qs_circuit_add(B.c, g.kind, g.targets, g.n_targets, ctrls, nc, g.param, g.coef, g.constant, nullptr);
       }
       if (s == QS_OK) B.c->n_params = std::max(B.c->n_params, param_offsets[i + 1] - param_offsets[i]);
+      // default plans: below 22 qubits the interpreter passes (micro-op passes
+      // in lock-step groups measured slower there: 2048-instance batch 4970 ->
+      // 4235 instances/s), micro-op passes from 22 qubits
       if (s == QS_OK) s = qs_circuit_finalize(B.c, dtype, nullptr);
       if (s == QS_OK) {
         const int t0 = term_offsets[i], nt = term_offsets[i + 1] - t0;

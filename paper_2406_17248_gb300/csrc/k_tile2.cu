@@ -26,20 +26,6 @@ namespace {
 
 constexpr int kT2NB = 3;  // tile buffers
 
-struct T2Args {
-  CUtensorMap tm[2];  // psi, lam (8-byte words)
-  const T2Pass* pass;
-  const T2Phase* phases;
-  const T2Op* ops;
-  const float2* coef;
-  float2* psi;
-  float2* lam;
-  double* partials;
-  int stride;       // partials columns of one slot
-  int cols;         // columns this launch fills (>= gridDim.x; the rest are zeros)
-  int n;
-  float plus_amp;
-};
 
 __device__ __forceinline__ float2 lds64(uint32_t a) {
   float2 v;
@@ -403,7 +389,7 @@ __device__ __forceinline__ bool t2_is_grad(uint16_t code) {
 }
 
 template <int NS>
-__global__ void __launch_bounds__(NS == 2 ? 288 : 544, 1) tile2_kernel(const __grid_constant__ T2Args args) {
+__device__ __forceinline__ void tile2_body(const T2Args& args, const CUtensorMap* tmap) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t s_full[kT2NB], s_done[kT2NB];
   __shared__ int s_bad;
@@ -499,8 +485,8 @@ __global__ void __launch_bounds__(NS == 2 ? 288 : 544, 1) tile2_kernel(const __g
       for (uint32_t j = lane; j < nb; j += 32) {
         int x[5];
         tile_coords(P.ma, P.mw, toff + l2g(j << P.mlb), x);
-        tma_load5(tsh(b) + j * bb, &args.tm[0], x, fb);
-        if (NS == 2) tma_load5(tsh(b) + tile_bytes + j * bb, &args.tm[1], x, fb);
+        tma_load5(tsh(b) + j * bb, &tmap[0], x, fb);
+        if (NS == 2) tma_load5(tsh(b) + tile_bytes + j * bb, &tmap[1], x, fb);
       }
     };
     auto store = [&](uint64_t t, int b) {
@@ -508,8 +494,8 @@ __global__ void __launch_bounds__(NS == 2 ? 288 : 544, 1) tile2_kernel(const __g
       for (uint32_t j = lane; j < nb; j += 32) {
         int x[5];
         tile_coords(P.ma, P.mw, toff + l2g(j << P.mlb), x);
-        if (st_psi) tma_store5(&args.tm[0], x, tsh(b) + j * bb);
-        if (st_lam) tma_store5(&args.tm[1], x, tsh(b) + tile_bytes + j * bb);
+        if (st_psi) tma_store5(&tmap[0], x, tsh(b) + j * bb);
+        if (st_lam) tma_store5(&tmap[1], x, tsh(b) + tile_bytes + j * bb);
       }
       bulk_commit();
       bulk_wait_read0();  // the buffer may be refilled once the stores have read it
@@ -630,6 +616,27 @@ __global__ void __launch_bounds__(NS == 2 ? 288 : 544, 1) tile2_kernel(const __g
   }
 }
 
+template <int NS>
+__global__ void __launch_bounds__(NS == 2 ? 288 : 544, 1) tile2_kernel(const __grid_constant__ T2Args args) {
+  tile2_body<NS>(args, args.tm);
+}
+
+// The same pass of many instances in one launch: instance blockIdx.y, its
+// arguments from a table in global memory (copied to shared memory, except
+// the tensor maps, which the TMA unit reads where they are).
+template <int NS>
+__global__ void __launch_bounds__(NS == 2 ? 288 : 544, 1) tile2_multi_kernel(const T2Args* __restrict__ argv) {
+  __shared__ T2Args s_args;
+  const T2Args* g = argv + blockIdx.y;
+  {
+    const int* src = reinterpret_cast<const int*>(g);
+    int* dst = reinterpret_cast<int*>(&s_args);
+    for (int i = threadIdx.x; i < (int)(sizeof(T2Args) / 4); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  tile2_body<NS>(s_args, g->tm);
+}
+
 int sm_count2() {
   static int n = 0;
   if (!n) {
@@ -643,12 +650,11 @@ int sm_count2() {
 
 }  // namespace
 
-// One pass in its micro-op form (complex64).  grid: the launch's partial columns
-// (the kernel runs one CTA per SM at most and zero-fills the other columns).
-qs_status launch_tile2_pass(const TilePlan& plan, int pi, const TileLaunch& L, cudaStream_t st) {
-  const PlannedPass& pp = plan.passes[pi];
-  const T2Pass& h = pp.t2hdr;
-  T2Args a;
+// Arguments of pass pi of one instance (tensor maps of its psi and lam).
+qs_status make_tile2_args(const TilePlan& plan, int pi, void* psi, void* lam, const void* coef, double* partials,
+                          int stride, int cols, int n, T2Args* out) {
+  const T2Pass& h = plan.passes[pi].t2hdr;
+  T2Args& a = *out;
   TileMapDims d;
   for (int i = 0; i < 5; ++i) {
     d.a[i] = h.ma[i];
@@ -657,24 +663,47 @@ qs_status launch_tile2_pass(const TilePlan& plan, int pi, const TileLaunch& L, c
   }
   d.e = 0;
   d.lb = h.mlb;
-  QS_TRY(encode_tile_map(d, L.psi, true, &a.tm[0]));
-  if (h.ns == 2) QS_TRY(encode_tile_map(d, L.lam, true, &a.tm[1]));
+  QS_TRY(encode_tile_map(d, psi, true, &a.tm[0]));
+  if (h.ns == 2) QS_TRY(encode_tile_map(d, lam, true, &a.tm[1]));
   else a.tm[1] = a.tm[0];
   a.pass = plan.d_t2pass + pi;
   a.phases = plan.d_t2ph + plan.t2_phase_off[pi];
   a.ops = plan.d_t2ops + plan.t2_op_off[pi];
-  a.coef = reinterpret_cast<const float2*>(L.coef);
-  a.psi = reinterpret_cast<float2*>(L.psi);
-  a.lam = reinterpret_cast<float2*>(L.lam);
-  a.partials = L.partials;
-  a.stride = L.stride;
-  a.n = L.n;
-  a.plus_amp = (float)std::pow(2.0, -0.5 * L.n);
+  a.coef = reinterpret_cast<const float2*>(coef);
+  a.psi = reinterpret_cast<float2*>(psi);
+  a.lam = reinterpret_cast<float2*>(lam);
+  a.partials = partials;
+  a.stride = stride;
+  a.cols = cols;
+  a.n = n;
+  a.plus_amp = (float)std::pow(2.0, -0.5 * n);
+  return QS_OK;
+}
+
+qs_status launch_tile2_multi(int ns, const T2Args* d_argv, int count, int grid_x, uint32_t smem, cudaStream_t st) {
+  if (count <= 0) return QS_OK;
+  const void* fn = ns == 2 ? (const void*)tile2_multi_kernel<2> : (const void*)tile2_multi_kernel<1>;
+  QS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const dim3 g((unsigned)std::max(grid_x, 1), (unsigned)count);
+  if (ns == 2)
+    tile2_multi_kernel<2><<<g, 256 + 32, smem, st>>>(d_argv);
+  else
+    tile2_multi_kernel<1><<<g, 512 + 32, smem, st>>>(d_argv);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+// One pass in its micro-op form (complex64).  grid: the launch's partial columns
+// (the kernel runs one CTA per SM at most and zero-fills the other columns).
+qs_status launch_tile2_pass(const TilePlan& plan, int pi, const TileLaunch& L, cudaStream_t st) {
+  const PlannedPass& pp = plan.passes[pi];
+  const T2Pass& h = pp.t2hdr;
   const uint64_t n_tiles = 1ull << (L.n - h.m);
   uint64_t g = std::min<uint64_t>((uint64_t)sm_count2(), n_tiles);
   g = std::min<uint64_t>(g, (uint64_t)std::max(L.grid, 1));
   const int grid = (int)std::max<uint64_t>(g, 1);
-  a.cols = std::max(L.grid, grid);
+  T2Args a;
+  QS_TRY(make_tile2_args(plan, pi, L.psi, L.lam, L.coef, L.partials, L.stride, std::max(L.grid, grid), L.n, &a));
   const int T = std::min(1 << (h.m - kRegBits), h.ns == 2 ? 256 : 512);
   const void* fn = h.ns == 2 ? (const void*)tile2_kernel<2> : (const void*)tile2_kernel<1>;
   static size_t set_smem[2] = {0, 0};

@@ -1,6 +1,7 @@
 // Internal types shared by the host runtime (api.cu, plan.cu) and the kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -232,6 +233,27 @@ struct TileKArgs {
 qs_status launch_tile_pass_multi(qs_dtype dt, int ns, int m, const TileKArgs* d_argv, int count, int grid,
                                  cudaStream_t st);
 qs_status launch_tile2_pass(const TilePlan& plan, int pass_index, const TileLaunch& L, cudaStream_t st);
+// Kernel arguments of one instance's micro-op pass (device layout; the tensor
+// maps are read by the TMA unit from wherever the arguments live).
+struct T2Args {
+  CUtensorMap tm[2];  // psi, lam (8-byte words)
+  const T2Pass* pass;
+  const T2Phase* phases;
+  const T2Op* ops;
+  const float2* coef;
+  float2* psi;
+  float2* lam;
+  double* partials;
+  int stride;  // partials columns of one slot
+  int cols;    // columns this launch fills (>= gridDim.x; the rest are zeros)
+  int n;
+  float plus_amp;
+};
+qs_status make_tile2_args(const TilePlan& plan, int pass_index, void* psi, void* lam, const void* coef,
+                          double* partials, int stride, int cols, int n, T2Args* out);
+// Pass arguments of `count` instances (d_argv, 64-byte aligned), grid_x CTAs per
+// instance, each looping over its share of the instance's tiles.
+qs_status launch_tile2_multi(int ns, const T2Args* d_argv, int count, int grid_x, uint32_t smem, cudaStream_t st);
 qs_status launch_tile_pass(qs_dtype dt, const TilePlan& plan, int pass_index, const TileLaunch& L,
                            cudaStream_t st);
 int tile_grid_size(qs_dtype dt, int m, int ns, int n_tiles);

@@ -547,8 +547,8 @@ QS_API qs_status qs_adam_f64(int n, double* dev_w, double* dev_m, double* dev_v,
  * The call allocates no device memory: its working memory is a fixed 256 KiB
  * array inside the library, held by every device that loads the library until
  * the process exits.  The first call on a device (with that device current)
- * looks up the array's device address; make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents;
+ * looks up the array's device address.  All calls share the array and it keeps
+ * the last call's contents;
  * calls that overlap on the GPU (other host threads, other streams) race on it,
  * so serialise them.  The call synchronises `cuda_stream` before returning. */
 QS_API qs_status qs_expectation_noalloc(const void* dev_psi, int n_qubits, qs_dtype dtype, int n_terms,

@@ -15,7 +15,8 @@
 // it and stores it in the no-swizzle K-major core-matrix layout; one thread
 // issues the MMAs and commits them to an mbarrier; each warp reads its 32 TMEM
 // lanes back (tcgen05.ld 32x32b, the columns of its half) and stores those
-// outputs in place.  Every other
+// outputs in place (k = 4; k = 5 runs the warp-specialised form below, whose
+// roles overlap the chain of consecutive tiles).  Every other
 // case (complex128, other k, small n) runs on the CUDA cores in the state's
 // own precision.
 #include <cuda_runtime.h>
@@ -296,6 +297,211 @@ __global__ void __launch_bounds__(kTcThreads) dense_tc_kernel(float2* __restrict
   (void)lane;
 }
 
+// ------------------------------------------------------------------ warp-specialised tensor-core kernel
+//
+// The same contraction with the per-tile chain split over roles, so that
+// gathering, tensor-core work and write-back of consecutive tiles overlap in
+// one CTA: 16 producer warps (four threads per row) gather a tile's
+// rows into one of two operand stages and split them; one MMA warp issues the
+// three products per K-step into one of two TMEM accumulators and commits them
+// to the stage's "empty" and the accumulator's "full" mbarriers; 4 epilogue
+// warps (warp w: TMEM lanes 32 w..) read the accumulator back, store the rows
+// and release it.  Every wait is bounded; a wait that runs out records an
+// error and ends the role's loop.
+constexpr int kWsProducers = 512, kWsThreads = kWsProducers + 32 + 128;  // producers: 4 threads per row
+
+template <int K>
+struct WsCfg {
+  static constexpr int KB = 1 << K, KR = 2 * KB;
+  static constexpr int A_BYTES = kTcRows * KR * 4, B_BYTES = KR * KR * 4;
+  static constexpr int TMEM_COLS = 2 * KR < 32 ? 32 : 2 * KR;
+  static constexpr size_t SMEM = 4 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + 16 * 8 + 128;
+};
+
+__device__ __forceinline__ bool ws_wait(uint32_t mbar, uint32_t parity) {
+  for (long long it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(mbar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void ws_arrive(uint32_t mbar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
+}
+
+template <int K>
+__global__ void __launch_bounds__(kWsThreads, 1) dense_ws_kernel(float2* __restrict__ psi, const DenseGeom G,
+                                                                 const double2* __restrict__ U, uint64_t n_tiles,
+                                                                 int* __restrict__ err) {
+  using Cfg = WsCfg<K>;
+  constexpr int KB = Cfg::KB, KR = Cfg::KR, KQ = KB / 4;  // amplitudes per producer thread
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  // stage st: head at smem + 2 st A_BYTES, tail right after it (arithmetic, not
+  // an indexed array, which would live in local memory)
+  auto a_hi = [&](int st) { return smem + (size_t)(2 * st) * Cfg::A_BYTES; };
+  auto a_lo = [&](int st) { return smem + (size_t)(2 * st + 1) * Cfg::A_BYTES; };
+  unsigned char* b_hi = smem + 4 * Cfg::A_BYTES;
+  unsigned char* b_lo = b_hi + Cfg::B_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(b_lo + Cfg::B_BYTES);
+  // full[s], empty[s], tfull[a], tempty[a]
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + 2), tfull0 = smem_u32(bars + 4),
+                 tempty0 = smem_u32(bars + 6);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 8);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  for (int e = tid; e < KR * KR; e += kWsThreads) {  // B = real form of U^T, split h/t (as above)
+    const int n = e / KR, kk = e % KR;
+    const int i = n >> 1, cp = n & 1, j = kk >> 1, c = kk & 1;
+    const double2 u = U[i * KB + j];
+    const float w = (float)(cp == 0 ? (c == 0 ? u.x : -u.y) : (c == 0 ? u.y : u.x));
+    const float h = tf32_round(w);
+    const uint32_t off = op_offset(n, kk, KR);
+    *reinterpret_cast<float*>(b_hi + off) = h;
+    *reinterpret_cast<float*>(b_lo + off) = tf32_round(w - h);
+  }
+  if (tid == 0) {
+    for (int q = 0; q < 2; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8 * q), "r"(kWsProducers / 32) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8 * q) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tfull0 + 8 * q) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(tempty0 + 8 * q) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                 "r"((uint32_t)Cfg::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  bool bad = false;
+
+  if (tid < kWsProducers) {
+    // ------------------------------------------------------------ producers
+    // thread: row tid % 128, quarter tid / 128 of its amplitudes; the next
+    // tile's amplitudes are loaded before this tile's are split and stored, so
+    // two tiles' gathers are in flight per thread
+    const int row = tid & (kTcRows - 1), qt = tid / kTcRows;
+    float2 xn[KQ];
+    uint64_t tile = blockIdx.x;
+    if (tile < n_tiles) {
+      const uint64_t base = deposit_other(G, tile * kTcRows + row);
+#pragma unroll
+      for (int j = 0; j < KQ; ++j) xn[j] = psi[base | G.tgt_off[qt * KQ + j]];
+    }
+    int i = 0;
+    for (; tile < n_tiles; tile += gridDim.x, ++i) {
+      const int st = i & 1;
+      float2 x[KQ];
+#pragma unroll
+      for (int j = 0; j < KQ; ++j) x[j] = xn[j];
+      const uint64_t next = tile + gridDim.x;
+      if (next < n_tiles) {
+        const uint64_t nb = deposit_other(G, next * kTcRows + row);
+#pragma unroll
+        for (int j = 0; j < KQ; ++j) xn[j] = psi[nb | G.tgt_off[qt * KQ + j]];
+      }
+      if (i >= 2 && !ws_wait(empty0 + 8 * st, (uint32_t)(((i - 2) >> 1) & 1))) {
+        bad = true;
+        break;
+      }
+#pragma unroll
+      for (int c = 0; c < KQ / 2; ++c) {
+        const float2 p0 = x[2 * c], p1 = x[2 * c + 1];
+        float4 h, t;
+        h.x = tf32_round(p0.x);
+        h.y = tf32_round(p0.y);
+        h.z = tf32_round(p1.x);
+        h.w = tf32_round(p1.y);
+        t.x = tf32_round(p0.x - h.x);
+        t.y = tf32_round(p0.y - h.y);
+        t.z = tf32_round(p1.x - h.z);
+        t.w = tf32_round(p1.y - h.w);
+        const uint32_t off = op_offset(row, qt * (KB / 2) + 4 * c, KR);
+        *reinterpret_cast<float4*>(a_hi(st) + off) = h;
+        *reinterpret_cast<float4*>(a_lo(st) + off) = t;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+      __syncwarp();
+      if (lane == 0) ws_arrive(full0 + 8 * st);
+    }
+  } else if (tid < kWsProducers + 32) {
+    // ------------------------------------------------------------ MMA warp
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32(kTcRows, KR);
+      const uint32_t lbo = 128, sbo = KR * 32;
+      const uint32_t bh_s = smem_u32(b_hi), bl_s = smem_u32(b_lo);
+      int i = 0;
+      for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
+        const int st = i & 1, ac = i & 1;
+        if (!ws_wait(full0 + 8 * st, (uint32_t)((i >> 1) & 1))) {
+          bad = true;
+          break;
+        }
+        if (i >= 2 && !ws_wait(tempty0 + 8 * ac, (uint32_t)(((i - 2) >> 1) & 1))) {
+          bad = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t ah_s = smem_u32(a_hi(st)), al_s = smem_u32(a_lo(st));
+        const uint32_t d = tmem + (uint32_t)(ac * KR);
+#pragma unroll
+        for (int s = 0; s < KR / 8; ++s) {
+          const uint32_t ko = s * 256;
+          const uint64_t ah = smem_desc(ah_s + ko, lbo, sbo), al = smem_desc(al_s + ko, lbo, sbo);
+          const uint64_t bh = smem_desc(bh_s + ko, lbo, sbo), bl = smem_desc(bl_s + ko, lbo, sbo);
+          mma_tf32(d, ah, bh, idesc, s > 0);
+          mma_tf32(d, ah, bl, idesc, 1);
+          mma_tf32(d, al, bh, idesc, 1);
+        }
+        mma_commit(empty0 + 8 * st);  // the stage may be refilled once these MMAs have read it
+        mma_commit(tfull0 + 8 * ac);  // the accumulator holds the tile
+      }
+      // the last commits before the tensor memory is freed (bounded)
+      if (i >= 1) (void)ws_wait(tfull0 + 8 * ((i - 1) & 1), (uint32_t)(((i - 1) >> 1) & 1));
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue warps
+    // a warp may access only the TMEM lanes of its quarter, 32 (warp % 4) ..; the
+    // four epilogue warps (9..12) cover the quarters 1, 2, 3, 0
+    const int ew = warp & 3;
+    const int row = ew * 32 + lane;
+    int i = 0;
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
+      const int ac = i & 1;
+      if (!ws_wait(tfull0 + 8 * ac, (uint32_t)((i >> 1) & 1))) {
+        bad = true;
+        break;
+      }
+      tc_fence_after();
+      const uint64_t base = deposit_other(G, tile * kTcRows + row);
+      const uint32_t trow = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(ac * KR);
+#pragma unroll
+      for (int c0 = 0; c0 < KR; c0 += 16) {
+        float v[16];
+        tmem_ld16(trow + c0, v);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) psi[base | G.tgt_off[c0 / 2 + q]] = make_float2(v[2 * q], v[2 * q + 1]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ws_arrive(tempty0 + 8 * ac);
+    }
+  }
+  if (bad) atomicExch(err, 1);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)Cfg::TMEM_COLS)
+                 : "memory");
+}
+
 // ------------------------------------------------------------------ CUDA-core kernel
 
 template <class T>
@@ -356,6 +562,20 @@ int cc_threads(qs_dtype dt, int k) {
   int t = 128;
   while (t > 32 && (KB * KB + (size_t)t * KB) * amp > 160 * 1024) t >>= 1;
   return t;
+}
+
+template <int K>
+qs_status launch_ws(float2* psi, const DenseGeom& G, const double2* dU, int* d_err, cudaStream_t st) {
+  using Cfg = WsCfg<K>;
+  const uint64_t n_tiles = (1ull << (G.n - K)) / kTcRows;
+  int dev = 0, sms = 1;
+  QS_CUDA(cudaGetDevice(&dev));
+  QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  QS_CUDA(cudaFuncSetAttribute(dense_ws_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+  const uint64_t grid = std::min<uint64_t>(n_tiles, (uint64_t)sms);  // one CTA per SM, looping over tiles
+  dense_ws_kernel<K><<<(unsigned)grid, kWsThreads, Cfg::SMEM, st>>>(psi, G, dU, n_tiles, d_err);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
 }
 
 template <int K>
@@ -449,8 +669,11 @@ qs_status qs_apply_matrix(qs_state* s, int k, const int* targets, const double* 
   if (use_tc) {
     QS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s->st));
     TraceRec* rec = trace_begin(s->st);
+    // k = 5: the warp-specialised kernel (28 qubits, spread targets 0.874 vs
+    // 0.933 ms; targets 0-4 2.31 vs 2.91 ms); k = 4: the serial one (0.92 vs
+    // 1.18 ms: a 32-column tile leaves the pipeline's hand-offs uncovered)
     qs_status r = k == 4 ? launch_tc<4>(static_cast<float2*>(s->ptr), G, dU, d_err, s->st)
-                         : launch_tc<5>(static_cast<float2*>(s->ptr), G, dU, d_err, s->st);
+                         : launch_ws<5>(static_cast<float2*>(s->ptr), G, dU, d_err, s->st);
     if (r != QS_OK) return r;
     if (rec) {
       rec->bytes = 2.0 * 8.0 * (double)(1ull << s->ne);

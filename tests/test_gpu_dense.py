@@ -61,6 +61,17 @@ def test_tensor_core_blocks(Q, k, layout):
     assert err <= 2e-6  # float32-level: the head/tail split keeps ~21 bits per product
 
 
+@pytest.mark.parametrize("k", [4, 5])
+def test_tensor_core_blocks_many_tiles_per_cta(Q, k):
+    """21 qubits: 512 (k = 5) / 1024 (k = 4) tiles of 128 rows over one CTA per
+    SM, so every CTA runs several tiles through its two operand stages and two
+    tensor-memory accumulators (the pipeline's parity bookkeeping)."""
+    n = 21
+    targets = [1, 6, 11, 16, 20][:k]
+    err = _run(Q, n, Q.C64, targets, _unitary(k, 17 + k), 2, 9)
+    assert err <= 2e-6
+
+
 def test_tensor_core_identity_and_permutation(Q):
     n, k = 13, 5
     psi0 = I.random_state(n, 9).astype(np.complex64)

@@ -372,14 +372,14 @@ QS_API qs_status qs_qaoa_expectation_with_grad(qs_qaoa* q, qs_state* psi, qs_sta
  * (cos b/2, -sin b/2)), [7..9] output slot of accumulators 0..2 (-1 none),
  * [10] tile bits, [11] low bits, then per phase 7 entries: step-1 register
  * mask, step-3 register mask, diagonal (0 none, 1 cost, 2 cost gradient and
- * cost^dag, 3 energy), the qubits of register bits 0..3 (8 phase slots), then
- * at [68] and [85] the tile's load and store tensor maps, 17 entries each:
+ * cost^dag, 3 energy), the qubits of register bits 0..3 (-1: none; 12 phase
+ * slots), then at [96] and [113] the tile's load and store tensor maps, 17 entries each:
  * log2 of 8-byte words per amplitude, local bits covered by one box, and per
  * dimension 0..4 its first word-index bit, its width in bits and the box width
- * in bits, then at [102] the offset of the pass's phase weights in the
+ * in bits, then at [130] the offset of the pass's phase weights in the
  * per-call coefficient table.  slot_out/slot_w: output (0 = E, 1 + l =
  * dgamma_l, 1 + p + l = dbeta_l) and weight per slot. */
-#define QS_XPLAN_REC 103
+#define QS_XPLAN_REC 131
 QS_API qs_status qs_qaoa_xplan(int n_qubits, const int* edges, int n_edges, int p, double gamma_scale, int tile_bits,
                                int low_bits, int which, long long* rec, int max_passes, int* n_passes,
                                int* slot_out, double* slot_w, int max_slots, int* n_slots);
@@ -392,7 +392,7 @@ QS_API qs_status qs_qaoa_xplan(int n_qubits, const int* edges, int n_edges, int 
  * the scaled mixer of RX(beta_l) and of RX(-beta_l): [[1, -it], [-it, 1]]
  * with t = s/c when |c| >= |s| (c, s = cos, sin of the half angle), else
  * t = -c/s with every qubit the step rotates flipped in the data.  Then each
- * pass's phase weights (record [102]): per phase (w1, w3), (wd, 0), the factors
+ * pass's phase weights (record [130]): per phase (w1, w3), (wd, 0), the factors
  * of the step-1, step-3 and diagonal sums.  *flip = 1: the energy plan leaves
  * every qubit flipped (the engine flips the state back). */
 QS_API qs_status qs_qaoa_xcoef(int n_qubits, const int* edges, int n_edges, int p, double gamma_scale, int tile_bits,

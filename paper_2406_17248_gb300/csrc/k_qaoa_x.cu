@@ -23,6 +23,7 @@
 // two tiles ahead), so no cut-value array is read.
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <type_traits>
 
 #include "qaoa_pass.h"
@@ -292,16 +293,16 @@ __device__ __forceinline__ bool xdispatch1(int code, const XPh& h, float (&acc)[
 }
 
 __device__ __forceinline__ bool xdispatch2(int code, const XPh& h, float (&acc)[3]) {
+  // bodies for 3 register bits (the planner emits these step shapes only)
+  static_assert(qx_reg_bits(true) == 3, "two-state phase table is written for 3 register bits");
   switch (code) {
 #define C2(K1, DG, K3) \
   case xcode(K1, DG, K3): xphase2<K1, DG, K3>(h, acc); return true;
-    C2(1, 0, 0) C2(2, 0, 0) C2(3, 0, 0) C2(4, 0, 0)
-    C2(0, 0, 1) C2(0, 0, 2) C2(0, 0, 3) C2(0, 0, 4)
-    C2(0, XD_COST_GRAD, 4) C2(1, XD_COST_GRAD, 4) C2(2, XD_COST_GRAD, 4) C2(3, XD_COST_GRAD, 4)
-    C2(4, XD_COST_GRAD, 4)
+    C2(1, 0, 0) C2(2, 0, 0) C2(3, 0, 0)
+    C2(0, 0, 1) C2(0, 0, 2) C2(0, 0, 3)
+    C2(0, XD_COST_GRAD, 3) C2(1, XD_COST_GRAD, 3) C2(2, XD_COST_GRAD, 3) C2(3, XD_COST_GRAD, 3)
     C2(0, XD_COST_GRAD, 0) C2(1, XD_COST_GRAD, 0) C2(2, XD_COST_GRAD, 0) C2(3, XD_COST_GRAD, 0)
-    C2(4, XD_COST_GRAD, 0)
-    C2(0, XD_ENERGY, 4) C2(1, XD_ENERGY, 4) C2(2, XD_ENERGY, 4) C2(3, XD_ENERGY, 4) C2(4, XD_ENERGY, 4)
+    C2(0, XD_ENERGY, 3) C2(1, XD_ENERGY, 3) C2(2, XD_ENERGY, 3) C2(3, XD_ENERGY, 3)
 #undef C2
     default: return false;
   }
@@ -315,7 +316,7 @@ __device__ __forceinline__ bool xdispatch2(int code, const XPh& h, float (&acc)[
 // never stall on HBM back-pressure; mbarriers hand buffers over: full[b] when a
 // tile's copies have landed, done[b] when the compute warps have finished it.
 template <bool TWO>
-__global__ void __launch_bounds__(TWO ? 288 : 544, 1) qx_kernel(const __grid_constant__ XArgs args) {
+__global__ void __launch_bounds__(544, 1) qx_kernel(const __grid_constant__ XArgs args) {
   constexpr uint32_t ES = TWO ? 16 : 8;  // bytes per shared-memory element
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ XPass P;
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(TWO ? 288 : 544, 1) qx_kernel(const __grid_con
   uint8_t* s_fs = smem + off;
   off += ((size_t)tile_n + 127) & ~(size_t)127;
   uint32_t* s_pl = reinterpret_cast<uint32_t*>(smem + off);
-  off += (size_t)kXMaxPhases * T * 4;
+  off += (size_t)n_ph * T * 4;
   // tiled tensor copies need 128-byte aligned shared addresses; the dynamic
   // shared block follows the static variables and is only 16-byte aligned
   const uint32_t tile0 = (xsh(smem) + (uint32_t)off + 127u) & ~127u;
@@ -497,12 +498,13 @@ __global__ void __launch_bounds__(TWO ? 288 : 544, 1) qx_kernel(const __grid_con
       const uint32_t tb = tsh(cur);
       if (ld_psi8) {  // turnaround: the tile came in as 8-byte psi amplitudes; expand them in place to
                       // (psi.re, 0, psi.im, 0) elements (all threads read, then all write)
-        float2 v[16];
+        constexpr int EPT = 1 << qx_reg_bits(TWO);  // elements per compute thread
+        float2 v[EPT];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] = lds64(tb + 8u * ((uint32_t)tid + (uint32_t)T * k));
+        for (int k = 0; k < EPT; ++k) v[k] = lds64(tb + 8u * ((uint32_t)tid + (uint32_t)T * k));
         bar_compute(T);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) sts128(tb + 16u * ((uint32_t)tid + (uint32_t)T * k), v[k].x, 0.f, v[k].y, 0.f);
+        for (int k = 0; k < EPT; ++k) sts128(tb + 16u * ((uint32_t)tid + (uint32_t)T * k), v[k].x, 0.f, v[k].y, 0.f);
         bar_compute(T);
       }
       const int* lin = s_lin[cur];
@@ -580,12 +582,12 @@ __global__ void __launch_bounds__(TWO ? 288 : 544, 1) qx_kernel(const __grid_con
 #undef XCUT
 
 // Dynamic shared memory: LUT, edge counts and phase bases, then the tile buffers.
-size_t qx_smem(int two_state, int m, int n_edges) {
+size_t qx_smem(int two_state, int m, int n_edges, int n_phases) {
   const size_t T = (size_t)1 << (m - qx_reg_bits(two_state));
   const size_t tile = ((size_t)1 << m) * (two_state ? 16 : 8);
   size_t off = ((size_t)(n_edges + 1) * 8 + 127) & ~(size_t)127;
   off += (((size_t)1 << m) + 127) & ~(size_t)127;
-  off += ((size_t)kXMaxPhases * T * 4 + 127) & ~(size_t)127;
+  off += ((size_t)n_phases * T * 4 + 127) & ~(size_t)127;
   return off + 128 + (size_t)kXNB * tile;
 }
 
@@ -614,23 +616,27 @@ qs_status launch_qx_flip(float2* psi, int n, cudaStream_t st) {
   return QS_OK;
 }
 
-int qx_occupancy(int two_state, int m, int n_edges, int /*n_phases*/) {
-  static int last_key[2] = {-1, -1}, last_occ[2] = {0, 0};
+int qx_occupancy(int two_state, int m, int n_edges, int n_phases) {
+  static std::map<long long, int> cache[2];  // a few (m, edges, phases) shapes per engine
   if (m < 5 + qx_reg_bits(two_state) || m > (two_state ? 12 : kXMaxM)) return 0;
-  const size_t smem = qx_smem(two_state, m, n_edges);
-  const int key = m * 1024 + n_edges;
-  if (last_key[two_state] == key) return last_occ[two_state];
+  const size_t smem = qx_smem(two_state, m, n_edges, n_phases);
+  const long long key = ((long long)m * 1024 + n_edges) * 64 + n_phases;
+  auto it = cache[two_state].find(key);
+  if (it != cache[two_state].end()) return it->second;
   const void* fn = two_state ? (const void*)qx_kernel<true> : (const void*)qx_kernel<false>;
   int blocks = 0;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+  static size_t set_smem[2] = {0, 0};  // the attribute only grows
+  if ((smem > set_smem[two_state] &&
+       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, (1 << (m - qx_reg_bits(two_state))) + 32, smem) !=
           cudaSuccess ||
       blocks < 1) {
     (void)cudaGetLastError();
     blocks = 0;
+  } else if (smem > set_smem[two_state]) {
+    set_smem[two_state] = smem;
   }
-  last_key[two_state] = key;
-  last_occ[two_state] = blocks;
+  cache[two_state][key] = blocks;
   return blocks;
 }
 
@@ -685,7 +691,7 @@ qs_status launch_qx_pass(int two_state, const XPass* d_pass, const XPass& h, con
   a.stride = L.stride;
   a.n = L.n;
   a.n_edges = L.n_edges;
-  const size_t smem = qx_smem(two_state, h.m, L.n_edges);
+  const size_t smem = qx_smem(two_state, h.m, L.n_edges, h.n_phases);
   const int threads = (1 << (h.m - qx_reg_bits(two_state))) + 32;  // compute threads + the producer warp
   if (two_state)
     qx_kernel<true><<<L.grid, threads, smem, st>>>(a);

@@ -430,8 +430,11 @@ qs_status build_x_engine(qs_qaoa* q, const std::vector<std::pair<int, int>>& es,
   q->xe_two = X.energy_two;
   q->gslots = X.gslots;
   q->eslots = X.eslots;
-  q->xgrid_f = qx_grid(0, B.mf, q->n_edges, 0, 1ull << (n - B.mf));
-  q->xgrid_r = qx_grid(1, mr, q->n_edges, 0, 1ull << (n - mr));
+  int ph_f = 1, ph_r = 1;  // the most phases of a pass of each kernel (shared-memory sizing)
+  for (size_t i = 0; i < X.grad.size(); ++i) (X.grad_two[i] ? ph_r : ph_f) = std::max(X.grad_two[i] ? ph_r : ph_f, X.grad[i].n_phases);
+  for (size_t i = 0; i < X.energy.size(); ++i) ph_f = std::max(ph_f, X.energy[i].n_phases);
+  q->xgrid_f = qx_grid(0, B.mf, q->n_edges, ph_f, 1ull << (n - B.mf));
+  q->xgrid_r = qx_grid(1, mr, q->n_edges, ph_r, 1ull << (n - mr));
   if (q->xgrid_f < 1 || q->xgrid_r < 1) {
     set_error("qaoa: the two-shape tiles do not fit in shared memory");
     return QS_ERR_UNSUPPORTED;

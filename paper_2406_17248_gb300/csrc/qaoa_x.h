@@ -29,7 +29,7 @@
 
 namespace qs {
 
-constexpr int kXMaxPhases = 8;
+constexpr int kXMaxPhases = 12;
 constexpr int kXMaxM = 13;
 constexpr int kXMaxComp = 40;
 
@@ -98,8 +98,10 @@ struct XLaunch {
   int stride, grid, n, n_edges;
 };
 
-// Register bits per phase: 4 (16 amplitudes per thread) in both kernels.
-constexpr int qx_reg_bits(bool /*two_state*/) { return 4; }
+// Register bits per phase: 4 (16 amplitudes per thread) for psi alone, 3 (8
+// psi/lam pairs) in the two-state kernel, whose 2^(m-3) compute threads then
+// fit in 96 registers: twice the warps of 4 register bits at 168.
+constexpr int qx_reg_bits(bool two_state) { return two_state ? 3 : 4; }
 
 // two_state = 0: forward kernel (psi alone, 8-byte elements); 1: psi and lam
 // interleaved (16-byte elements).  Returns the resident CTAs per SM (0: does

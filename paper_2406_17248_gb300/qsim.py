@@ -630,7 +630,7 @@ def apply_matrix(state: State, targets, matrix, engine: int = 0) -> State:
     return state
 
 
-XPLAN_REC = 103
+XPLAN_REC = 131
 
 
 def qaoa_xplan(n: int, edges, p: int, gamma_scale: float = 1.0, tile_bits: int = 0, low_bits: int = 0,
@@ -653,10 +653,10 @@ def qaoa_xplan(n: int, edges, p: int, gamma_scale: float = 1.0, tile_bits: int =
         for ph in range(r[3]):
             q = r[12 + 7 * ph:12 + 7 * ph + 7]
             d["phases"].append(dict(m1=q[0], m3=q[1], diag=q[2], reg=list(q[3:7])))
-        d["cw"] = r[102]
+        d["cw"] = r[130]
         d["maps"] = []
         for k in range(2):
-            t = r[68 + 17 * k:68 + 17 * k + 17]
+            t = r[96 + 17 * k:96 + 17 * k + 17]
             d["maps"].append(dict(e=t[0], lb=t[1], a=list(t[2:7]), w=list(t[7:12]), box=list(t[12:17])))
         out.append(d)
     return out, [(so[i], sw[i]) for i in range(nslot.value)]

@@ -66,7 +66,7 @@ def replay(plan, slots, n, edges, gamma, beta, gs, p):
         c1 = tab[P["c1"]] if P["c1"] >= 0 else 1.0
         c3 = tab[P["c3"]] if P["c3"] >= 0 else 1.0
         seen1, seen3 = set(), set()
-        R = 4  # register bits per phase
+        R = 3 if two else 4  # register bits per phase (psi/lam kernel: 3)
         for ph in P["phases"]:
             reg = ph["reg"][:R]
             assert len(set(reg)) == R and all(q >= 0 for q in reg) and all(q == -1 for q in ph["reg"][R:])

@@ -761,7 +761,7 @@ def run_dense_workload(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (tf32 head/tail split)", "data": "synthetic",
             "config": {"workload": f"{n}-qubit complex64 state, seeded random {k}-qubit unitary on qubits {targets}",
                        "l2": "state 2 GiB > L2, no flush needed"},
-            "roofline": {"bound": "hbm", "kernel": "dense_tc_kernel", "achieved": tc["kernel_GBps"], "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": "dense_ws_kernel<5>" if k == 5 else f"dense_tc_kernel<{k}>", "achieved": tc["kernel_GBps"], "peak": peak,
                          "unit": "GB/s", "frac": tc["kernel_GBps"] / peak, "traffic": None,
                          "peak_kind": f"{peak_kind} hbm_gbs", "tensor_tflops": tflops},
             "cuda_core": res["cuda_core"], "tensor": tc,

@@ -353,6 +353,7 @@ def run_ours(args, ws, rank, local):
         line["gate_sweep"] = {k: sw[k] for k in ("n_qubits", "dtype", "GBps", "frac", "gates_per_s", "launches")}
         line["gate_sweep"]["per_kind_frac_median"] = {k: v["frac_median"] for k, v in sw["per_kind"].items()}
         line["random28"] = measure_random_c64(Q)
+        line["random28"]["library_kernels"] = measure_random_c64(Q, fuse=3)
         line["batched_vs_plain"] = measure_batched_vs_plain(Q, args.instances, 3, args.plain_instances)
     print(json.dumps(line), flush=True)
 
@@ -479,14 +480,18 @@ def run_batch_partitioned(Q, args, ws, rank, local):
     dist.destroy_process_group()
 
 
-def measure_random_c64(Q, n=28, G=500, reps=5, warmup=3):
+def measure_random_c64(Q, n=28, G=500, reps=5, warmup=3, fuse=1):
     """The 28-qubit random circuit (500 gates over {H, RX, RY, RZ, CNOT, CZ},
     seed 2) on complex64 fused passes: gates/s and the passes' HBM roofline
-    (algorithmic bytes of the traced passes / their CUDA-event time)."""
+    (algorithmic bytes of the traced passes / their CUDA-event time).  fuse = 1
+    (the default): the passes compiled for the circuit; fuse = 3: the library's
+    precompiled micro-op kernels."""
     import torch
     from paper_2406_17248_gb300 import inputs as I
     circ = I.random_circuit(n, G, seed=2)
-    c = Q.circuit_from(circ).finalize(Q.C64)
+    t_fin = time.perf_counter()
+    c = Q.circuit_from(circ).finalize(Q.C64, fuse=fuse)
+    t_fin = time.perf_counter() - t_fin
     s = Q.State(n, Q.C64)
     for _ in range(warmup):
         s.set_basis(0)
@@ -506,10 +511,12 @@ def measure_random_c64(Q, n=28, G=500, reps=5, warmup=3):
     peak, peak_kind = measured_peak_hbm()
     gbps = float(k_by.sum() / (k_ms.sum() / 1e3) / 1e9) if len(k_ms) else None
     micro = int((k_kind == 10).sum()) // reps
+    gen = int((k_kind == 11).sum()) // reps
     del s
     torch.cuda.empty_cache()
-    return {"n_qubits": n, "gates": G, "dtype": "c64", "gates_per_s": G / (ms / 1e3), "ms": ms,
-            "passes": c.info()["passes"], "micro_op_passes": micro, "GBps": gbps, "peak": peak,
+    return {"n_qubits": n, "gates": G, "dtype": "c64", "fuse": fuse, "gates_per_s": G / (ms / 1e3), "ms": ms,
+            "passes": c.info()["passes"], "micro_op_passes": micro, "generated_passes": gen,
+            "finalize_s": t_fin, "GBps": gbps, "peak": peak,
             "frac": gbps / peak if gbps else None, "peak_source": f"{peak_kind} hbm_gbs",
             "note": "state reset to |0...0> each repetition (set_basis, inside the timed region)"}
 
@@ -529,7 +536,8 @@ def run_random_workload(args):
     H = Q.Hamiltonian(zsum)
     for name, dt in (("c64", Q.C64), ("c128", Q.C128)):
         s = Q.State(n, dt)
-        for mode, fuse in (("fused", 1), ("per_gate", -1)):
+        modes = (("fused", 1), ("library_kernels", 3), ("per_gate", -1)) if name == "c64" else (("fused", 1), ("per_gate", -1))
+        for mode, fuse in modes:
             c = Q.circuit_from(circ).finalize(dt, fuse=fuse)
             s.set_basis(0)
             c.apply(s)

@@ -86,9 +86,14 @@ typedef struct qs_qaoa qs_qaoa;
 /* Execution options for a circuit plan.  Zero means "library default". */
 typedef struct {
   int fuse;       /* 1 (default): fused shared-memory tile passes (complex64 states of 22 or more
-                     qubits run the passes that qualify as pre-decoded micro-ops on TMA-fed tiles,
-                     the rest on the op interpreter); 2: all on the op interpreter; 3: micro-ops
-                     wherever a pass qualifies, whatever the size; -1: one kernel per gate */
+                     qubits run the passes that qualify as micro-ops on TMA-fed tiles, each pass
+                     compiled for the circuit at finalize by the runtime compiler, the rest on the
+                     op interpreter); 2: all on the op interpreter; 3: micro-ops wherever a pass
+                     qualifies, whatever the size, on the library's precompiled kernels (ops
+                     dispatched from a table); 4: as 3, compiled for the circuit (the same
+                     arithmetic as 3, bit for bit); -1: one kernel per gate.  Compiled passes
+                     are cached by their source for the life of the process; finalize returns
+                     QS_ERR_UNSUPPORTED if the runtime compiler fails. */
   int tile_bits;  /* log2 amplitudes per fused tile, 6..13 (default 12 for c64, 11 for c128) */
   int low_bits;   /* low (contiguous) qubits present in every tile, 1..tile_bits (default 4) */
   int checkpoint; /* adjoint state checkpoints, 0 (default): none.  Circuits: every `checkpoint`
@@ -143,6 +148,20 @@ QS_API qs_status qs_circuit_add(qs_circuit* c, int kind, const int* targets, int
  * NULL.  Called implicitly by the first apply if absent. */
 QS_API qs_status qs_circuit_finalize(qs_circuit* c, qs_dtype dtype, const qs_options* opts);
 /* Plan statistics: gates, parameters (max param_idx + 1), forward HBM passes. */
+/* Per-circuit kernels of the complex64 micro-op passes (option fuse = 4), for
+ * inspection and host-side tests; host only, no device work.  Plans the
+ * circuit (which must not have been finalized) for complex64 with `opts`
+ * (NULL or fuse 0: fuse = 4; tile_bits / low_bits as for finalize), writes the
+ * CUDA source of the micro-op passes of the forward (which = 0) or adjoint
+ * (which = 1) plan into src (at most cap - 1 characters and a terminating 0;
+ * src may be NULL when cap = 0), its full length to *src_len and the number of
+ * passes it holds to *n_gen, and with compile != 0 compiles it for sm_103a
+ * with the runtime compiler (*cubin_bytes: the binary's size).  Returns
+ * QS_ERR_UNSUPPORTED when the source cannot be generated or compiled (message:
+ * the compiler's log).  The circuit is left unfinalized; out pointers may be
+ * NULL. */
+QS_API qs_status qs_circuit_codegen(qs_circuit* c, const qs_options* opts, int which, int compile, char* src,
+                                    size_t cap, size_t* src_len, int* n_gen, size_t* cubin_bytes);
 QS_API qs_status qs_circuit_info(const qs_circuit* c, int* n_gates, int* n_params, int* n_passes);
 
 /* psi <- U(params) psi: the circuit applied in order (§2.6.1 apply_circuit).
@@ -578,7 +597,8 @@ typedef enum {
   QS_TRACE_QX_FWD = 7,    /* complex64 two-shape QAOA pass on psi alone (forward sweep) */
   QS_TRACE_QX_TURN = 8,   /* two-shape turnaround: psi in, interleaved (psi, lam) out */
   QS_TRACE_QX_REV = 9,    /* two-shape reverse pass on interleaved (psi, lam) */
-  QS_TRACE_TILE2 = 10     /* complex64 fused tile pass as micro-ops (TMA-fed) */
+  QS_TRACE_TILE2 = 10,    /* complex64 fused tile pass as micro-ops (TMA-fed) */
+  QS_TRACE_TILE2GEN = 11  /* ... its per-circuit kernel (fuse = 4: compiled at finalize) */
 } qs_trace_kind;
 
 /* Tracing of the engine's launches: while enabled, every tile-pass or batch

@@ -29,6 +29,16 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
+def cuda_lib_dir(cc: str) -> str:
+    """The toolkit's library folder (the runtime compiler, libnvrtc, is linked from there)."""
+    root = os.path.dirname(os.path.dirname(os.path.realpath(cc)))
+    for sub in ("lib64", "lib"):
+        d = os.path.join(root, sub)
+        if os.path.exists(os.path.join(d, "libnvrtc.so")):
+            return d
+    raise RuntimeError(f"libnvrtc.so not found under {root}")
+
+
 def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
@@ -38,7 +48,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     objdir = os.path.join(OUT_DIR, "obj")
     os.makedirs(objdir, exist_ok=True)
     srcs = sources()
-    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")] + \
+    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))] + \
         [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
@@ -59,7 +69,9 @@ def build(verbose: bool = False, force: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp"
-    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    libdir = cuda_lib_dir(cc)
+    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-L", libdir, "-lnvrtc", "-ldl", "-lpthread", "-Xlinker", "-rpath",
+                        "-Xlinker", libdir], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)

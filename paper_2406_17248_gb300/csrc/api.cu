@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "handles.h"
+#include "t2gen.h"
 
 using cd = std::complex<double>;
 
@@ -252,7 +253,8 @@ qs_status check_state(const qs_state* s) {
 
 // ---------------------------------------------------------------------------- circuit plan
 
-qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
+// host_only: plan on the host and stop before any device work (inspection).
+qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st, bool host_only = false) {
   CircuitPlan& P = c->plan;
   P.release();
   P.dt = dt;
@@ -325,7 +327,7 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
     }
   }
   P.n_coef = std::max(off, 1);
-  QS_CUDA(cudaMalloc(&P.d_coef, (size_t)P.n_coef * 16));
+  if (!host_only) QS_CUDA(cudaMalloc(&P.d_coef, (size_t)P.n_coef * 16));
   if (P.fuse < 0) {
     P.valid = true;
     return QS_OK;
@@ -336,7 +338,11 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
   // (states below 22 qubits have too few tiles to fill the GPU with one
   // 192 KB CTA per SM; their many small launches overlap better on the
   // interpreter kernel: the 2048-instance batch ran 5150 -> 3897 instances/s)
-  const bool micro = dt == QS_C64 && (P.fuse == 3 || (P.fuse == 1 && P.ne >= kMicroMinQubits));
+  // From 22 qubits the default compiles the micro-op passes for the circuit
+  // (t2gen.cu: the op dispatch taken out; 28-qubit random circuit 46.4 -> 15.0
+  // ms); fuse = 3 keeps the library's micro-op kernels.
+  const bool micro = dt == QS_C64 && (P.fuse == 3 || P.fuse == 4 || (P.fuse == 1 && P.ne >= kMicroMinQubits));
+  const bool gen = micro && P.fuse != 3;
   int m_fwd = P.m, m_rev = P.m;
   if (micro && !c->opts.tile_bits) {
     m_fwd = std::min(13, P.ne);
@@ -413,6 +419,8 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st) {
                         &P.rev_slots));
     P.rev_seg_end.push_back((int)P.rev.passes.size());
   }
+  P.fwd.gen = P.rev.gen = gen;
+  if (host_only) return QS_OK;
   QS_TRY(P.fwd.upload(st));
   QS_TRY(P.rev.upload(st));
   QS_TRY(build_csr(P.rev_slots, std::max(P.n_params, 1), &P.d_row, &P.d_sidx, &P.d_w, st));
@@ -514,7 +522,8 @@ qs_status run_passes(const TilePlan& plan, int begin, int end, qs_dtype dt, void
       rec->bytes = S * (((f & PF_LOAD_PSI) ? 1 : 0) + ((f & PF_LOAD_LAM) ? 1 : 0) + ((f & PF_STORE_PSI) ? 1 : 0) +
                         ((f & PF_STORE_LAM) ? 1 : 0)) +
                    ((f & PF_NEED_CUT) ? (double)(1ull << n) : 0.0);
-      rec->kind = plan.passes[i].t2 ? QS_TRACE_TILE2 : QS_TRACE_TILE;
+      const bool gen = (size_t)i < plan.gen_fn.size() && plan.gen_fn[i];
+      rec->kind = !plan.passes[i].t2 ? QS_TRACE_TILE : gen ? QS_TRACE_TILE2GEN : QS_TRACE_TILE2;
       QS_CUDA(cudaEventRecord(rec->end, st));
     }
   }
@@ -796,12 +805,65 @@ qs_status qs_circuit_finalize(qs_circuit* c, qs_dtype dtype, const qs_options* o
     QS_CHECK(opts->tile_bits == 0 || (opts->tile_bits >= kMinTileBits && opts->tile_bits <= kMaxTileBits),
              "tile_bits must be 0 or 6..13");
     QS_CHECK(opts->low_bits >= 0 && opts->low_bits <= kMaxTileBits, "low_bits must be 0..13");
-    QS_CHECK(opts->fuse >= -1 && opts->fuse <= 3, "fuse must be -1, 0, 1, 2 or 3");
+    QS_CHECK(opts->fuse >= -1 && opts->fuse <= 4, "fuse must be -1, 0, 1, 2, 3 or 4");
     QS_CHECK(opts->checkpoint >= 0, "checkpoint must be >= 0");
     c->opts = *opts;
   }
   cudaDeviceSynchronize();
   return finalize_plan(c, dtype, nullptr);
+}
+
+qs_status qs_circuit_codegen(qs_circuit* c, const qs_options* opts, int which, int compile, char* src, size_t cap,
+                             size_t* src_len, int* n_gen, size_t* cubin_bytes) {
+  QS_CHECK(c != nullptr, "null circuit");
+  QS_CHECK(which == 0 || which == 1, "which must be 0 (forward plan) or 1 (reverse plan)");
+  QS_CHECK(cap == 0 || src != nullptr, "src is null");
+  QS_CHECK(c->dm_n == 0, "density-matrix circuits are planned by their own engine");
+  QS_CHECK(!c->plan.valid, "qs_circuit_codegen takes a circuit that has not been finalized");
+  if (opts) {
+    QS_CHECK(opts->tile_bits == 0 || (opts->tile_bits >= kMinTileBits && opts->tile_bits <= kMaxTileBits),
+             "tile_bits must be 0 or 6..13");
+    QS_CHECK(opts->low_bits >= 0 && opts->low_bits <= kMaxTileBits, "low_bits must be 0..13");
+    QS_CHECK(opts->fuse >= 0 && opts->fuse <= 4, "fuse must be 0..4 for a generated plan");
+    QS_CHECK(opts->checkpoint >= 0, "checkpoint must be >= 0");
+  }
+  const qs_options saved = c->opts;
+  qs_options o = opts ? *opts : qs_options{};
+  if (!o.fuse) o.fuse = 4;
+  c->opts = o;
+  const qs_status st = finalize_plan(c, QS_C64, nullptr, true);
+  c->opts = saved;
+  auto done = [&](qs_status r) {
+    c->plan.release();
+    return r;
+  };
+  if (st != QS_OK) return done(st);
+  const TilePlan& plan = which == 0 ? c->plan.fwd : c->plan.rev;
+  std::string text;
+  std::vector<int> ids;
+  if (!t2gen_source(plan, &text, &ids)) {
+    set_error("a micro-op pass holds an op the generator does not write out");
+    return done(QS_ERR_UNSUPPORTED);
+  }
+  if (src_len) *src_len = text.size();
+  if (n_gen) *n_gen = (int)ids.size();
+  if (cap) {
+    const size_t k = std::min(cap - 1, text.size());
+    std::memcpy(src, text.data(), k);
+    src[k] = 0;
+  }
+  if (cubin_bytes) *cubin_bytes = 0;
+  if (compile && !ids.empty()) {  // as the plan's upload compiles them: one program per pass
+    std::vector<std::string> srcs(ids.size());
+    for (size_t k = 0; k < ids.size(); ++k) t2gen_pass_source(plan, ids[k], &srcs[k]);
+    std::vector<std::vector<char>> cubins;
+    const qs_status r = t2gen_compile(srcs, &cubins);
+    if (r != QS_OK) return done(r);
+    size_t tot = 0;
+    for (const auto& cb : cubins) tot += cb.size();
+    if (cubin_bytes) *cubin_bytes = tot;
+  }
+  return done(QS_OK);
 }
 
 qs_status qs_circuit_info(const qs_circuit* c, int* n_gates, int* n_params, int* n_passes) {

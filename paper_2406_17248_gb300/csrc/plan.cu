@@ -7,6 +7,7 @@
 #include <cstring>
 
 #include "plan.h"
+#include "t2gen.h"
 #include "tma.h"
 
 namespace qs {
@@ -575,6 +576,8 @@ qs_status TilePlan::upload(cudaStream_t st) {
   QS_CUDA(cudaMemcpyAsync(d_phase, hph.data(), hph.size() * sizeof(DevPhase), cudaMemcpyHostToDevice, st));
   QS_CUDA(cudaMemcpyAsync(d_ops, hops.data(), hops.size() * sizeof(DevOp), cudaMemcpyHostToDevice, st));
   QS_CUDA(cudaStreamSynchronize(st));
+  gen_fn.clear();
+  if (gen) QS_TRY(t2gen_build(*this));
   return QS_OK;
 }
 

@@ -47,6 +47,7 @@ SIGNATURES = [
     ("qs_circuit_destroy", [_VP]),
     ("qs_circuit_add", [_VP, _I, _PI, _I, _PI, _I, _I, _D, _D, _PD]),
     ("qs_circuit_finalize", [_VP, _I, _VP]),
+    ("qs_circuit_codegen", [_VP, _VP, _I, _I, C.c_char_p, _SZ, C.POINTER(_SZ), _PI, C.POINTER(_SZ)]),
     ("qs_circuit_info", [_VP, _PI, _PI, _PI]),
     ("qs_apply_circuit", [_VP, _VP, _PD, _I]),
     ("qs_circuit_autotune", [_VP, _VP, _PD, _I, _I, _VP, _PD]),
@@ -257,6 +258,21 @@ class Circuit:
         o = Options(fuse, tile_bits, low_bits, checkpoint)
         _check(lib().qs_circuit_finalize(self.h, dtype, C.byref(o)))
         return self
+
+    def codegen(self, which: int = 0, compile: bool = False, tile_bits: int = 0, low_bits: int = 0,
+                fuse: int = 4, cap: int = 1 << 22):
+        """Source of the per-circuit micro-op kernels of the forward (which = 0) or
+        adjoint (1) plan, compiled for sm_103a when `compile` (qs_circuit_codegen;
+        host only, the circuit must not be finalized).  Returns {"source",
+        "passes", "cubin_bytes"}."""
+        o = Options(fuse, tile_bits, low_bits, 0)
+        buf = C.create_string_buffer(cap)
+        ln, ng, cb = C.c_size_t(), C.c_int(), C.c_size_t()
+        _check(lib().qs_circuit_codegen(self.h, C.byref(o), which, int(bool(compile)), buf, cap, C.byref(ln),
+                                        C.byref(ng), C.byref(cb)))
+        if ln.value >= cap:
+            raise RuntimeError(f"generated source of {ln.value} bytes does not fit {cap}")
+        return {"source": buf.value.decode(), "passes": ng.value, "cubin_bytes": cb.value}
 
     def info(self):
         g, p, s = C.c_int(), C.c_int(), C.c_int()
@@ -703,7 +719,8 @@ def trace_enable(on: bool = True):
 TRACE_KINDS = {0: "tile_pass_kernel", 1: "qaoa_pass_kernel (psi)", 2: "qaoa_pass_kernel (psi, lam)",
                3: "qaoa_il_kernel (interleaved reverse)", 4: "batch_kernel", 5: "dense_tc_kernel (tcgen05)",
                6: "dense_cc_kernel", 7: "qx_kernel<false> (psi, forward)", 8: "qx_kernel<true> (turnaround)",
-               9: "qx_kernel<true> (psi/lam interleaved, reverse)", 10: "tile2_kernel (micro-op tile pass)"}
+               9: "qx_kernel<true> (psi/lam interleaved, reverse)", 10: "tile2_kernel (micro-op tile pass)",
+               11: "qs_t2g (per-circuit micro-op tile pass)"}
 
 
 def trace_read(max_records: int = 65536):

@@ -87,8 +87,9 @@ typedef struct qs_qaoa qs_qaoa;
 typedef struct {
   int fuse;       /* 1 (default): fused shared-memory tile passes (complex64 states of 22 or more
                      qubits run the passes that qualify as micro-ops on TMA-fed tiles, each pass
-                     compiled for the circuit at finalize by the runtime compiler, the rest on the
-                     op interpreter); 2: all on the op interpreter; 3: micro-ops wherever a pass
+                     of at most 192 ops (128 in adjoint passes) compiled for the circuit at
+                     finalize by the runtime compiler, larger ones on the precompiled micro-op
+                     kernels, the rest on the op interpreter); 2: all on the op interpreter; 3: micro-ops wherever a pass
                      qualifies, whatever the size, on the library's precompiled kernels (ops
                      dispatched from a table); 4: as 3, compiled for the circuit (the same
                      arithmetic as 3, bit for bit); -1: one kernel per gate.  Compiled passes

@@ -340,9 +340,10 @@ qs_status finalize_plan(qs_circuit* c, qs_dtype dt, cudaStream_t st, bool host_o
   // interpreter kernel: the 2048-instance batch ran 5150 -> 3897 instances/s)
   // From 22 qubits the default compiles the micro-op passes for the circuit
   // (t2gen.cu: the op dispatch taken out; 28-qubit random circuit 46.4 -> 15.0
-  // ms); fuse = 3 keeps the library's micro-op kernels.
+  // ms), each pass within the compile budget; fuse = 3 keeps the library's
+  // micro-op kernels, fuse = 4 compiles every micro-op pass.
   const bool micro = dt == QS_C64 && (P.fuse == 3 || P.fuse == 4 || (P.fuse == 1 && P.ne >= kMicroMinQubits));
-  const bool gen = micro && P.fuse != 3;
+  const int gen = !micro || P.fuse == 3 ? 0 : P.fuse == 4 ? 2 : 1;
   int m_fwd = P.m, m_rev = P.m;
   if (micro && !c->opts.tile_bits) {
     m_fwd = std::min(13, P.ne);

@@ -577,7 +577,7 @@ qs_status TilePlan::upload(cudaStream_t st) {
   QS_CUDA(cudaMemcpyAsync(d_ops, hops.data(), hops.size() * sizeof(DevOp), cudaMemcpyHostToDevice, st));
   QS_CUDA(cudaStreamSynchronize(st));
   gen_fn.clear();
-  if (gen) QS_TRY(t2gen_build(*this));
+  if (gen > 0) QS_TRY(t2gen_build(*this));
   return QS_OK;
 }
 

@@ -129,9 +129,11 @@ struct TilePlan {
   T2Phase* d_t2ph = nullptr;
   T2Op* d_t2ops = nullptr;
   std::vector<int> t2_phase_off, t2_op_off;  // per pass: first phase / op in the device arrays
-  // per-circuit kernels (t2gen.cu): compiled at upload when `gen` is set; the
-  // kernel of pass i in gen_fn[i] (null: the library's micro-op kernel)
-  bool gen = false;
+  // per-circuit kernels (t2gen.cu), compiled at upload: gen = 1 for the
+  // micro-op passes within the compile budget (t2gen_budget_ops), 2 for every
+  // micro-op pass; the kernel of pass i in gen_fn[i] (null: the library's
+  // micro-op kernel, the same arithmetic)
+  int gen = 0;
   std::vector<void*> gen_fn;
   void free_device();
   qs_status upload(cudaStream_t st);

@@ -286,12 +286,16 @@ qs_status t2gen_compile(const std::vector<std::string>& srcs, std::vector<std::v
   return QS_OK;
 }
 
+int t2gen_budget_ops(int ns) { return ns == 2 ? 128 : 192; }
+
 qs_status t2gen_build(TilePlan& plan) {
   plan.gen_fn.assign(plan.passes.size(), nullptr);
   std::vector<int> ids;
   std::vector<std::string> srcs;
   for (int pi = 0; pi < (int)plan.passes.size(); ++pi) {
     if (!plan.passes[pi].t2) continue;
+    const T2Pass& h = plan.passes[pi].t2hdr;
+    if (plan.gen == 1 && h.n_ops > t2gen_budget_ops(h.ns)) continue;
     std::string src;
     if (!t2gen_pass_source(plan, pi, &src)) {
       set_error("a micro-op pass holds an op the generator does not write out");

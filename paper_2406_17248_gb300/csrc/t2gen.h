@@ -16,6 +16,10 @@ bool t2gen_pass_source(const TilePlan& plan, int pi, std::string* src);
 // Compiles generated sources for sm_103a on the host's cores (runtime
 // compiler; needs no GPU).
 qs_status t2gen_compile(const std::vector<std::string>& srcs, std::vector<std::vector<char>>* cubins);
+// Ops above which a pass is left to the library kernel when plan.gen == 1
+// (compile time grows with the ops of a pass: about 30 ms per op of a
+// one-state pass and 45 ms of a two-state pass on one host core).
+int t2gen_budget_ops(int ns);
 // Compiles (or finds in the process cache) and loads the plan's generated
 // passes; fills plan.gen_fn.
 qs_status t2gen_build(TilePlan& plan);

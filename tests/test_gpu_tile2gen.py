@@ -115,3 +115,28 @@ def test_generated_kernels_are_cached_by_source(Q):
     _, kinds = traced(Q, lambda: c2.apply(s, []))
     assert (kinds == GEN).all()
     assert second < 0.5 * first, (first, second)
+
+
+def test_default_compiles_passes_within_budget_22q(Q):
+    """fuse = 1 from 22 qubits: passes within the op budget compiled for the
+    circuit, larger ones (the first adjoint pass of this ansatz, 131 ops) on the
+    library kernel; all results equal fuse = 3's bit for bit."""
+    n = 22
+    circ = I.hea_circuit(n, 4)
+    rng = np.random.default_rng(5700)
+    ham = I.tfim(n, rng)
+    H = Q.Hamiltonian(ham)
+    params = rng.uniform(-np.pi, np.pi, circ.n_params)
+    res = {}
+    for fuse in (1, 3):
+        c = Q.circuit_from(circ).finalize(Q.C64, fuse=fuse)
+        psi, lam = Q.State(n, Q.C64).set_basis(0), Q.State(n, Q.C64)
+        (E, g), kinds = traced(Q, lambda: Q.expectation_with_grad(psi, lam, c, H, params))
+        res[fuse] = (E, np.asarray(g), kinds)
+    kinds = res[1][2]
+    assert (kinds == GEN).any() and (kinds == MICRO).sum() == 1, kinds
+    assert not (res[3][2] == GEN).any()
+    assert res[1][0] == res[3][0] and np.array_equal(res[1][1], res[3][1])
+    E0, g0 = O.adjoint_gradient(circ, ham, params, O.zero_state(n))
+    check("default 22q HEA energy", abs(res[1][0] - E0), energy_tol(0, ham))
+    check("default 22q HEA grad", np.abs(res[1][1] - g0), grad_tol(0, ham, circ))

@@ -905,9 +905,12 @@ def run_dm_workload(args):
     wall = (time.perf_counter() - t0) / args.steps
     Q.trace_enable(False)
     ck = clocks.stop()
-    k_ms, k_by, _ = Q.trace_read()
+    k_ms, k_by, k_kind = Q.trace_read()
     peak, peak_kind = measured_peak_hbm()
     ach = float(k_by.sum() / (k_ms.sum() / 1e3) / 1e9)
+    # the passes' kernels by traced time (compiled per circuit, library micro-op, interpreter)
+    kinds = {int(k): float(k_ms[k_kind == k].sum()) for k in np.unique(k_kind)} if len(k_ms) else {}
+    top = Q.TRACE_KINDS.get(max(kinds, key=kinds.get), "?") if kinds else None
     line = {"metric": "noisy density-matrix evolutions + tr(rho H)/s, 14 qubits (28-qubit vector) complex64",
             "value": 1.0 / wall, "unit": "evals/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
             "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -915,8 +918,9 @@ def run_dm_workload(args):
             "config": {"workload": "14-qubit HEA, 4 layers, params U[-pi,pi] seed 1, depolarizing 0.01 on every "
                                    "qubit after every layer; H = sum ZZ + 0.5 sum X", "l2": "2 GiB state > L2"},
             "energy": E, "passes": c.info()["passes"],
-            "roofline": {"bound": "hbm", "kernel": "tile_pass_kernel", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "roofline": {"bound": "hbm", "kernel": top, "achieved": ach, "peak": peak, "unit": "GB/s",
                          "frac": ach / peak, "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs"},
+            "pass_kernels_ms": {Q.TRACE_KINDS.get(k, str(k)): v / max(args.steps, 1) for k, v in kinds.items()},
             "gpu_launches": int(len(k_ms) / max(args.steps, 1)) + 3, "clocks": ck}
     if not args.no_cpu_baseline:
         from oracle import dm_oracle as D

@@ -382,29 +382,30 @@ __global__ void __launch_bounds__(kWsThreads, 1) dense_ws_kernel(float2* __restr
 
   if (tid < kWsProducers) {
     // ------------------------------------------------------------ producers
-    // thread: row tid % 128, quarter tid / 128 of its amplitudes; the next
-    // tile's amplitudes are loaded before this tile's are split and stored, so
-    // two tiles' gathers are in flight per thread
+    // thread: row tid % 128, quarter tid / 128 of its amplitudes; the two
+    // following tiles' amplitudes are loaded before this tile's are split and
+    // stored, so three tiles' gathers are in flight per thread
     const int row = tid & (kTcRows - 1), qt = tid / kTcRows;
-    float2 xn[KQ];
+    float2 xn[KQ], xnn[KQ];
     uint64_t tile = blockIdx.x;
-    if (tile < n_tiles) {
-      const uint64_t base = deposit_other(G, tile * kTcRows + row);
+    auto gather = [&](uint64_t t, float2(&dst)[KQ]) {
+      if (t >= n_tiles) return;
+      const uint64_t base = deposit_other(G, t * kTcRows + row);
 #pragma unroll
-      for (int j = 0; j < KQ; ++j) xn[j] = psi[base | G.tgt_off[qt * KQ + j]];
-    }
+      for (int j = 0; j < KQ; ++j) dst[j] = psi[base | G.tgt_off[qt * KQ + j]];
+    };
+    gather(tile, xn);
+    gather(tile + gridDim.x, xnn);
     int i = 0;
     for (; tile < n_tiles; tile += gridDim.x, ++i) {
       const int st = i & 1;
       float2 x[KQ];
 #pragma unroll
-      for (int j = 0; j < KQ; ++j) x[j] = xn[j];
-      const uint64_t next = tile + gridDim.x;
-      if (next < n_tiles) {
-        const uint64_t nb = deposit_other(G, next * kTcRows + row);
-#pragma unroll
-        for (int j = 0; j < KQ; ++j) xn[j] = psi[nb | G.tgt_off[qt * KQ + j]];
+      for (int j = 0; j < KQ; ++j) {
+        x[j] = xn[j];
+        xn[j] = xnn[j];
       }
+      gather(tile + 2ull * gridDim.x, xnn);
       if (i >= 2 && !ws_wait(empty0 + 8 * st, (uint32_t)(((i - 2) >> 1) & 1))) {
         bad = true;
         break;

@@ -121,6 +121,7 @@ __device__ __forceinline__ uint32_t op_offset(int row, int kk, int KR) {
 struct DenseGeom {
   int n, k;
   int n_other;
+  int pair0;  // target 0 is qubit 0 and the state 16-byte aligned: columns (2c, 2c + 1) form one 16-byte word
   uint64_t tgt_off[1 << kDenseMaxK];  // deposit(j, targets)
   uint8_t other_bit[64];              // bit position of the b-th other bit
 };
@@ -391,8 +392,17 @@ __global__ void __launch_bounds__(kWsThreads, 1) dense_ws_kernel(float2* __restr
     auto gather = [&](uint64_t t, float2(&dst)[KQ]) {
       if (t >= n_tiles) return;
       const uint64_t base = deposit_other(G, t * kTcRows + row);
+      if (G.pair0) {
 #pragma unroll
-      for (int j = 0; j < KQ; ++j) dst[j] = psi[base | G.tgt_off[qt * KQ + j]];
+        for (int c = 0; c < KQ / 2; ++c) {
+          const float4 v = *reinterpret_cast<const float4*>(psi + (base | G.tgt_off[qt * KQ + 2 * c]));
+          dst[2 * c] = make_float2(v.x, v.y);
+          dst[2 * c + 1] = make_float2(v.z, v.w);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < KQ; ++j) dst[j] = psi[base | G.tgt_off[qt * KQ + j]];
+      }
     };
     gather(tile, xn);
     gather(tile + gridDim.x, xnn);
@@ -486,8 +496,15 @@ __global__ void __launch_bounds__(kWsThreads, 1) dense_ws_kernel(float2* __restr
       for (int c0 = 0; c0 < KR; c0 += 16) {
         float v[16];
         tmem_ld16(trow + c0, v);
+        if (G.pair0) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) psi[base | G.tgt_off[c0 / 2 + q]] = make_float2(v[2 * q], v[2 * q + 1]);
+          for (int q = 0; q < 8; q += 2)
+            *reinterpret_cast<float4*>(psi + (base | G.tgt_off[c0 / 2 + q])) =
+                make_float4(v[2 * q], v[2 * q + 1], v[2 * q + 2], v[2 * q + 3]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) psi[base | G.tgt_off[c0 / 2 + q]] = make_float2(v[2 * q], v[2 * q + 1]);
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -658,6 +675,7 @@ qs_status qs_apply_matrix(qs_state* s, int k, const int* targets, const double* 
   G.n_other = 0;
   for (int q = 0; q < s->ne; ++q)
     if (!((tmask >> q) & 1ull)) G.other_bit[G.n_other++] = (uint8_t)q;
+  G.pair0 = (targets[0] == 0 && ((uintptr_t)s->ptr & 15) == 0) ? 1 : 0;
   const bool tc_ok = s->dt == QS_C64 && (k == 4 || k == 5) && (s->ne - k) >= 7;
   QS_CHECK(engine != 2 || tc_ok, "tensor-core blocks need complex64, k = 4 or 5 and at least 7 other qubits");
   const bool use_tc = engine == 2 || (engine == 0 && tc_ok);

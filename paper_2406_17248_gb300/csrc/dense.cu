@@ -664,6 +664,31 @@ qs_status qs_apply_matrix(qs_state* s, int k, const int* targets, const double* 
   }
   const int KB = 1 << k;
   for (int e = 0; e < 2 * KB * KB; ++e) QS_CHECK(std::isfinite(matrix[e]), "non-finite matrix entry");
+  // With qubit 0 among the targets, list it first (the matrix's index bits
+  // permuted to match: the same operator), so that each column pair of a row is
+  // one 16-byte word of the state.
+  int tg[kDenseMaxK];
+  for (int b = 0; b < k; ++b) tg[b] = targets[b];
+  std::vector<double> permuted;
+  int b0 = -1;
+  for (int b = 0; b < k; ++b)
+    if (targets[b] == 0) b0 = b;
+  if (b0 > 0) {
+    auto old_index = [&](int jn) {  // new bit 0 <- old bit b0, new bits 1..b0 <- old bits 0..b0-1
+      int jo = 0;
+      for (int p = 0; p < k; ++p) jo |= ((jn >> p) & 1) << (p == 0 ? b0 : p <= b0 ? p - 1 : p);
+      return jo;
+    };
+    permuted.resize(2 * (size_t)KB * KB);
+    for (int r = 0; r < KB; ++r)
+      for (int c = 0; c < KB; ++c)
+        for (int z = 0; z < 2; ++z)
+          permuted[2 * ((size_t)r * KB + c) + z] = matrix[2 * ((size_t)old_index(r) * KB + old_index(c)) + z];
+    tg[0] = 0;
+    for (int p = 1; p <= b0; ++p) tg[p] = targets[p - 1];
+    targets = tg;
+    matrix = permuted.data();
+  }
   DenseGeom G{};
   G.n = s->ne;
   G.k = k;

@@ -72,6 +72,23 @@ def test_tensor_core_blocks_many_tiles_per_cta(Q, k):
     assert err <= 2e-6
 
 
+@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("pos", [1, 2, 4])
+def test_tensor_core_blocks_qubit0_not_first(Q, k, pos):
+    """Qubit 0 listed at another position than first: the library lists it
+    first with the matrix's index bits permuted to match (so that column pairs
+    move as 16-byte words); the result is the same operator on the same bits,
+    for the many-tile launch and for the cuda-core engine."""
+    if pos >= k:
+        pytest.skip("position beyond k")
+    n = 21
+    targets = [1, 6, 11, 16, 20][:k]
+    targets[pos] = 0
+    U = _unitary(k, 40 + 3 * k + pos)
+    assert _run(Q, n, Q.C64, targets, U, 2, 11) <= 2e-6
+    assert _run(Q, 12, Q.C64, [t % 12 for t in targets], U, 1, 12) <= TOL[0]
+
+
 def test_tensor_core_identity_and_permutation(Q):
     n, k = 13, 5
     psi0 = I.random_state(n, 9).astype(np.complex64)

@@ -316,7 +316,7 @@ struct WsCfg {
   static constexpr int KB = 1 << K, KR = 2 * KB;
   static constexpr int A_BYTES = kTcRows * KR * 4, B_BYTES = KR * KR * 4;
   static constexpr int TMEM_COLS = 2 * KR < 32 ? 32 : 2 * KR;
-  static constexpr size_t SMEM = 4 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + 16 * 8 + 128;
+  static constexpr size_t SMEM = 4 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + 16 * 8 + 3 * 256 * 8 + 128;
 };
 
 __device__ __forceinline__ bool ws_wait(uint32_t mbar, uint32_t parity) {
@@ -347,7 +347,23 @@ __global__ void __launch_bounds__(kWsThreads, 1) dense_ws_kernel(float2* __restr
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + 2), tfull0 = smem_u32(bars + 4),
                  tempty0 = smem_u32(bars + 6);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 8);
+  // row index r = tile * 128 + row: its other-qubit offset is deposit(row) |
+  // deposit(tile << 7); the tile part comes from three tables of 8 tile bits
+  // (tiles < 2^24: n - k - 7 <= 23)
+  uint64_t* s_dep = bars + 16;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < 3 * 256; e += kWsThreads) {
+    const int c = e >> 8, v = e & 255;
+    uint64_t x = 0;
+    for (int i = 0; i < 8; ++i) {
+      const int b = 7 + 8 * c + i;
+      if (((v >> i) & 1) && b < G.n_other) x |= 1ull << G.other_bit[b];
+    }
+    s_dep[e] = x;
+  }
+  auto tile_dep = [&](uint64_t t) {
+    return s_dep[t & 255] | s_dep[256 + ((t >> 8) & 255)] | s_dep[512 + ((t >> 16) & 255)];
+  };
 
   for (int e = tid; e < KR * KR; e += kWsThreads) {  // B = real form of U^T, split h/t (as above)
     const int n = e / KR, kk = e % KR;
@@ -387,11 +403,12 @@ __global__ void __launch_bounds__(kWsThreads, 1) dense_ws_kernel(float2* __restr
     // following tiles' amplitudes are loaded before this tile's are split and
     // stored, so three tiles' gathers are in flight per thread
     const int row = tid & (kTcRows - 1), qt = tid / kTcRows;
+    const uint64_t row_dep = deposit_other(G, (uint64_t)row);
     float2 xn[KQ], xnn[KQ];
     uint64_t tile = blockIdx.x;
     auto gather = [&](uint64_t t, float2(&dst)[KQ]) {
       if (t >= n_tiles) return;
-      const uint64_t base = deposit_other(G, t * kTcRows + row);
+      const uint64_t base = row_dep | tile_dep(t);
       if (G.pair0) {
 #pragma unroll
         for (int c = 0; c < KQ / 2; ++c) {
@@ -482,6 +499,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) dense_ws_kernel(float2* __restr
     // four epilogue warps (9..12) cover the quarters 1, 2, 3, 0
     const int ew = warp & 3;
     const int row = ew * 32 + lane;
+    const uint64_t row_dep = deposit_other(G, (uint64_t)row);
     int i = 0;
     for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
       const int ac = i & 1;
@@ -490,7 +508,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) dense_ws_kernel(float2* __restr
         break;
       }
       tc_fence_after();
-      const uint64_t base = deposit_other(G, tile * kTcRows + row);
+      const uint64_t base = row_dep | tile_dep(tile);
       const uint32_t trow = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(ac * KR);
 #pragma unroll
       for (int c0 = 0; c0 < KR; c0 += 16) {

@@ -141,7 +141,8 @@ struct TcCfg {
   static constexpr int A_BYTES = kTcRows * KR * 4;
   static constexpr int B_BYTES = KR * KR * 4;
   static constexpr int TMEM_COLS = KR < 32 ? 32 : KR;
-  static constexpr size_t SMEM = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + 64 + 128;  // + barrier, slack for align
+  // + barrier, tile-bit tables, slack for align
+  static constexpr size_t SMEM = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + 64 + 3 * 256 * 8 + 128;
 };
 
 template <int K>
@@ -158,11 +159,40 @@ __global__ void __launch_bounds__(kTcThreads) dense_tc_kernel(float2* __restrict
   unsigned char* b_lo = b_hi + Cfg::B_BYTES;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(b_lo + Cfg::B_BYTES);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint64_t* s_dep = mbar + 8;  // [3][256]: tile bits 8c.. deposited into the other qubits
   __shared__ int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row = tid & (kTcRows - 1), half = tid / kTcRows;
   constexpr int KH = KB / 2;  // amplitudes per thread
+  // row index r = tile * 128 + row: offset deposit(row) | deposit(tile << 7)
+  // (tiles < 2^24: n - k - 7 <= 23)
+  for (int e = tid; e < 3 * 256; e += kTcThreads) {
+    const int c = e >> 8, v = e & 255;
+    uint64_t xd = 0;
+    for (int i = 0; i < 8; ++i) {
+      const int b = 7 + 8 * c + i;
+      if (((v >> i) & 1) && b < G.n_other) xd |= 1ull << G.other_bit[b];
+    }
+    s_dep[e] = xd;
+  }
+  const uint64_t row_dep = deposit_other(G, (uint64_t)row);
+  auto tile_dep = [&](uint64_t t) {
+    return s_dep[t & 255] | s_dep[256 + ((t >> 8) & 255)] | s_dep[512 + ((t >> 16) & 255)];
+  };
+  auto gather = [&](uint64_t b, float2(&dst)[KH]) {
+    if (G.pair0) {  // column pairs (2c, 2c + 1) as one 16-byte word
+#pragma unroll
+      for (int c = 0; c < KH / 2; ++c) {
+        const float4 v = *reinterpret_cast<const float4*>(psi + (b | G.tgt_off[half * KH + 2 * c]));
+        dst[2 * c] = make_float2(v.x, v.y);
+        dst[2 * c + 1] = make_float2(v.z, v.w);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < KH; ++j) dst[j] = psi[b | G.tgt_off[half * KH + j]];
+    }
+  };
   // B[n][kk] = W[kk][n], W = real form of U^T (see the file comment); split h/t
   for (int e = tid; e < KR * KR; e += kTcThreads) {
     const int n = e / KR, kk = e % KR;
@@ -201,9 +231,8 @@ __global__ void __launch_bounds__(kTcThreads) dense_tc_kernel(float2* __restrict
   float2 x[KH];
   uint64_t base = 0;
   if (tile < n_tiles) {
-    base = deposit_other(G, tile * kTcRows + row);
-#pragma unroll
-    for (int j = 0; j < KH; ++j) x[j] = psi[base | G.tgt_off[half * KH + j]];
+    base = row_dep | tile_dep(tile);
+    gather(base, x);
   }
   for (; tile < n_tiles; tile += gridDim.x) {
     // split this thread's half row into tf32 head and tail, K-major core-matrix layout
@@ -244,9 +273,8 @@ __global__ void __launch_bounds__(kTcThreads) dense_tc_kernel(float2* __restrict
     uint64_t nbase = 0;
     float2 xn[KH];
     if (next < n_tiles) {
-      nbase = deposit_other(G, next * kTcRows + row);
-#pragma unroll
-      for (int j = 0; j < KH; ++j) xn[j] = psi[nbase | G.tgt_off[half * KH + j]];
+      nbase = row_dep | tile_dep(next);
+      gather(nbase, xn);
     } else {
 #pragma unroll
       for (int j = 0; j < KH; ++j) xn[j] = make_float2(0.f, 0.f);
@@ -280,8 +308,15 @@ __global__ void __launch_bounds__(kTcThreads) dense_tc_kernel(float2* __restrict
     for (int c0 = half * KB; c0 < half * KB + KB; c0 += 16) {
       float v[16];
       tmem_ld16(trow + c0, v);
+      if (G.pair0) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) psi[base | G.tgt_off[c0 / 2 + q]] = make_float2(v[2 * q], v[2 * q + 1]);
+        for (int q = 0; q < 8; q += 2)
+          *reinterpret_cast<float4*>(psi + (base | G.tgt_off[c0 / 2 + q])) =
+              make_float4(v[2 * q], v[2 * q + 1], v[2 * q + 2], v[2 * q + 3]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) psi[base | G.tgt_off[c0 / 2 + q]] = make_float2(v[2 * q], v[2 * q + 1]);
+      }
     }
     tc_fence_before();
     __syncthreads();
